@@ -1,0 +1,204 @@
+/*
+ * di.h -- C ABI of the GB300 homogeneous diffusion inpainting decoder.
+ *
+ * The decoder solves, per colour channel, the discrete inpainting problem of
+ * Section 2.2 (eq. 2.6):
+ *     (C + (I - C) L) u = C f,
+ * c the binary mask (known pixels), L the 5-point negated Laplacian with
+ * reflecting image boundaries and unit grid spacing.  The solver is the
+ * reduced full multigrid of Section 4.2 with the optimized restricted additive
+ * Schwarz smoother of Section 3 (Algorithm 2) and the grid transfers of
+ * Sections 4.3 and 4.4.  Everything runs in hand-written CUDA kernels for
+ * sm_103a on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Images are planar float32 [channels][height][width], row-major, in DEVICE
+ *    memory; masks are uint8 [height][width] in DEVICE memory, nonzero = known
+ *    pixel, shared by all channels.  Channels are 1..4.
+ *  - The caller owns every pointer it passes; the library never frees them.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue their kernels on it; argument errors are reported synchronously
+ *    and nothing is enqueued then.  DI_ERR_CUDA reports a failed launch or
+ *    allocation error from the CUDA runtime.
+ *  - Values of f at unknown pixels are never used in arithmetic (they may be
+ *    NaN or Inf).
+ *  - A context may be used from one host thread at a time.
+ */
+#ifndef DI_H
+#define DI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct di_ctx di_ctx;
+
+typedef enum {
+    DI_OK = 0,
+    DI_ERR_INVALID_ARG = 1,   /* null pointer, size < 1, channels not in 1..4,
+                                 tol <= 0, aliasing buffers, bad config */
+    DI_ERR_EMPTY_MASK = 2,    /* no known pixel: the problem has no unique solution */
+    DI_ERR_OOM = 3,           /* device workspace could not be allocated */
+    DI_ERR_NOT_CONVERGED = 4, /* max_cycles reached first; u holds the last iterate */
+    DI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    DI_ERR_TIMEOUT = 6        /* reserved for bounded device-side waits */
+} di_status;
+
+/* Stop rules of di_inpaint.  DI_STOP_ERROR_ESTIMATE: after every V-cycle the
+ * error is estimated from the size of the cycle's updates and their decay
+ * (est = U_k q/(1-q), q the larger of the last two ratios U_k/U_{k-1}, U_k the
+ * sum of the largest pre-smoothing, coarse-correction and post-smoothing
+ * updates on the finest grid); the solve stops when est <= tol/2.  DI_STOP_RELATIVE_RESIDUAL: the paper's criterion
+ * (Section 5.2), ||b - A u||_2 / ||b||_2 <= tol, per channel.
+ * DI_STOP_FIXED_CYCLES: exactly max_cycles V-cycles. */
+enum { DI_STOP_ERROR_ESTIMATE = 0, DI_STOP_RELATIVE_RESIDUAL = 1, DI_STOP_FIXED_CYCLES = 2 };
+
+/* Solver configuration; a zero field takes the default in brackets. */
+typedef struct {
+    int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
+    int overlap;      /* o, overlap of neighbouring blocks, 1..B/2 [6] (Section 3.1) */
+    int local_iters;  /* Jacobi-PCG steps of each local block solve [8] (Section 3.1) */
+    int coarse_iters; /* cap on the PCG steps of the single-block solve of the coarsest
+                         level, which otherwise runs to a relative residual of ~1e-6 [2048] */
+    int pre;          /* ORAS pre-smoothing iterations per V-cycle [1] (Section 4.4) */
+    int post;         /* ORAS post-smoothing iterations per V-cycle [1] (Section 4.4) */
+    int max_cycles;   /* cap on V-cycles after the cascade [16] */
+    int min_cycles;   /* V-cycles always run [1] */
+    float alpha;      /* Robin parameter of the inner block boundaries, > 0 [0.5] (Section 3) */
+    int downsample;   /* mask-value downsampling: 0 modified [default], 1 naive (Section 4.3) */
+    int stop_rule;    /* DI_STOP_* [DI_STOP_ERROR_ESTIMATE] */
+    int reserved[5];
+} di_config;
+
+/* Statistics of the last di_inpaint call on a context. */
+typedef struct {
+    int levels;            /* levels of the full pyramid (coarsest fits one block) */
+    int levels_used;       /* levels down to the first one without unknown pixels */
+    int cycles;            /* V-cycles run after the cascade */
+    int converged;         /* 1 if the stop rule was met */
+    float est_error;       /* last error estimate (gray levels), DI_STOP_ERROR_ESTIMATE */
+    float rel_residual[4]; /* final ||b - A u||_2 / ||b||_2 per channel (if computed) */
+    long long unknowns;    /* unknown pixels on the finest level */
+} di_stats;
+
+/* Static plan of a solve, computed on the host without touching a GPU. */
+typedef struct {
+    int levels;                /* pyramid depth: halve (rounding up) until max(w, h) <= B */
+    int width[24], height[24]; /* level sizes, level 0 = the image */
+    int blocks_x[24], blocks_y[24]; /* ORAS blocks per axis: ceil((n - o) / (B - o)), >= 1 */
+    long long local_problems;  /* blocks x channels on level 0 (36852 for 4K RGB, B=32, o=6,
+                                  Section 3.1) */
+    long long workspace_bytes; /* device bytes di_inpaint allocates for this image */
+} di_plan_info;
+
+/* Fill *out for an image of width x height x channels under cfg (NULL =
+ * defaults).  Pure host code; usable to size device memory before a solve. */
+di_status di_plan(const di_config *cfg, int width, int height, int channels,
+                  di_plan_info *out);
+
+/* Create a context bound to CUDA device `device`.  cfg may be NULL (all
+ * defaults).  Workspace (pyramids, block-weight buffers) is allocated lazily
+ * by di_inpaint and grows with the largest image seen; it is freed by
+ * di_destroy. */
+di_status di_create(const di_config *cfg, int device, di_ctx **out);
+
+/* Destroy a context and free its workspace; NULL is allowed. */
+void di_destroy(di_ctx *ctx);
+
+/* Inpaint f (known where c != 0) into u: the full decoder path.
+ *  f: device [channels][height][width] float32, read only at mask pixels.
+ *  c: device [height][width] uint8.
+ *  u: device output, same layout as f; must not overlap f.  On DI_OK and on
+ *     DI_ERR_NOT_CONVERGED it holds the solution (mask pixels equal f
+ *     exactly).
+ *  tol: target of the stop rule (gray levels for the error estimate, a ratio
+ *     for the relative residual), > 0.
+ * The call enqueues its kernels on `stream` and waits for the stream once per
+ * V-cycle to evaluate the stop rule, so it returns with the work finished. */
+di_status di_inpaint(di_ctx *ctx, const float *f, const uint8_t *c, int width, int height,
+                     int channels, float tol, float *u, void *stream);
+
+/* Statistics of the last di_inpaint call. */
+di_status di_get_stats(const di_ctx *ctx, di_stats *out);
+
+/* Human-readable name of a status code (static storage). */
+const char *di_status_string(di_status s);
+
+/* Last CUDA error text seen by the context (static per context, may be ""). */
+const char *di_last_error(const di_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Single steps of the path.  Each runs one kernel (or one kernel pair) of the
+ * solver on caller buffers; di_inpaint composes them.  They exist so each step
+ * can be checked on its own.
+ * ------------------------------------------------------------------------ */
+
+/* Mask downsampling by 2x2 max pooling (Section 4.3, "Mask Downsampling").
+ * c: [h][w]; cH: [ceil(h/2)][ceil(w/2)] output.  A coarse pixel is known iff
+ * any of its (up to four, fewer on odd edges) fine children is. */
+di_status di_mask_downsample(const uint8_t *c, int width, int height, uint8_t *cH,
+                             void *stream);
+
+/* Mask-value downsampling (Section 4.3).  b: [ch][h][w] values, read only
+ * where c != 0; cH: the downsampled mask; bH: [ch][ceil(h/2)][ceil(w/2)]
+ * output, 0 where cH == 0.  modified = 1: weights c (4 - masks of the four
+ * direct neighbours; fine masks inside the coarse cell, coarse masks across
+ * it, out-of-image neighbours unmasked), falling back to the naive average
+ * where a masked coarse cell gets total weight 0; modified = 0: the naive
+ * average of the masked children. */
+di_status di_values_downsample(const uint8_t *c, const float *b, int width, int height,
+                               int channels, const uint8_t *cH, float *bH, int modified,
+                               void *stream);
+
+/* Residual r = b - A u with A = C + (I - C) L (Algorithm 2 step 1, eq. 2.6),
+ * and its squared 2-norm per channel.
+ *  b: [ch][h][w]: at mask pixels the Dirichlet value, at unknown pixels the
+ *     right-hand side of L u = b; if rhs_zero != 0 the right-hand side at
+ *     unknown pixels is taken as 0 and b is read only at mask pixels.
+ *  r: [ch][h][w] output, may be NULL (norm only).
+ *  norm2: device double[channels] output.
+ * Needs a context for its reduction workspace; the sums are formed in a fixed
+ * order (deterministic). */
+di_status di_residual_norm(di_ctx *ctx, const float *u, const float *b, int rhs_zero,
+                           const uint8_t *c, int width, int height, int channels, float *r,
+                           double *norm2, void *stream);
+
+/* Residual restriction (Algorithm 3 steps 2-3, Section 4.4): for every coarse
+ * cell with cH == 0, rH = 4 * mean over its fine children of (b - A u) (the
+ * factor 4 = (H/h)^2 rescales the unit-spacing stencil to the coarse
+ * spacing); rH = 0 where cH == 1.  Arguments as for di_residual_norm. */
+di_status di_restrict_residual(const float *u, const float *b, int rhs_zero,
+                               const uint8_t *c, int width, int height, int channels,
+                               const uint8_t *cH, float *rH, void *stream);
+
+/* Cell-centred bilinear prolongation (Section 4.4) from uH
+ * [ch][ceil(h/2)][ceil(w/2)] to the fine grid [ch][h][w] (weights 9/16, 3/16,
+ * 3/16, 1/16, coarse indices clamped at the border).
+ *  mode 0 (cascadic): u = b at mask pixels, P uH elsewhere (b read only at
+ *         mask pixels).
+ *  mode 1 (correction): u += P uH at unknown pixels, u unchanged at mask
+ *         pixels (b unused, may be NULL). */
+di_status di_prolong(const float *uH, const float *b, const uint8_t *c, int width, int height,
+                     int channels, float *u, int mode, void *stream);
+
+/* One ORAS iteration (Algorithm 2) with the context's block size, overlap
+ * and alpha: r = b - A u_in; on every block i, `local_iters` Jacobi-PCG steps
+ * (from 0) on A_i v_i = R_i r, A_i = A restricted to the block with Robin rows
+ * on inner block edges (Section 3); u_out = u_in + sum_i R_i^T D_i v_i with
+ * the separable linear partition-of-unity weights of Section 3.1.
+ *  u_in: [ch][h][w]; must equal b at mask pixels (then r = 0 there).
+ *  b, rhs_zero: as for di_residual_norm.
+ *  u_out: [ch][h][w] output; must not overlap u_in.
+ * Deterministic: overlapping contributions are summed in a fixed order. */
+di_status di_oras_iteration(di_ctx *ctx, const float *u_in, const float *b, int rhs_zero,
+                            const uint8_t *c, int width, int height, int channels,
+                            int local_iters, float *u_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DI_H */

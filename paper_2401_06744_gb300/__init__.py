@@ -1,0 +1,20 @@
+"""GB300-native homogeneous diffusion inpainting decoder.
+
+Solves (C + (I - C) L) u = C f per colour channel (Kaemper, Chizhov, Weickert,
+"Efficient Parallel Algorithms for Inpainting-Based Representations of 4K
+Images - Part I", Section 2.2) by reduced full multigrid (Section 4.2) with an
+optimized restricted additive Schwarz block smoother (Section 3, Algorithm 2),
+in hand-written CUDA kernels for sm_103a behind the C ABI of include/di.h.
+
+    import torch, paper_2401_06744_gb300 as di
+    ctx = di.Context()
+    u, status = ctx.inpaint(f_cuda_float32_CHW, mask_cuda_uint8_HW, tol=0.05)
+"""
+from ._lib import (  # noqa: F401
+    CUDA_ERROR, EMPTY_MASK, INVALID_ARG, NOT_CONVERGED, OK, OOM, STOP_ERROR_ESTIMATE,
+    STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
+    exported_symbols, load, mask_downsample, plan, prolong, restrict_residual, status_string,
+    values_downsample)
+
+__all__ = ["Context", "DiError", "load", "plan", "mask_downsample", "values_downsample",
+           "restrict_residual", "prolong", "status_string", "exported_symbols", "LIB_PATH"]

@@ -1,0 +1,283 @@
+"""ctypes binding of libdi.so (the C ABI in include/di.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are torch CUDA tensors (PyTorch provides device memory and streams);
+outputs are allocated with torch on the input's device when not given.
+There is no CPU fallback: if libdi.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdi.so")
+
+OK, INVALID_ARG, EMPTY_MASK, OOM, NOT_CONVERGED, CUDA_ERROR, TIMEOUT = range(7)
+STOP_ERROR_ESTIMATE, STOP_RELATIVE_RESIDUAL, STOP_FIXED_CYCLES = range(3)
+
+
+class di_config(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("overlap", ctypes.c_int),
+                ("local_iters", ctypes.c_int), ("coarse_iters", ctypes.c_int),
+                ("pre", ctypes.c_int), ("post", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("min_cycles", ctypes.c_int),
+                ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
+                ("stop_rule", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class di_stats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("levels_used", ctypes.c_int),
+                ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
+                ("est_error", ctypes.c_float), ("rel_residual", ctypes.c_float * 4),
+                ("unknowns", ctypes.c_longlong)]
+
+
+class di_plan_info(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("width", ctypes.c_int * 24),
+                ("height", ctypes.c_int * 24), ("blocks_x", ctypes.c_int * 24),
+                ("blocks_y", ctypes.c_int * 24), ("local_problems", ctypes.c_longlong),
+                ("workspace_bytes", ctypes.c_longlong)]
+
+
+class DiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_F = ctypes.c_float
+
+_SIGS = {
+    "di_plan": (_I, [ctypes.POINTER(di_config), _I, _I, _I, ctypes.POINTER(di_plan_info)]),
+    "di_create": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(_P)]),
+    "di_destroy": (None, [_P]),
+    "di_inpaint": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P]),
+    "di_get_stats": (_I, [_P, ctypes.POINTER(di_stats)]),
+    "di_status_string": (ctypes.c_char_p, [_I]),
+    "di_last_error": (ctypes.c_char_p, [_P]),
+    "di_mask_downsample": (_I, [_P, _I, _I, _P, _P]),
+    "di_values_downsample": (_I, [_P, _P, _I, _I, _I, _P, _P, _I, _P]),
+    "di_residual_norm": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
+    "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
+    "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
+    "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
+}
+
+
+def load():
+    """Load libdi.so (build it first with paper_2401_06744_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdi.so not built ({LIB_PATH}); run "
+                                   "python -m paper_2401_06744_gb300.build")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def status_string(st: int) -> str:
+    return load().di_status_string(st).decode()
+
+
+def _check(st: int, ctx=None):
+    if st != OK:
+        msg = status_string(st)
+        if ctx is not None and ctx._h:
+            extra = load().di_last_error(ctx._h).decode()
+            if extra:
+                msg += f" ({extra})"
+        raise DiError(st, msg)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _img(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous [C,H,W] or [H,W] tensor")
+    return t
+
+
+def _mask(t: torch.Tensor) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.uint8:
+        raise TypeError("mask must be a uint8 CUDA tensor")
+    if t.dim() != 2 or not t.is_contiguous():
+        raise ValueError("mask must be a contiguous [H,W] tensor")
+    return t
+
+
+def make_config(**kw) -> di_config:
+    cfg = di_config()
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def plan(width: int, height: int, channels: int, **config) -> dict:
+    """Level sizes, block counts and workspace bytes of a solve (host only)."""
+    cfg = make_config(**config)
+    out = di_plan_info()
+    _check(load().di_plan(ctypes.byref(cfg), int(width), int(height), int(channels),
+                          ctypes.byref(out)))
+    L = out.levels
+    return {"levels": L, "sizes": [(out.width[i], out.height[i]) for i in range(L)],
+            "blocks": [(out.blocks_x[i], out.blocks_y[i]) for i in range(L)],
+            "local_problems": out.local_problems, "workspace_bytes": out.workspace_bytes}
+
+
+class Context:
+    """A decoder context (di_create / di_destroy) with its device workspace."""
+
+    def __init__(self, device: int | None = None, **config):
+        lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        self.config = make_config(**config)
+        h = _P()
+        self._h = None
+        _check(lib.di_create(ctypes.byref(self.config), int(device), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            load().di_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the decoder -------------------------------------------------------
+    def inpaint(self, f: torch.Tensor, c: torch.Tensor, tol: float = 0.05,
+                out: torch.Tensor | None = None, stream=None, check: bool = True):
+        """u with (C + (I - C) L) u = C f per channel; returns (u, status)."""
+        f3 = _img(f, "f")
+        c = _mask(c)
+        C, H, W = f3.shape
+        if c.shape != (H, W):
+            raise ValueError("mask shape does not match f")
+        u = torch.empty_like(f3) if out is None else _img(out, "out")
+        st = load().di_inpaint(self._h, f3.data_ptr(), c.data_ptr(), W, H, C, float(tol),
+                               u.data_ptr(), _stream(stream))
+        if check and st not in (OK, NOT_CONVERGED):
+            _check(st, self)
+        res = u if f.dim() == 3 else u[0]
+        return res, st
+
+    def stats(self) -> dict:
+        s = di_stats()
+        _check(load().di_get_stats(self._h, ctypes.byref(s)), self)
+        return {"levels": s.levels, "levels_used": s.levels_used, "cycles": s.cycles,
+                "converged": bool(s.converged), "est_error": s.est_error,
+                "rel_residual": list(s.rel_residual), "unknowns": s.unknowns}
+
+    # -- single steps needing a context -----------------------------------
+    def residual_norm(self, u, b, c, rhs_zero=False, want_r=True, stream=None):
+        u3, b3, c = _img(u, "u"), _img(b, "b"), _mask(c)
+        C, H, W = u3.shape
+        r = torch.empty_like(u3) if want_r else None
+        n2 = torch.empty(C, dtype=torch.float64, device=u3.device)
+        st = load().di_residual_norm(self._h, u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
+                                     c.data_ptr(), W, H, C, r.data_ptr() if want_r else None,
+                                     n2.data_ptr(), _stream(stream))
+        _check(st, self)
+        return r, n2
+
+    def oras_iteration(self, u_in, b, c, local_iters, rhs_zero=False, out=None, stream=None):
+        u3, b3, c = _img(u_in, "u_in"), _img(b, "b"), _mask(c)
+        C, H, W = u3.shape
+        uo = torch.empty_like(u3) if out is None else _img(out, "out")
+        st = load().di_oras_iteration(self._h, u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
+                                      c.data_ptr(), W, H, C, int(local_iters), uo.data_ptr(),
+                                      _stream(stream))
+        _check(st, self)
+        return uo
+
+
+# -- single steps without a context -----------------------------------------
+
+def mask_downsample(c, stream=None):
+    c = _mask(c)
+    H, W = c.shape
+    cH = torch.empty(((H + 1) // 2, (W + 1) // 2), dtype=torch.uint8, device=c.device)
+    _check(load().di_mask_downsample(c.data_ptr(), W, H, cH.data_ptr(), _stream(stream)))
+    return cH
+
+
+def values_downsample(c, b, cH, modified=True, stream=None):
+    c, b3, cH = _mask(c), _img(b, "b"), _mask(cH)
+    C, H, W = b3.shape
+    bH = torch.empty((C, (H + 1) // 2, (W + 1) // 2), dtype=torch.float32, device=b3.device)
+    _check(load().di_values_downsample(c.data_ptr(), b3.data_ptr(), W, H, C, cH.data_ptr(),
+                                       bH.data_ptr(), int(bool(modified)), _stream(stream)))
+    return bH
+
+
+def restrict_residual(u, b, c, cH, rhs_zero=False, stream=None):
+    u3, b3, c, cH = _img(u, "u"), _img(b, "b"), _mask(c), _mask(cH)
+    C, H, W = u3.shape
+    rH = torch.empty((C, (H + 1) // 2, (W + 1) // 2), dtype=torch.float32, device=u3.device)
+    _check(load().di_restrict_residual(u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
+                                       c.data_ptr(), W, H, C, cH.data_ptr(), rH.data_ptr(),
+                                       _stream(stream)))
+    return rH
+
+
+def prolong(uH, c, mode, b=None, u=None, stream=None):
+    """mode 0: returns c ? b : P uH; mode 1: u += P uH off the mask (in place)."""
+    uH3, c = _img(uH, "uH"), _mask(c)
+    C = uH3.shape[0]
+    H, W = c.shape
+    if mode == 0:
+        b3 = _img(b, "b")
+        out = torch.empty((C, H, W), dtype=torch.float32, device=uH3.device)
+        bp = b3.data_ptr()
+    else:
+        out = _img(u, "u")
+        bp = None
+    _check(load().di_prolong(uH3.data_ptr(), bp, c.data_ptr(), W, H, C, out.data_ptr(),
+                             int(mode), _stream(stream)))
+    return out

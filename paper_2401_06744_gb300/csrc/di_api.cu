@@ -1,0 +1,610 @@
+// Host side of the decoder: context and device workspace, the reduced-FMG /
+// V-cycle scheduler (Sections 4.2 and 4.4) and the C ABI declared in di.h.
+//
+// Schedule of di_inpaint for an image with L levels (level 0 finest; the
+// coarsest fits one B x B block, Section 4.4):
+//   1. mask pyramid c_l (max pooling) with unknown-pixel counts per level, and
+//      the value pyramid b_l (modified downsampling), Section 4.3;
+//   2. the cascade (one-way multigrid, Section 4.2 "reduced FMG"): on the
+//      coarsest level u = b on the mask, 0 elsewhere, then one ORAS iteration
+//      (one block: a local solve of the whole level); on each finer level
+//      u = P u_coarse with u = b on the mask, then one ORAS iteration;
+//   3. V(pre, post)-cycles on the finest level (Algorithm 3 applied
+//      recursively), each followed by the stop test.
+// A level whose mask covers every pixel has an identically zero correction,
+// so recursion stops above the first such level and the cascade starts from
+// it (u = b there); this changes no arithmetic result.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <new>
+
+#include "../../include/di.h"
+#include "di_internal.h"
+
+using namespace di;
+
+namespace {
+
+struct Level {
+    int w = 0, h = 0;
+    size_t n = 0;
+    const uint8_t* c = nullptr;  // level 0: caller's mask
+    const float* b = nullptr;    // mask values (level 0: caller's f, read only on the mask)
+    float* u[2] = {nullptr, nullptr};
+    float* r = nullptr;          // restricted residual (right-hand side of the error equation)
+    long long unknowns = 0;
+};
+
+}  // namespace
+
+struct di_ctx {
+    di_config cfg;
+    int device = 0;
+    // workspace capacity
+    int cap_w = 0, cap_h = 0, cap_c = 0;
+    void* pool = nullptr;           // one allocation for every level buffer
+    float* planes = nullptr;        // 4 * C * n0 floats
+    double* partials = nullptr;     // residual norm partial sums
+    size_t partials_cap = 0;
+    double* norm2 = nullptr;        // [kMaxChannels]
+    unsigned long long* counts = nullptr;  // [kMaxLevels + 1]
+    unsigned* upd = nullptr;        // [kMaxUpdSlots] per-cycle max update (float bits)
+    void* host = nullptr;           // pinned staging for small device->host reads
+    Level lv[kMaxLevels];
+    int L = 0;
+    di_stats stats;
+    char err[256];
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+// The single-block solve of the coarsest level iterates until its
+// preconditioned residual r.z has dropped by this factor (relative residual
+// about 1e-6, near the FP32 floor), capped at coarse_iters steps.
+constexpr float kCoarseRtol2 = 1e-12f;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+di_config resolve(const di_config* in) {
+    di_config c;
+    std::memset(&c, 0, sizeof c);
+    if (in) c = *in;
+    if (c.block == 0) c.block = 32;
+    if (c.overlap == 0) c.overlap = 6;
+    if (c.local_iters == 0) c.local_iters = 8;
+    if (c.coarse_iters == 0) c.coarse_iters = 2048;
+    if (c.pre == 0) c.pre = 1;
+    if (c.post == 0) c.post = 1;
+    if (c.max_cycles == 0) c.max_cycles = 16;
+    if (c.min_cycles == 0) c.min_cycles = 1;
+    if (c.alpha == 0.f) c.alpha = 0.5f;
+    return c;
+}
+
+bool config_ok(const di_config& c) {
+    if (c.block != 8 && c.block != 16 && c.block != 32) return false;
+    if (c.overlap < 1 || 2 * c.overlap > c.block) return false;
+    if (c.local_iters < 0 || c.coarse_iters < 0) return false;
+    if (c.pre < 0 || c.post < 0 || c.pre + 1 + c.post > kMaxUpdSlots) return false;
+    if (c.max_cycles < 0 || c.min_cycles < 0 || c.min_cycles > c.max_cycles) return false;
+    if (!(c.alpha > 0.f) || !std::isfinite(c.alpha)) return false;
+    if (c.downsample != 0 && c.downsample != 1) return false;
+    if (c.stop_rule < 0 || c.stop_rule > 2) return false;
+    return true;
+}
+
+di_status cuda_fail(di_ctx* ctx, cudaError_t e, const char* what) {
+    if (ctx) std::snprintf(ctx->err, sizeof ctx->err, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? DI_ERR_OOM : DI_ERR_CUDA;
+}
+
+#define DI_CUDA(ctx, call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+void free_workspace(di_ctx* ctx) {
+    if (ctx->pool) cudaFree(ctx->pool);
+    if (ctx->planes) cudaFree(ctx->planes);
+    if (ctx->partials) cudaFree(ctx->partials);
+    ctx->pool = nullptr;
+    ctx->planes = nullptr;
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    ctx->cap_w = ctx->cap_h = ctx->cap_c = 0;
+}
+
+// Byte size of the pooled level buffers for an image of (w, h, C).
+size_t pool_bytes(int w, int h, int C, int L) {
+    size_t total = 0;
+    int lw = w, lh = h;
+    for (int l = 0; l < L; ++l) {
+        const size_t n = (size_t)lw * lh;
+        if (l == 0) {
+            total += align_up(n * C * sizeof(float));  // u[1]
+        } else {
+            total += align_up(n);                           // c
+            total += 4 * align_up(n * C * sizeof(float));  // b, u[0], u[1], r
+        }
+        coarse_dims(lw, lh, &lw, &lh);
+    }
+    return total;
+}
+
+// Make sure the workspace covers (w, h, C); grows to the elementwise maximum
+// of everything seen so far (level l of a smaller image is never larger).
+di_status ensure_workspace(di_ctx* ctx, int w, int h, int C) {
+    if (w <= ctx->cap_w && h <= ctx->cap_h && C <= ctx->cap_c) return DI_OK;
+    const int nw = w > ctx->cap_w ? w : ctx->cap_w;
+    const int nh = h > ctx->cap_h ? h : ctx->cap_h;
+    const int nc = C > ctx->cap_c ? C : ctx->cap_c;
+    free_workspace(ctx);
+    const int L = num_levels(nw, nh, ctx->cfg.block);
+    cudaError_t e = cudaMalloc(&ctx->pool, pool_bytes(nw, nh, nc, L));
+    if (e != cudaSuccess) { ctx->pool = nullptr; return cuda_fail(ctx, e, "cudaMalloc(pool)"); }
+    const size_t n0 = (size_t)nw * nh;
+    e = cudaMalloc(&ctx->planes, 4 * n0 * nc * sizeof(float));
+    if (e != cudaSuccess) { free_workspace(ctx); return cuda_fail(ctx, e, "cudaMalloc(planes)"); }
+    ctx->partials_cap = residual_partials_per_channel(nw, nh) * nc;
+    e = cudaMalloc(&ctx->partials, ctx->partials_cap * sizeof(double));
+    if (e != cudaSuccess) { free_workspace(ctx); return cuda_fail(ctx, e, "cudaMalloc(partials)"); }
+    ctx->cap_w = nw;
+    ctx->cap_h = nh;
+    ctx->cap_c = nc;
+    return DI_OK;
+}
+
+// Lay the pooled buffers out for this image.
+void bind_levels(di_ctx* ctx, const float* f, const uint8_t* c, float* u, int w, int h, int C) {
+    const int L = num_levels(w, h, ctx->cfg.block);
+    ctx->L = L;
+    char* p = static_cast<char*>(ctx->pool);
+    int lw = w, lh = h;
+    for (int l = 0; l < L; ++l) {
+        Level& v = ctx->lv[l];
+        v.w = lw;
+        v.h = lh;
+        v.n = (size_t)lw * lh;
+        const size_t fb = align_up(v.n * C * sizeof(float));
+        if (l == 0) {
+            v.c = c;
+            v.b = f;
+            v.u[0] = u;
+            v.u[1] = reinterpret_cast<float*>(p); p += fb;
+            v.r = nullptr;
+        } else {
+            v.c = reinterpret_cast<uint8_t*>(p); p += align_up(v.n);
+            v.b = reinterpret_cast<float*>(p); p += fb;
+            v.u[0] = reinterpret_cast<float*>(p); p += fb;
+            v.u[1] = reinterpret_cast<float*>(p); p += fb;
+            v.r = reinterpret_cast<float*>(p); p += fb;
+        }
+        v.unknowns = 0;
+        coarse_dims(lw, lh, &lw, &lh);
+    }
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Scheduler
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Sched {
+    di_ctx* ctx;
+    int C;
+    int Leff;   // levels that carry unknown pixels (recursion depth)
+    cudaStream_t s;
+    bool vcycle_phase = false;
+
+    // right-hand side of level l: level 0 solves A u = C f (the right-hand side
+    // is zero at unknown pixels); coarse levels in the cascade solve
+    // A u = b_l (zero off the mask) and in the V-cycles A e = r_l.
+    di_status run_oras(int l, const float* in, int zero_in, float* out, int iters,
+                       unsigned* maxupd, float rtol2 = 0.f) {
+        const Level& v = ctx->lv[l];
+        const float* rhs;
+        int rhs_zero;
+        if (l == 0) { rhs = v.b; rhs_zero = 1; }
+        else if (vcycle_phase) { rhs = v.r; rhs_zero = 0; }
+        else { rhs = v.b; rhs_zero = 1; }
+        DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.c, v.w, v.h, C, ctx->cfg.block,
+                                 ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
+                                 ctx->planes, maxupd, s));
+        return DI_OK;
+    }
+
+    // V-cycle on level l.  The iterate starts in lv[l].u[0] (or is zero) and
+    // ends in lv[l].u[*which].  upd: per-step max-update slots (level 0 only).
+    di_status vcycle(int l, bool zero_init, int* which, unsigned* upd) {
+        const di_config& cfg = ctx->cfg;
+        Level& v = ctx->lv[l];
+        const bool coarsest = (l == ctx->L - 1);
+        int cur = 0;
+        di_status st;
+        if (coarsest) {
+            // one block covers the level: one ORAS iteration is a local solve
+            st = run_oras(l, v.u[0], zero_init ? 1 : 0, v.u[1], cfg.coarse_iters,
+                          upd ? &upd[0] : nullptr, kCoarseRtol2);
+            if (st) return st;
+            *which = 1;
+            return DI_OK;
+        }
+        int slot = 0;
+        bool zero = zero_init;
+        for (int k = 0; k < cfg.pre; ++k) {
+            st = run_oras(l, v.u[cur], zero ? 1 : 0, v.u[cur ^ 1], cfg.local_iters,
+                          upd ? &upd[slot] : nullptr);
+            if (st) return st;
+            ++slot;
+            cur ^= 1;
+            zero = false;
+        }
+        if (zero) {  // pre = 0 on a zero start: materialise the zero iterate
+            DI_CUDA(ctx, cudaMemsetAsync(v.u[cur], 0, v.n * C * sizeof(float), s));
+            zero = false;
+        }
+        if (l + 1 < Leff) {
+            Level& cv = ctx->lv[l + 1];
+            const float* rhs = l == 0 ? v.b : v.r;
+            DI_CUDA(ctx, launch_restrict(v.u[cur], rhs, l == 0 ? 1 : 0, v.c, v.w, v.h, C, cv.c,
+                                         cv.r, s));
+            int cw = 0;
+            st = vcycle(l + 1, true, &cw, nullptr);
+            if (st) return st;
+            DI_CUDA(ctx, launch_prolong(cv.u[cw], nullptr, v.c, v.w, v.h, C, v.u[cur], 1,
+                                        upd ? &upd[slot] : nullptr, s));
+        }
+        ++slot;
+        for (int k = 0; k < cfg.post; ++k) {
+            st = run_oras(l, v.u[cur], 0, v.u[cur ^ 1], cfg.local_iters,
+                          upd ? &upd[slot] : nullptr);
+            if (st) return st;
+            ++slot;
+            cur ^= 1;
+        }
+        *which = cur;
+        return DI_OK;
+    }
+};
+
+float bits_to_float(unsigned b) {
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+di_status di_plan(const di_config* cfg, int width, int height, int channels,
+                  di_plan_info* out) {
+    if (!out || width < 1 || height < 1 || channels < 1 || channels > kMaxChannels)
+        return DI_ERR_INVALID_ARG;
+    di_config c = resolve(cfg);
+    if (!config_ok(c)) return DI_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof *out);
+    const int L = num_levels(width, height, c.block);
+    if (L > kMaxLevels) return DI_ERR_INVALID_ARG;
+    out->levels = L;
+    int lw = width, lh = height;
+    for (int l = 0; l < L; ++l) {
+        out->width[l] = lw;
+        out->height[l] = lh;
+        out->blocks_x[l] = axis_blocks(lw, c.block, c.overlap);
+        out->blocks_y[l] = axis_blocks(lh, c.block, c.overlap);
+        coarse_dims(lw, lh, &lw, &lh);
+    }
+    out->local_problems = (long long)out->blocks_x[0] * out->blocks_y[0] * channels;
+    const size_t n0 = (size_t)width * height;
+    out->workspace_bytes = (long long)(pool_bytes(width, height, channels, L) +
+                                       4 * n0 * channels * sizeof(float) +
+                                       residual_partials_per_channel(width, height) * channels *
+                                           sizeof(double));
+    return DI_OK;
+}
+
+di_status di_create(const di_config* cfg, int device, di_ctx** out) {
+    if (!out) return DI_ERR_INVALID_ARG;
+    *out = nullptr;
+    di_config c = resolve(cfg);
+    if (!config_ok(c)) return DI_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return DI_ERR_INVALID_ARG;
+    di_ctx* ctx = new (std::nothrow) di_ctx();
+    if (!ctx) return DI_ERR_OOM;
+    ctx->cfg = c;
+    ctx->device = device;
+    std::memset(&ctx->stats, 0, sizeof ctx->stats);
+    ctx->err[0] = 0;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->norm2, kMaxChannels * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->counts, (kMaxLevels + 1) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->upd, kMaxUpdSlots * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->host, 4096);
+    if (e != cudaSuccess) {
+        di_status st = cuda_fail(ctx, e, "di_create");
+        di_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return DI_OK;
+}
+
+void di_destroy(di_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_workspace(ctx);
+    if (ctx->norm2) cudaFree(ctx->norm2);
+    if (ctx->counts) cudaFree(ctx->counts);
+    if (ctx->upd) cudaFree(ctx->upd);
+    if (ctx->host) cudaFreeHost(ctx->host);
+    delete ctx;
+}
+
+const char* di_status_string(di_status s) {
+    switch (s) {
+        case DI_OK: return "ok";
+        case DI_ERR_INVALID_ARG: return "invalid argument";
+        case DI_ERR_EMPTY_MASK: return "empty mask";
+        case DI_ERR_OOM: return "out of device memory";
+        case DI_ERR_NOT_CONVERGED: return "not converged";
+        case DI_ERR_CUDA: return "CUDA error";
+        case DI_ERR_TIMEOUT: return "timeout";
+    }
+    return "unknown status";
+}
+
+const char* di_last_error(const di_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+di_status di_get_stats(const di_ctx* ctx, di_stats* out) {
+    if (!ctx || !out) return DI_ERR_INVALID_ARG;
+    *out = ctx->stats;
+    return DI_OK;
+}
+
+di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, int height,
+                     int channels, float tol, float* u, void* stream) {
+    if (!ctx || !f || !c || !u || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels || !(tol > 0.f) || !std::isfinite(tol))
+        return DI_ERR_INVALID_ARG;
+    const size_t n0 = (size_t)width * height;
+    const size_t img_bytes = n0 * channels * sizeof(float);
+    if (overlaps(f, img_bytes, u, img_bytes) || overlaps(c, n0, u, img_bytes))
+        return DI_ERR_INVALID_ARG;
+    if (num_levels(width, height, ctx->cfg.block) > kMaxLevels - 1) return DI_ERR_INVALID_ARG;
+    std::memset(&ctx->stats, 0, sizeof ctx->stats);
+    for (int k = 0; k < 4; ++k) ctx->stats.rel_residual[k] = -1.f;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DI_CUDA(ctx, cudaSetDevice(ctx->device));
+    di_status st = ensure_workspace(ctx, width, height, channels);
+    if (st) return st;
+    bind_levels(ctx, f, c, u, width, height, channels);
+    const di_config& cfg = ctx->cfg;
+    const int L = ctx->L;
+    const int C = channels;
+
+    // 1. pyramids and unknown counts
+    unsigned long long* cnt = ctx->counts;
+    DI_CUDA(ctx, cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s));
+    DI_CUDA(ctx, launch_count_mask(c, n0, cnt, s));  // cnt[0] known, cnt[1] unknown (level 0)
+    for (int l = 1; l < L; ++l) {
+        Level& f_ = ctx->lv[l - 1];
+        Level& cv = ctx->lv[l];
+        DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), cnt + 1 + l, s));
+        DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
+                                        const_cast<float*>(cv.b), cfg.downsample == 0 ? 1 : 0, s));
+    }
+    unsigned long long* hcnt = static_cast<unsigned long long*>(ctx->host);
+    DI_CUDA(ctx, cudaMemcpyAsync(hcnt, cnt, (L + 1) * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+    DI_CUDA(ctx, cudaStreamSynchronize(s));
+    if (hcnt[0] == 0) return DI_ERR_EMPTY_MASK;
+    ctx->lv[0].unknowns = (long long)hcnt[1];
+    int Leff = L;
+    for (int l = 1; l < L; ++l) {
+        ctx->lv[l].unknowns = (long long)hcnt[1 + l];
+        if (ctx->lv[l].unknowns == 0) { Leff = l; break; }
+    }
+    if (ctx->lv[0].unknowns == 0) Leff = 0;
+    ctx->stats.levels = L;
+    ctx->stats.levels_used = Leff;
+    ctx->stats.unknowns = ctx->lv[0].unknowns;
+
+    if (Leff == 0) {  // every pixel is known
+        DI_CUDA(ctx, launch_select(f, c, width, height, C, u, s));
+        DI_CUDA(ctx, cudaStreamSynchronize(s));
+        ctx->stats.converged = 1;
+        return DI_OK;
+    }
+
+    Sched S{ctx, C, Leff, s};
+    // 2. cascade
+    int top;
+    if (Leff == L) {
+        top = L - 1;
+        Level& v = ctx->lv[top];
+        DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s));
+        st = S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2);
+        if (st) return st;
+    } else {
+        top = Leff;  // fully known level: u = b there
+        Level& v = ctx->lv[top];
+        DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s));
+    }
+    for (int l = top - 1; l >= 0; --l) {
+        Level& v = ctx->lv[l];
+        Level& cv = ctx->lv[l + 1];
+        DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s));
+        st = S.run_oras(l, v.u[1], 0, v.u[0], cfg.local_iters, nullptr);
+        if (st) return st;
+    }
+
+    // 3. V-cycles with the stop test
+    S.vcycle_phase = true;
+    Level& v0 = ctx->lv[0];
+    const int nslots = cfg.pre + 1 + cfg.post;
+    float prevU = -1.f, prevQ = -1.f;
+    int cycles = 0;
+    bool converged = false;
+    float est = INFINITY;
+    float* hupd = static_cast<float*>(ctx->host);
+    double* hnorm = reinterpret_cast<double*>(static_cast<char*>(ctx->host) + 256);
+    double bnorm2[kMaxChannels] = {0, 0, 0, 0};
+    int nparts = 0;
+    if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL) {
+        DI_CUDA(ctx, launch_residual(nullptr, 1, f, 1, c, width, height, C, nullptr,
+                                     ctx->partials, &nparts, s));
+        DI_CUDA(ctx, launch_reduce_partials(ctx->partials, nparts, C, ctx->norm2, s));
+        DI_CUDA(ctx, cudaMemcpyAsync(hnorm, ctx->norm2, C * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(ctx, cudaStreamSynchronize(s));
+        for (int k = 0; k < C; ++k) bnorm2[k] = hnorm[k];
+    }
+    while (cycles < cfg.max_cycles) {
+        DI_CUDA(ctx, cudaMemsetAsync(ctx->upd, 0, kMaxUpdSlots * sizeof(unsigned), s));
+        int which = 0;
+        // The iterate lives in v0.u[0] (the caller's buffer) between cycles.
+        st = S.vcycle(0, false, &which, ctx->upd);
+        if (st) return st;
+        if (which != 0)
+            DI_CUDA(ctx, cudaMemcpyAsync(v0.u[0], v0.u[1], v0.n * C * sizeof(float),
+                                         cudaMemcpyDeviceToDevice, s));
+        ++cycles;
+        if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) continue;
+        if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE) {
+            DI_CUDA(ctx, cudaMemcpyAsync(hupd, ctx->upd, nslots * sizeof(unsigned),
+                                         cudaMemcpyDeviceToHost, s));
+            DI_CUDA(ctx, cudaStreamSynchronize(s));
+            float U = 0.f;
+            for (int k = 0; k < nslots; ++k) U += bits_to_float(reinterpret_cast<unsigned*>(hupd)[k]);
+            if (!std::isfinite(U)) { est = INFINITY; prevU = -1.f; prevQ = -1.f; }
+            else if (prevU > 0.f) {
+                // decay factor: the larger of the last two measured ratios
+                const float qk = U / prevU;
+                const float q = prevQ > qk ? prevQ : qk;
+                prevQ = qk;
+                est = q < 1.f ? U * q / (1.f - q) : INFINITY;
+            } else {
+                est = U;  // first cycle: no decay measured yet (factor 1/2 assumed)
+            }
+            prevU = U;
+            if (U == 0.f) est = 0.f;
+            ctx->stats.est_error = est;
+            if (cycles >= cfg.min_cycles && est <= 0.5f * tol) { converged = true; break; }
+        } else {
+            DI_CUDA(ctx, launch_residual(v0.u[0], 0, f, 1, c, width, height, C, nullptr,
+                                         ctx->partials, &nparts, s));
+            DI_CUDA(ctx, launch_reduce_partials(ctx->partials, nparts, C, ctx->norm2, s));
+            DI_CUDA(ctx, cudaMemcpyAsync(hnorm, ctx->norm2, C * sizeof(double),
+                                         cudaMemcpyDeviceToHost, s));
+            DI_CUDA(ctx, cudaStreamSynchronize(s));
+            bool ok = true;
+            for (int k = 0; k < C; ++k) {
+                const double rr = bnorm2[k] > 0 ? std::sqrt(hnorm[k] / bnorm2[k]) : 0.0;
+                ctx->stats.rel_residual[k] = (float)rr;
+                if (!(rr <= tol)) ok = false;
+            }
+            if (cycles >= cfg.min_cycles && ok) { converged = true; break; }
+        }
+    }
+    if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) {
+        DI_CUDA(ctx, cudaStreamSynchronize(s));
+        converged = true;
+    }
+    ctx->stats.cycles = cycles;
+    ctx->stats.converged = converged ? 1 : 0;
+    return converged ? DI_OK : DI_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// Single steps
+// ---------------------------------------------------------------------------
+
+di_status di_mask_downsample(const uint8_t* c, int width, int height, uint8_t* cH,
+                             void* stream) {
+    if (!c || !cH || width < 1 || height < 1) return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_mask_down(c, width, height, cH, nullptr, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
+di_status di_values_downsample(const uint8_t* c, const float* b, int width, int height,
+                               int channels, const uint8_t* cH, float* bH, int modified,
+                               void* stream) {
+    if (!c || !b || !cH || !bH || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels || (modified != 0 && modified != 1))
+        return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_values_down(c, b, width, height, channels, cH, bH, modified,
+                                       static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
+di_status di_residual_norm(di_ctx* ctx, const float* u, const float* b, int rhs_zero,
+                           const uint8_t* c, int width, int height, int channels, float* r,
+                           double* norm2, void* stream) {
+    if (!ctx || !u || !b || !c || !norm2 || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels)
+        return DI_ERR_INVALID_ARG;
+    DI_CUDA(ctx, cudaSetDevice(ctx->device));
+    di_status st = ensure_workspace(ctx, width, height, channels);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int nparts = 0;
+    DI_CUDA(ctx, launch_residual(u, 0, b, rhs_zero ? 1 : 0, c, width, height, channels, r,
+                                 ctx->partials, &nparts, s));
+    DI_CUDA(ctx, launch_reduce_partials(ctx->partials, nparts, channels, norm2, s));
+    return DI_OK;
+}
+
+di_status di_restrict_residual(const float* u, const float* b, int rhs_zero, const uint8_t* c,
+                               int width, int height, int channels, const uint8_t* cH,
+                               float* rH, void* stream) {
+    if (!u || !b || !c || !cH || !rH || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels)
+        return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_restrict(u, b, rhs_zero ? 1 : 0, c, width, height, channels, cH, rH,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
+di_status di_prolong(const float* uH, const float* b, const uint8_t* c, int width, int height,
+                     int channels, float* u, int mode, void* stream) {
+    if (!uH || !c || !u || width < 1 || height < 1 || channels < 1 || channels > kMaxChannels ||
+        (mode != 0 && mode != 1) || (mode == 0 && !b))
+        return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_prolong(uH, b, c, width, height, channels, u, mode, nullptr,
+                                   static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
+di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int rhs_zero,
+                            const uint8_t* c, int width, int height, int channels,
+                            int local_iters, float* u_out, void* stream) {
+    if (!ctx || !u_in || !b || !c || !u_out || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels || local_iters < 0)
+        return DI_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)width * height * channels * sizeof(float);
+    if (overlaps(u_in, bytes, u_out, bytes)) return DI_ERR_INVALID_ARG;
+    DI_CUDA(ctx, cudaSetDevice(ctx->device));
+    di_status st = ensure_workspace(ctx, width, height, channels);
+    if (st) return st;
+    DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, c, width, height, channels,
+                             ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
+                             u_out, ctx->planes, nullptr, static_cast<cudaStream_t>(stream)));
+    return DI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Launch wrappers shared between the kernel translation unit and the host
+// scheduler.  All pointers are device pointers; images are planar
+// [C][h][w] float32, masks [h][w] uint8.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace di {
+
+constexpr int kMaxChannels = 4;
+constexpr int kMaxLevels = 24;
+constexpr int kMaxUpdSlots = 16;
+
+// Count known (nonzero) and unknown pixels of a mask: out[0] += known,
+// out[1] += unknown.  out must be zeroed by the caller.
+cudaError_t launch_count_mask(const uint8_t* c, size_t n, unsigned long long* out,
+                              cudaStream_t s);
+
+// cH = 2x2 max pool of c; *unknownH += number of zero entries of cH (nullable).
+cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH,
+                             unsigned long long* unknownH, cudaStream_t s);
+
+// bH from (c, b, cH): modified (1) or naive (0) mask-value downsampling.
+cudaError_t launch_values_down(const uint8_t* c, const float* b, int w, int h, int C,
+                               const uint8_t* cH, float* bH, int modified, cudaStream_t s);
+
+// r = b - A u (r may be null) and per-CTA partial sums of r^2 into
+// partials[ch * nparts + cta]; returns nparts through *nparts.
+cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_zero,
+                            const uint8_t* c, int w, int h, int C, float* r, double* partials,
+                            int* nparts, cudaStream_t s);
+size_t residual_partials_per_channel(int w, int h);
+
+// out[ch] = sum of partials[ch * nparts + i] in a fixed order.
+cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, double* out,
+                                   cudaStream_t s);
+
+// rH = 4 * mean over children of (b - A u) where cH == 0, else 0.
+cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const uint8_t* c,
+                            int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s);
+
+// mode 0: u = c ? b : P uH.  mode 1: u += c ? 0 : P uH, max |P uH| (unknown
+// pixels) folded into *maxupd (as float bits, nullable).
+cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, int w, int h,
+                           int C, float* u, int mode, unsigned* maxupd, cudaStream_t s);
+
+// u = c ? b : 0.
+cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
+                          cudaStream_t s);
+
+// One ORAS iteration u_in -> u_out (planes: 4*C*w*h floats of workspace).
+// Each local PCG runs `iters` steps or until r.z <= rtol2 * (r.z)_0.
+// max |v_i| over pixels with nonzero weight folded into *maxupd (nullable).
+cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
+                        const uint8_t* c, int w, int h, int C, int B, int o, float alpha,
+                        int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
+                        cudaStream_t s);
+
+// Host-side geometry shared with the kernels.
+inline int axis_blocks(int n, int B, int o) {
+    const int s = B - o;
+    int nb = (n - o + s - 1) / s;
+    return nb < 1 ? 1 : nb;
+}
+inline void coarse_dims(int w, int h, int* wH, int* hH) {
+    *wH = (w + 1) / 2;
+    *hH = (h + 1) / 2;
+}
+inline int num_levels(int w, int h, int B) {
+    int n = 1;
+    while ((w > h ? w : h) > B) {
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+        ++n;
+    }
+    return n;
+}
+
+}  // namespace di

@@ -1,0 +1,188 @@
+"""GPU parity of each step of the path against the oracle's restatement of
+the same step (oracle.method), through the C ABI.
+
+Tolerances: integer/mask work is bit-exact.  Floating-point steps compute in
+FP32 against an FP64 oracle on values of at most 255 gray; a single FP32
+operation on such values carries an error of about 255 * 2^-24 = 1.5e-5, so
+stencil-sized expressions are compared at 2e-4 (absolute) and the ORAS
+iteration, whose local PCG amplifies rounding over its steps, at 1e-3 of the
+largest correction plus 2e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import method as M
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def di():
+    from paper_2401_06744_gb300 import build as b
+
+    b.build()
+    import paper_2401_06744_gb300 as di
+
+    di.load()
+    return di
+
+
+def T(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def N(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _case(h, w, C, d, seed, nan=True):
+    g = np.random.default_rng(seed)
+    f = g.uniform(0, 255, size=(C, h, w)).astype(np.float32)
+    c = (g.random((h, w)) < d).astype(np.uint8)
+    if not c.any():
+        c[g.integers(h), g.integers(w)] = 1
+    fn = f.copy()
+    if nan:
+        fn[:, c == 0] = np.nan  # never read at unknown pixels
+    return f, fn, c
+
+
+SIZES = [(1, 1), (1, 9), (7, 1), (3, 5), (17, 33), (64, 64), (101, 67), (130, 257)]
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+def test_mask_downsample_bit_exact(di, h, w):
+    _, _, c = _case(h, w, 1, 0.15, h * 7 + w)
+    cH = di.mask_downsample(T(c))
+    assert np.array_equal(N(cH), M.mask_downsample(c))
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+@pytest.mark.parametrize("modified", [True, False])
+def test_values_downsample(di, h, w, modified):
+    f, fn, c = _case(h, w, 3, 0.3, h * 11 + w)
+    cH = M.mask_downsample(c)
+    out = N(di.values_downsample(T(c), T(fn), T(cH), modified=modified))
+    ref = (M.values_downsample_modified(c, f, cH) if modified
+           else M.values_downsample_naive(c, f))
+    assert np.isfinite(out).all()
+    assert np.abs(out - ref).max() < 2e-4
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+def test_residual_and_norm(di, h, w):
+    f, fn, c = _case(h, w, 2, 0.1, h * 13 + w)
+    g = np.random.default_rng(5)
+    u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+    with di.Context() as ctx:
+        # b = C f (values off the mask never read) ...
+        r, n2 = ctx.residual_norm(T(u), T(fn), T(c), rhs_zero=True)
+        ref = M.residual(u, M.rhs(f, c), c)
+        assert np.abs(N(r) - ref).max() < 2e-4
+        assert np.allclose(N(n2), (ref ** 2).sum(axis=(1, 2)), rtol=1e-5, atol=1e-6)
+        # ... and a general right-hand side at unknown pixels
+        b = np.where(c.astype(bool), f, g.normal(size=f.shape)).astype(np.float32)
+        r, n2 = ctx.residual_norm(T(u), T(b), T(c), rhs_zero=False)
+        ref = M.residual(u, b, c)
+        assert np.abs(N(r) - ref).max() < 2e-4
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+def test_restrict_residual(di, h, w):
+    f, fn, c = _case(h, w, 2, 0.05, h * 17 + w)
+    g = np.random.default_rng(6)
+    u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+    cH = M.mask_downsample(c)
+    rH = N(di.restrict_residual(T(u), T(fn), T(c), T(cH), rhs_zero=True))
+    ref = M.restrict_residual(M.residual(u, M.rhs(f, c), c), cH)
+    assert np.abs(rH - ref).max() < 1e-3
+    b = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+    u2 = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+    rH = N(di.restrict_residual(T(u2), T(b), T(c), T(cH), rhs_zero=False))
+    ref = M.restrict_residual(M.residual(u2, b, c), cH)
+    assert np.abs(rH - ref).max() < 1e-4
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+def test_prolong_both_modes(di, h, w):
+    f, fn, c = _case(h, w, 2, 0.2, h * 19 + w)
+    H, W = M.coarse_shape(h, w)
+    g = np.random.default_rng(7)
+    uH = g.uniform(0, 255, (2, H, W)).astype(np.float32)
+    out = N(di.prolong(T(uH), T(c), 0, b=T(fn)))
+    ref = M.prolong_solution(uH, f, c)
+    assert np.abs(out - ref).max() < 1e-4
+    assert np.array_equal(out[:, c == 1], f[:, c == 1])  # mask values exact
+    u = g.uniform(0, 255, (2, h, w)).astype(np.float32)
+    ut = T(u)
+    di.prolong(T(uH), T(c), 1, u=ut)
+    ref = M.prolong_correct(u, uH, c)
+    out = N(ut)
+    assert np.abs(out - ref).max() < 1e-4
+    assert np.array_equal(out[:, c == 1], u[:, c == 1])
+
+
+ORAS_CASES = [  # (h, w, block, overlap, iters)
+    (32, 32, 32, 6, 8), (70, 95, 32, 6, 8), (77, 61, 16, 4, 6), (61, 77, 16, 2, 5),
+    (45, 38, 8, 2, 4), (45, 38, 8, 4, 3), (40, 41, 8, 1, 4), (50, 33, 16, 1, 2),
+    (130, 100, 32, 6, 0), (130, 100, 32, 6, 1), (9, 120, 32, 6, 8), (120, 9, 16, 4, 8),
+]
+
+
+@pytest.mark.parametrize("h,w,B,o,K", ORAS_CASES)
+def test_oras_iteration_matches_oracle_pcg(di, h, w, B, o, K):
+    f, fn, c = _case(h, w, 2, 0.06, h * 23 + w + B)
+    g = np.random.default_rng(8)
+    # an iterate that equals b on the mask (cascadic form, b = C f) ...
+    u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+    with di.Context(block=B, overlap=o, alpha=0.5) as ctx:
+        out = N(ctx.oras_iteration(T(u), T(fn), T(c), K, rhs_zero=True))
+        ref = M.oras_iteration(u, M.rhs(f, c), c, B, o, 0.5, ("pcg", K))
+        scale = np.abs(ref - u).max()
+        assert np.abs(out - ref).max() < 1e-3 * scale + 2e-4
+        assert np.array_equal(out[:, c == 1], u[:, c == 1])
+        # ... and the correction form (zero on the mask, general right-hand side)
+        b = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+        e = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+        out = N(ctx.oras_iteration(T(e), T(b), T(c), K, rhs_zero=False))
+        ref = M.oras_iteration(e, b, c, B, o, 0.5, ("pcg", K))
+        scale = np.abs(ref - e).max()
+        assert np.abs(out - ref).max() < 1e-3 * scale + 1e-5
+
+
+@pytest.mark.parametrize("B,o", [(32, 6), (16, 4), (8, 2)])
+def test_oras_converged_local_solves_match_exact(di, B, o):
+    # with enough local PCG steps each block solve is exact: compare with the
+    # oracle's direct local solves (Algorithm 2 as printed)
+    f, fn, c = _case(48, 53, 1, 0.08, 99 + B)
+    g = np.random.default_rng(9)
+    u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+    with di.Context(block=B, overlap=o) as ctx:
+        out = N(ctx.oras_iteration(T(u), T(fn), T(c), 3 * B * B, rhs_zero=True))
+    ref = M.oras_iteration(u, M.rhs(f, c), c, B, o, 0.5, "exact")
+    assert np.abs(out - ref).max() < 2e-3
+
+
+def test_oras_is_deterministic(di):
+    f, fn, c = _case(300, 257, 3, 0.05, 5)
+    u = np.where(c.astype(bool), f, 100.0).astype(np.float32)
+    with di.Context() as ctx:
+        a = N(ctx.oras_iteration(T(u), T(fn), T(c), 8, rhs_zero=True))
+        b = N(ctx.oras_iteration(T(u), T(fn), T(c), 8, rhs_zero=True))
+    assert np.array_equal(a, b)
+
+
+def test_oras_rejects_aliasing(di):
+    f, fn, c = _case(40, 40, 1, 0.1, 1)
+    with di.Context() as ctx:
+        ut = T(f)
+        with pytest.raises(di.DiError):
+            ctx.oras_iteration(ut, T(fn), T(c), 4, rhs_zero=True, out=ut)
