@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 inpainting decoder: 3840x2160 RGB frames per second
+at a 0.05 gray-level error target.
+
+Workload: six seeded synthetic 4K RGB frames (sinusoids + disks, Section 5
+sizes; masks of 10 %, 4 % and 1 % density, edge-clustered and uniform),
+resident in HBM and decoded in rotation, one frame per step, with the error
+estimate stop rule at tol = 0.05 gray.  The six frames (650 MB of inputs)
+exceed the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank decodes its own frames on its own GPU (the
+path shards by frame, no collective on the data path); rank 0 prints one JSON
+line with the whole-job frames/s over the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (conjugate gradients on the
+reduced system) on the machine's host cores instead, each step one bounded crop of
+the same frames, scaled to frames/s by pixel-channels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "4K RGB inpainting frames/s at ≤0.05 gray err; p50/p99 latency; HBM GB/s"
+UNIT = "frames/s"
+W4K, H4K, C4K = 3840, 2160, 3
+TOL = 0.05
+CASES = [(0.10, "edge"), (0.04, "edge"), (0.01, "edge"),
+         (0.10, "uniform"), (0.04, "uniform"), (0.01, "uniform")]
+BASE_SEED = 20240112
+# Local CG flops per pixel-channel and step of the ORAS block kernel (stencil
+# 6, p.Ap 2, x update 2, r update 2, r.r 2, p update 2) and per launch outside
+# the loop (residual 8, weighted output 3).
+FLOP_PER_STEP = 16
+FLOP_PER_LAUNCH = 11
+# FP32 FMA issue peak from unit counts and the maximum SM clock:
+# 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the finest-level ORAS block kernel (ncu, 4K RGB,
+# the same launch as in the bench; see profiles/); None once the kernel changes.
+ORAS_TRAFFIC_BYTES = None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _case_seed(i: int) -> int:
+    return BASE_SEED + 1000 * i
+
+
+def _make_cases():
+    import synth
+
+    return [synth.make_case(W4K, H4K, C4K, d, kind, _case_seed(i))
+            for i, (d, kind) in enumerate(CASES)]
+
+
+def _cpu_sample(f, c, w, h):
+    """A centred single-channel crop of one frame: the bounded CPU sample."""
+    H, W = c.shape
+    y0, x0 = (H - h) // 2, (W - w) // 2
+    fs = f[:1, y0:y0 + h, x0:x0 + w].copy()
+    cs = c[y0:y0 + h, x0:x0 + w].copy()
+    if not cs.any():
+        cs[h // 2, w // 2] = 1
+    return fs, cs
+
+
+def _run_oracle_timed(fs, cs):
+    import oracle
+
+    t = time.perf_counter()
+    u = oracle.cg_inpaint(fs, cs, rel_tol=1e-12)
+    return u, time.perf_counter() - t
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id(torch, dev: int) -> str | None:
+    try:
+        uuid = torch.cuda.get_device_properties(dev).uuid
+        s = str(uuid)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2401_06744_gb300 import build as _build
+
+    _build.build()
+    import paper_2401_06744_gb300 as di
+
+    cases = _make_cases()
+    f_dev = [torch.from_numpy(f).to(dev) for f, _ in cases]
+    c_dev = [torch.from_numpy(c).to(dev) for _, c in cases]
+    u_dev = torch.empty_like(f_dev[0])
+    ctx = di.Context(device=local, profile=1)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        k = i % len(cases)
+        _, st = ctx.inpaint(f_dev[k], c_dev[k], tol=TOL, out=u_dev)
+        if st != di.OK:
+            raise RuntimeError(f"frame {k}: {di.status_string(st)} {ctx.stats()}")
+        return ctx.stats()["cycles"]
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+
+    # --- timed region: device-resident inputs -------------------------------
+    sampler = ClockSampler(_gpu_id(torch, local)) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cycles = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ctx.reset_profile()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        cycles.append(step(args.warmup + i))
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    prof = ctx.profile()
+    clocks = sampler.stop() if sampler else None
+    elapsed_ms = t_start.elapsed_time(t_end)
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    frames_total = args.steps * ws
+    value = frames_total / (elapsed_ms / 1e3)
+
+    # --- end to end: host buffers, copies inside the timed region -----------
+    e2e_steps = max(3, min(args.steps, 12))
+    f_host = [torch.from_numpy(f).pin_memory() for f, _ in cases]
+    c_host = [torch.from_numpy(c).pin_memory() for _, c in cases]
+    u_host = torch.empty(f_host[0].shape, dtype=torch.float32).pin_memory()
+    f_buf = torch.empty_like(f_dev[0])
+    c_buf = torch.empty_like(c_dev[0])
+
+    def e2e_step(i):
+        k = i % len(cases)
+        f_buf.copy_(f_host[k], non_blocking=True)
+        c_buf.copy_(c_host[k], non_blocking=True)
+        _, st = ctx.inpaint(f_buf, c_buf, tol=TOL, out=u_dev)
+        if st != di.OK:
+            raise RuntimeError(di.status_string(st))
+        u_host.copy_(u_dev, non_blocking=True)
+
+    e2e_step(0)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = f_host[0].numel() * 4 + c_host[0].numel()
+    d2h = u_host.numel() * 4
+
+    if rank != 0:
+        ctx.close()
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    # --- roofline of the dominant kernel (finest-level ORAS block kernel) -----
+    n_l = max(1, prof["oras_l0_launches"])
+    avg_ms = prof["oras_l0_ms"] / n_l
+    pxch = prof["oras_l0_pixel_channels"] / n_l
+    steps_per = prof["oras_l0_cg_steps"] / n_l
+    flop = (FLOP_PER_STEP * steps_per + FLOP_PER_LAUNCH) * pxch
+    achieved = flop / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_oras_warp<32> (finest level)",
+                "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": ORAS_TRAFFIC_BYTES, "avg_launch_us": round(avg_ms * 1e3, 1),
+                "launches": prof["oras_l0_launches"],
+                "peak_note": "FP32 FMA issue rate from unit counts x max clock (no measured "
+                             "FP32 figure in the peak file)",
+                "algorithmic_bytes_per_launch": int(8 * pxch),
+                "achieved_hbm_gbs_algorithmic": round(8 * pxch / (avg_ms / 1e3) / 1e9, 1)}
+    # whole-frame bytes model: N C (46 + 83 k) bytes for k V-cycles
+    mean_cycles = sum(cycles) / len(cycles)
+    model_bytes = W4K * H4K * C4K * (46 + 83 * mean_cycles)
+    hbm_model_gbs = model_bytes * value / ws / 1e9
+
+    # --- CPU baseline: the oracle on a bounded sample (and a parity check) ----
+    cpu = None
+    accuracy = None
+    if ws == 1 and not args.skip_cpu:
+        # the oracle on one whole frame of the workload (all three channels)
+        f0, c0 = cases[1]
+        u_ref, t_cpu = _run_oracle_timed(f0, c0)
+        cpu = {"value": round(1.0 / t_cpu, 6), "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "FP64 CG (OpenMP over rows) to rel. residual 1e-12 on one whole "
+                         f"frame (the 4% edge-clustered 4K RGB case), {t_cpu:.1f} s"}
+        u_gpu, st = ctx.inpaint(f_dev[1], c_dev[1], tol=TOL)
+        torch.cuda.synchronize(dev)
+        err = np.abs(u_gpu.cpu().numpy().astype(np.float64) - u_ref)
+        accuracy = {"sample": "that frame, GPU vs oracle", "max_abs": float(err.max()),
+                    "rms": float(np.sqrt((err ** 2).mean())), "status": di.status_string(st)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3840x2160x3 frames, masks {10,4,1}% x {edge-clustered, "
+                               "uniform} in rotation, tol 0.05 gray (error-estimate stop rule)",
+                   "block": 32, "overlap": 6, "local_iters": 8, "frames": len(cases),
+                   "l2": "inputs larger than L2 (6 rotating frames, 650 MB), no flush",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "latency_ms": {"p50": round(lat[len(lat) // 2], 4),
+                       "p99": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 4)},
+        "cycles_mean": round(mean_cycles, 3),
+        "hbm_model_gbs": round(hbm_model_gbs, 1),
+        "e2e": {"value": round(e2e_steps * ws / (e2e_ms / 1e3), 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches"]),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "accuracy": accuracy,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+
+    samples = []
+    for i, (d, kind) in enumerate(CASES):
+        f, c = synth.make_case(W4K, H4K, C4K, d, kind, _case_seed(i))
+        samples.append(_cpu_sample(f, c, 640, 360))
+    for i in range(args.warmup):
+        _run_oracle_timed(*samples[i % len(samples)])
+    t0 = time.perf_counter()
+    times = []
+    for i in range(args.steps):
+        _, t = _run_oracle_timed(*samples[i % len(samples)])
+        times.append(t)
+    total = time.perf_counter() - t0
+    share = samples[0][0].size / float(W4K * H4K * C4K)
+    value = args.steps * share / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3840x2160x3 frames, masks {10,4,1}% x {edge-clustered, "
+                               "uniform} in rotation; each step one 640x360 channel crop",
+                   "solver": "FP64 CG on the reduced system, rel. residual 1e-12"},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": "one 640x360 single-channel crop per step, frames/s "
+                                   "scaled by pixel-channels"},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

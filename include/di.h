@@ -70,7 +70,9 @@ typedef struct {
     float alpha;      /* Robin parameter of the inner block boundaries, > 0 [0.5] (Section 3) */
     int downsample;   /* mask-value downsampling: 0 modified [default], 1 naive (Section 4.3) */
     int stop_rule;    /* DI_STOP_* [DI_STOP_ERROR_ESTIMATE] */
-    int reserved[5];
+    int profile;      /* 1: time every finest-level ORAS block launch with CUDA events
+                         recorded on the call's stream (see di_get_profile) [0] */
+    int reserved[4];
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */
@@ -123,6 +125,25 @@ di_status di_inpaint(di_ctx *ctx, const float *f, const uint8_t *c, int width, i
 
 /* Statistics of the last di_inpaint call. */
 di_status di_get_stats(const di_ctx *ctx, di_stats *out);
+
+/* Kernel counters of a context, accumulated over di_inpaint calls since the
+ * last di_reset_profile.  launches counts every kernel the library enqueued
+ * (all contexts of the process, since the library has one launch counter).
+ * The oras_* fields are filled only when cfg.profile = 1: number of
+ * finest-level ORAS block-kernel launches, their summed duration (from CUDA
+ * events on the launching stream, so they include nothing but that kernel)
+ * and the pixel-channels they processed. */
+typedef struct {
+    long long launches;
+    long long oras_l0_launches;
+    double oras_l0_ms;
+    long long oras_l0_pixel_channels;
+    long long oras_l0_cg_steps;  /* local CG step limit of those launches, summed */
+    long long reserved[4];
+} di_profile;
+
+di_status di_get_profile(const di_ctx *ctx, di_profile *out);
+di_status di_reset_profile(di_ctx *ctx);
 
 /* Human-readable name of a status code (static storage). */
 const char *di_status_string(di_status s);

@@ -347,35 +347,34 @@ def _apply_local(diag, couple, cb, v):
     return np.where(cb, 0.0, q)
 
 
-def solve_local_pcg(c, y0, y1, x0, x1, alpha, rb: np.ndarray, iters: int) -> np.ndarray:
-    """`iters` steps of Jacobi-preconditioned CG (Hestenes-Stiefel) on A_i v =
-    R_i r from v = 0, for the unknown pixels of the block; v = r at mask pixels
-    (the scheduler keeps r = 0 there).  Breakdown guards: a step with
-    p.Ap <= 0 takes alpha = 0, and r.z = 0 gives beta = 0 (both happen only
-    when the block's residual is exactly zero).  The paper stops its local CG at a fraction of
-    the global residual (Section 3.1); a fixed count is this build's reading."""
+def solve_local_cg(c, y0, y1, x0, x1, alpha, rb: np.ndarray, iters: int) -> np.ndarray:
+    """`iters` steps of plain conjugate gradients (Hestenes-Stiefel; Section
+    3.1 solves the local problems with "a simple conjugate gradient
+    algorithm") on A_i v = R_i r from v = 0, over the unknown pixels of the
+    block; v = r at mask pixels (the scheduler keeps r = 0 there).  Breakdown
+    guards: a step with p.Ap <= 0 takes alpha = 0, and r.r = 0 gives beta = 0
+    (both happen only when the block's residual is exactly zero).  The paper
+    stops its local CG at a fraction of the global residual; a fixed step
+    count is this build's reading."""
     diag, couple, cb = local_operator(c, y0, y1, x0, x1, alpha)
     rb = np.asarray(rb, dtype=np.float64)
     v = np.zeros_like(rb)
     r = np.where(cb, 0.0, rb)
-    dinv = np.where(cb, 0.0, 1.0 / diag)
     for ch in range(rb.shape[0]):
         x = v[ch]
         rr = r[ch].copy()
-        z = dinv * rr
-        p = z.copy()
-        rz = float((rr * z).sum())
+        p = rr.copy()
+        rho = float((rr * rr).sum())
         for _ in range(iters):
             q = _apply_local(diag, couple, cb, p)
             pq = float((p * q).sum())
-            a = rz / pq if pq > 0.0 else 0.0
+            a = rho / pq if pq > 0.0 else 0.0
             x += a * p
             rr -= a * q
-            z = dinv * rr
-            rz_new = float((rr * z).sum())
-            beta = rz_new / rz if rz > 0.0 else 0.0
-            rz = rz_new
-            p = z + beta * p
+            rho_new = float((rr * rr).sum())
+            beta = rho_new / rho if rho > 0.0 else 0.0
+            rho = rho_new
+            p = rr + beta * p
         v[ch] = x
     return np.where(cb, rb, v)
 
@@ -387,7 +386,7 @@ def solve_local_pcg(c, y0, y1, x0, x1, alpha, rb: np.ndarray, iters: int) -> np.
 
 def oras_iteration(u, b, c, block=32, overlap=6, alpha=0.5, local="exact"):
     """One ORAS iteration (Algorithm 2): r = b - A u; A_i v_i = R_i r for every
-    block; u + sum_i R_i^T D_i v_i.  local = "exact" or ("pcg", iters)."""
+    block; u + sum_i R_i^T D_i v_i.  local = "exact" or ("cg", iters)."""
     u = np.asarray(u, dtype=np.float64)
     if u.ndim == 2:
         u = u[None]
@@ -403,7 +402,7 @@ def oras_iteration(u, b, c, block=32, overlap=6, alpha=0.5, local="exact"):
             if local == "exact":
                 v = solve_local_exact(c, y0, y1, x0, x1, alpha, rb)
             else:
-                v = solve_local_pcg(c, y0, y1, x0, x1, alpha, rb, int(local[1]))
+                v = solve_local_cg(c, y0, y1, x0, x1, alpha, rb, int(local[1]))
             d = wy[ky, y0:y1][:, None] * wx[kx, x0:x1][None, :]
             du[:, y0:y1, x0:x1] += d * v
     return u + du

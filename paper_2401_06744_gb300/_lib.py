@@ -26,7 +26,8 @@ class di_config(ctypes.Structure):
                 ("pre", ctypes.c_int), ("post", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("min_cycles", ctypes.c_int),
                 ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
-                ("stop_rule", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class di_stats(ctypes.Structure):
@@ -41,6 +42,12 @@ class di_plan_info(ctypes.Structure):
                 ("height", ctypes.c_int * 24), ("blocks_x", ctypes.c_int * 24),
                 ("blocks_y", ctypes.c_int * 24), ("local_problems", ctypes.c_longlong),
                 ("workspace_bytes", ctypes.c_longlong)]
+
+
+class di_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("oras_l0_launches", ctypes.c_longlong),
+                ("oras_l0_ms", ctypes.c_double), ("oras_l0_pixel_channels", ctypes.c_longlong),
+                ("oras_l0_cg_steps", ctypes.c_longlong), ("reserved", ctypes.c_longlong * 4)]
 
 
 class DiError(RuntimeError):
@@ -62,6 +69,8 @@ _SIGS = {
     "di_destroy": (None, [_P]),
     "di_inpaint": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P]),
     "di_get_stats": (_I, [_P, ctypes.POINTER(di_stats)]),
+    "di_get_profile": (_I, [_P, ctypes.POINTER(di_profile)]),
+    "di_reset_profile": (_I, [_P]),
     "di_status_string": (ctypes.c_char_p, [_I]),
     "di_last_error": (ctypes.c_char_p, [_P]),
     "di_mask_downsample": (_I, [_P, _I, _I, _P, _P]),
@@ -213,6 +222,16 @@ class Context:
         return {"levels": s.levels, "levels_used": s.levels_used, "cycles": s.cycles,
                 "converged": bool(s.converged), "est_error": s.est_error,
                 "rel_residual": list(s.rel_residual), "unknowns": s.unknowns}
+
+    def profile(self) -> dict:
+        pr = di_profile()
+        _check(load().di_get_profile(self._h, ctypes.byref(pr)), self)
+        return {"launches": pr.launches, "oras_l0_launches": pr.oras_l0_launches,
+                "oras_l0_ms": pr.oras_l0_ms, "oras_l0_pixel_channels": pr.oras_l0_pixel_channels,
+                "oras_l0_cg_steps": pr.oras_l0_cg_steps}
+
+    def reset_profile(self):
+        _check(load().di_reset_profile(self._h), self)
 
     # -- single steps needing a context -----------------------------------
     def residual_norm(self, u, b, c, rhs_zero=False, want_r=True, stream=None):

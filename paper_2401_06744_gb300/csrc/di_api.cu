@@ -34,6 +34,7 @@ struct Level {
     const float* b = nullptr;    // mask values (level 0: caller's f, read only on the mask)
     float* u[2] = {nullptr, nullptr};
     float* r = nullptr;          // restricted residual (right-hand side of the error equation)
+    uint32_t* mbits = nullptr;   // bit-packed mask for the block solver
     long long unknowns = 0;
 };
 
@@ -56,6 +57,13 @@ struct di_ctx {
     int L = 0;
     di_stats stats;
     char err[256];
+    // profiling (cfg.profile): event pairs around finest-level ORAS launches
+    static constexpr int kEvPairs = 64;
+    cudaEvent_t ev[kEvPairs][2] = {};
+    bool ev_made = false;
+    int ev_used = 0;
+    di_profile prof = {};
+    long long launch_base = 0;
 };
 
 namespace {
@@ -93,12 +101,24 @@ bool config_ok(const di_config& c) {
     if (!(c.alpha > 0.f) || !std::isfinite(c.alpha)) return false;
     if (c.downsample != 0 && c.downsample != 1) return false;
     if (c.stop_rule < 0 || c.stop_rule > 2) return false;
+    if (c.profile != 0 && c.profile != 1) return false;
     return true;
 }
 
 di_status cuda_fail(di_ctx* ctx, cudaError_t e, const char* what) {
     if (ctx) std::snprintf(ctx->err, sizeof ctx->err, "%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? DI_ERR_OOM : DI_ERR_CUDA;
+}
+
+// Add the durations of the recorded event pairs (the stream has been
+// synchronised) to the profile and recycle the pairs.
+void prof_flush(di_ctx* ctx) {
+    for (int i = 0; i < ctx->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess)
+            ctx->prof.oras_l0_ms += ms;
+    }
+    ctx->ev_used = 0;
 }
 
 #define DI_CUDA(ctx, call)                                  \
@@ -124,6 +144,7 @@ size_t pool_bytes(int w, int h, int C, int L) {
     int lw = w, lh = h;
     for (int l = 0; l < L; ++l) {
         const size_t n = (size_t)lw * lh;
+        total += align_up((size_t)lh * mask_words_per_row(lw) * sizeof(uint32_t));  // mbits
         if (l == 0) {
             total += align_up(n * C * sizeof(float));  // u[1]
         } else {
@@ -170,6 +191,8 @@ void bind_levels(di_ctx* ctx, const float* f, const uint8_t* c, float* u, int w,
         v.h = lh;
         v.n = (size_t)lw * lh;
         const size_t fb = align_up(v.n * C * sizeof(float));
+        v.mbits = reinterpret_cast<uint32_t*>(p);
+        p += align_up((size_t)lh * mask_words_per_row(lw) * sizeof(uint32_t));
         if (l == 0) {
             v.c = c;
             v.b = f;
@@ -220,9 +243,25 @@ struct Sched {
         if (l == 0) { rhs = v.b; rhs_zero = 1; }
         else if (vcycle_phase) { rhs = v.r; rhs_zero = 0; }
         else { rhs = v.b; rhs_zero = 1; }
-        DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.c, v.w, v.h, C, ctx->cfg.block,
+        cudaEvent_t* ev = nullptr;
+        if (l == 0 && ctx->cfg.profile) {
+            if (!ctx->ev_made) {
+                for (int i = 0; i < di_ctx::kEvPairs; ++i)
+                    for (int k = 0; k < 2; ++k) DI_CUDA(ctx, cudaEventCreate(&ctx->ev[i][k]));
+                ctx->ev_made = true;
+            }
+            if (ctx->ev_used == di_ctx::kEvPairs) {
+                DI_CUDA(ctx, cudaStreamSynchronize(s));
+                prof_flush(ctx);
+            }
+            ev = ctx->ev[ctx->ev_used++];
+            ctx->prof.oras_l0_launches += 1;
+            ctx->prof.oras_l0_pixel_channels += (long long)v.n * C;
+            ctx->prof.oras_l0_cg_steps += iters;
+        }
+        DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.mbits, v.w, v.h, C, ctx->cfg.block,
                                  ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
-                                 ctx->planes, maxupd, s));
+                                 ctx->planes, maxupd, s, ev));
         return DI_OK;
     }
 
@@ -328,6 +367,7 @@ di_status di_create(const di_config* cfg, int device, di_ctx** out) {
     di_ctx* ctx = new (std::nothrow) di_ctx();
     if (!ctx) return DI_ERR_OOM;
     ctx->cfg = c;
+    ctx->launch_base = launch_count();
     ctx->device = device;
     std::memset(&ctx->stats, 0, sizeof ctx->stats);
     ctx->err[0] = 0;
@@ -349,6 +389,9 @@ void di_destroy(di_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_workspace(ctx);
+    if (ctx->ev_made)
+        for (int i = 0; i < di_ctx::kEvPairs; ++i)
+            for (int k = 0; k < 2; ++k) cudaEventDestroy(ctx->ev[i][k]);
     if (ctx->norm2) cudaFree(ctx->norm2);
     if (ctx->counts) cudaFree(ctx->counts);
     if (ctx->upd) cudaFree(ctx->upd);
@@ -370,6 +413,20 @@ const char* di_status_string(di_status s) {
 }
 
 const char* di_last_error(const di_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+di_status di_get_profile(const di_ctx* ctx, di_profile* out) {
+    if (!ctx || !out) return DI_ERR_INVALID_ARG;
+    *out = ctx->prof;
+    out->launches = launch_count() - ctx->launch_base;
+    return DI_OK;
+}
+
+di_status di_reset_profile(di_ctx* ctx) {
+    if (!ctx) return DI_ERR_INVALID_ARG;
+    std::memset(&ctx->prof, 0, sizeof ctx->prof);
+    ctx->launch_base = launch_count();
+    return DI_OK;
+}
 
 di_status di_get_stats(const di_ctx* ctx, di_stats* out) {
     if (!ctx || !out) return DI_ERR_INVALID_ARG;
@@ -402,12 +459,14 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     unsigned long long* cnt = ctx->counts;
     DI_CUDA(ctx, cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s));
     DI_CUDA(ctx, launch_count_mask(c, n0, cnt, s));  // cnt[0] known, cnt[1] unknown (level 0)
+    DI_CUDA(ctx, launch_pack_mask(c, width, height, ctx->lv[0].mbits, s));
     for (int l = 1; l < L; ++l) {
         Level& f_ = ctx->lv[l - 1];
         Level& cv = ctx->lv[l];
         DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), cnt + 1 + l, s));
         DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
                                         const_cast<float*>(cv.b), cfg.downsample == 0 ? 1 : 0, s));
+        DI_CUDA(ctx, launch_pack_mask(cv.c, cv.w, cv.h, cv.mbits, s));
     }
     unsigned long long* hcnt = static_cast<unsigned long long*>(ctx->host);
     DI_CUDA(ctx, cudaMemcpyAsync(hcnt, cnt, (L + 1) * sizeof(unsigned long long),
@@ -489,6 +548,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
             DI_CUDA(ctx, cudaMemcpyAsync(hupd, ctx->upd, nslots * sizeof(unsigned),
                                          cudaMemcpyDeviceToHost, s));
             DI_CUDA(ctx, cudaStreamSynchronize(s));
+            prof_flush(ctx);
             float U = 0.f;
             for (int k = 0; k < nslots; ++k) U += bits_to_float(reinterpret_cast<unsigned*>(hupd)[k]);
             if (!std::isfinite(U)) { est = INFINITY; prevU = -1.f; prevQ = -1.f; }
@@ -512,6 +572,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
             DI_CUDA(ctx, cudaMemcpyAsync(hnorm, ctx->norm2, C * sizeof(double),
                                          cudaMemcpyDeviceToHost, s));
             DI_CUDA(ctx, cudaStreamSynchronize(s));
+            prof_flush(ctx);
             bool ok = true;
             for (int k = 0; k < C; ++k) {
                 const double rr = bnorm2[k] > 0 ? std::sqrt(hnorm[k] / bnorm2[k]) : 0.0;
@@ -525,6 +586,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         DI_CUDA(ctx, cudaStreamSynchronize(s));
         converged = true;
     }
+    prof_flush(ctx);
     ctx->stats.cycles = cycles;
     ctx->stats.converged = converged ? 1 : 0;
     return converged ? DI_OK : DI_ERR_NOT_CONVERGED;
@@ -601,9 +663,14 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     DI_CUDA(ctx, cudaSetDevice(ctx->device));
     di_status st = ensure_workspace(ctx, width, height, channels);
     if (st) return st;
-    DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, c, width, height, channels,
+    // the single-step call uses the finest level's packed-mask buffer of the pool
+    bind_levels(ctx, b, c, u_out, width, height, channels);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* bits = ctx->lv[0].mbits;
+    DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, s));
+    DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels,
                              ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
-                             u_out, ctx->planes, nullptr, static_cast<cudaStream_t>(stream)));
+                             u_out, ctx->planes, nullptr, s));
     return DI_OK;
 }
 

@@ -9,6 +9,9 @@
 namespace di {
 
 constexpr int kMaxChannels = 4;
+
+// Kernels enqueued by the launch wrappers below (process-wide counter).
+long long launch_count();
 constexpr int kMaxLevels = 24;
 constexpr int kMaxUpdSlots = 16;
 
@@ -49,13 +52,19 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
                           cudaStream_t s);
 
-// One ORAS iteration u_in -> u_out (planes: 4*C*w*h floats of workspace).
-// Each local PCG runs `iters` steps or until r.z <= rtol2 * (r.z)_0.
-// max |v_i| over pixels with nonzero weight folded into *maxupd (nullable).
+// Bit-packed mask (see mask_words_per_row) of c.
+cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cudaStream_t s);
+
+// One ORAS iteration u_in -> u_out (planes: 4*C*w*h floats of workspace;
+// mbits: the packed mask of this level).  Each local CG runs `iters` steps or
+// until r.r <= max(rtol2, 1e-14) * (r.r)_0.  max |v_i| over pixels with
+// nonzero weight is folded into *maxupd (nullable).
+// ev (nullable): two events recorded on `s` right before and right after the
+// block kernel (the combine kernels follow the second one).
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
-                        const uint8_t* c, int w, int h, int C, int B, int o, float alpha,
+                        const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s);
+                        cudaStream_t s, cudaEvent_t* ev = nullptr);
 
 // Host-side geometry shared with the kernels.
 inline int axis_blocks(int n, int B, int o) {
@@ -63,6 +72,8 @@ inline int axis_blocks(int n, int B, int o) {
     int nb = (n - o + s - 1) / s;
     return nb < 1 ? 1 : nb;
 }
+// 32-bit words per row of a bit-packed mask, with one padding word.
+inline int mask_words_per_row(int w) { return (w + 31) / 32 + 1; }
 inline void coarse_dims(int w, int h, int* wH, int* hH) {
     *wH = (w + 1) / 2;
     *hH = (h + 1) / 2;

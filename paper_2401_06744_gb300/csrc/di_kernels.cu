@@ -13,12 +13,14 @@
 //   k_restrict       Algorithm 3 steps 2-3 fused: residual + 2x2 averaging (x4)
 //   k_prolong        Section 4.4 bilinear prolongation, cascadic or correction mode
 //   k_select         u = c ? b : 0
-//   k_oras_block     Algorithm 2 step 2 and the D_i-weighted part of step 3:
-//                    one CTA per (block, channel); the block and a one-pixel
+//   k_pack_mask      bit-packed copy of a level's mask for the block solver
+//   k_oras_warp      Algorithm 2 step 2 and the D_i-weighted part of step 3:
+//                    one warp per (block, channel); the block and a one-pixel
 //                    halo are staged in shared memory and the local Robin
-//                    problem is solved there by Jacobi-PCG held in registers
-//   k_oras_combine   Algorithm 2 step 3 for pixels shared by several blocks:
-//                    sums the weighted block contributions in a fixed order
+//                    problem is solved by plain CG held in registers
+//   k_combine_rows/cols  Algorithm 2 step 3 for pixels shared by several
+//                    blocks: sum the weighted block contributions in a fixed
+//                    order (shared rows full width, then shared columns)
 //
 // Layout: images planar [C][h][w] float32, masks [h][w] uint8.  The ORAS
 // block pass writes pixels that only one block weights (weight 1) straight to
@@ -31,10 +33,18 @@
 #include <cfloat>
 #include <cmath>
 
+#include <atomic>
+
 namespace di {
+
+static std::atomic<long long> g_launches{0};
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+inline void count(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -50,19 +60,6 @@ __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
     return v;
-}
-
-// Weight of block k (of nb along this axis, stride s, overlap o) at local
-// coordinate l: linear ramps with 0 at the block's outermost overlap pixel and
-// 1 at its innermost one (Section 3.1); 1/2 for an overlap of width 1.
-__device__ __forceinline__ float axis_weight(int l, int k, int nb, int s, int o) {
-    float wgt = 1.f;
-    if (k > 0 && l < o) wgt *= (o == 1) ? 0.5f : (float)l / (float)(o - 1);
-    if (k < nb - 1 && l >= s) {
-        const int j = l - s;
-        wgt *= (o == 1) ? 0.5f : 1.f - (float)j / (float)(o - 1);
-    }
-    return wgt;
 }
 
 // Blocks with nonzero weight at global coordinate g along one axis: returns
@@ -340,202 +337,364 @@ __global__ void k_select(const float* __restrict__ b, const uint8_t* __restrict_
 // ORAS (Algorithm 2)
 // ---------------------------------------------------------------------------
 
-// One CTA solves one block of one channel.  Thread t owns column lx = t % B of
-// the block and the R rows [strip * R, strip * R + R) with strip = t / B, so a
-// B-lane segment of a warp covers R full rows: horizontal neighbours come from
-// lane shuffles, vertical ones from registers, and only the strip ends go
-// through shared memory.  Pixels of a block clipped at the image edge that
-// fall outside the image are inert (zero rows, zero couplings).
-template <int B, int R>
-__global__ void __launch_bounds__(B * B / R)
-k_oras_block(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
-             int rhs_zero, const uint8_t* __restrict__ c, int w, int h, int o, int nbx, int nby,
-             float alpha, int iters, float rtol2, float* __restrict__ u_out,
-             float* __restrict__ planes, unsigned* __restrict__ maxupd) {
-    constexpr int T = B * B / R;
-    constexpr int NS = B / R;
-    constexpr int NW = T / 32;
-    static_assert(T % 32 == 0 && B <= 32 && R <= 32, "block shape");
+// ---- packed FP32 pairs (Blackwell f32x2 arithmetic) -------------------------
+// A pair holds two horizontally adjacent pixels of one row (lo = even column).
+typedef unsigned long long f2;
 
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float lo2(f2 a) { return __uint_as_float((unsigned)(a & 0xffffffffull)); }
+__device__ __forceinline__ float hi2(f2 a) { return __uint_as_float((unsigned)(a >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Partition-of-unity weight of block k (of nb along an axis, stride s,
+// overlap o) at local coordinate l (Section 3.1): 0 at the block's outermost
+// overlap pixel, 1 at its innermost one, linear in between (1/2 for o = 1).
+// The ramp end points are exact so that "weight == 1" and "weight == 0"
+// agree with the integer classification of the combine pass.
+__device__ __forceinline__ float ramp_weight(int l, int k, int nb, int s, int o, float inv_o1) {
+    float wgt = 1.f;
+    if (k > 0 && l < o)
+        wgt *= (o == 1) ? 0.5f : (l == o - 1 ? 1.f : (float)l * inv_o1);
+    if (k < nb - 1 && l >= s) {
+        const int jj = l - s;
+        wgt *= (o == 1) ? 0.5f : (jj == 0 ? 1.f : (jj == o - 1 ? 0.f : 1.f - (float)jj * inv_o1));
+    }
+    return wgt;
+}
+
+// ---- asynchronous global -> shared copies (4-byte, zero fill) ----------------
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    const int nbytes = ok ? 4 : 0;  // 0: nothing is read, the word is zero-filled
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(src), "r"(nbytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Bit-packed mask: row y, word k covers columns [32k, 32k + 32); bit set =
+// known pixel or a column beyond the image.  wpr = words per row, including
+// one padding word so that two consecutive words can always be read.
+__global__ void k_pack_mask(const uint8_t* __restrict__ c, int w, int h,
+                            uint32_t* __restrict__ bits, int wpr) {
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long total = (long long)h * wpr;
+    if (wid >= total) return;  // whole warp: wid is warp-uniform
+    const int y = (int)(wid / wpr), k = (int)(wid % wpr);
+    const int x = 32 * k + lane;
+    const bool known = x >= w || c[(size_t)y * w + x] != 0;
+    const unsigned word = __ballot_sync(kFull, known);
+    if (lane == 0) bits[wid] = word;
+}
+
+// One ORAS iteration, one warp per (block, channel) task.
+//
+// Lane layout: lane = (g, col), col = lane % B the block column and g the row
+// group of R = B*B/32 rows; every CG vector is kept in registers as NP = R/2
+// packed pairs, pair k = (row gR + k, row gR + k + NP) of the lane's column.
+// Vertical neighbours of a pair are the neighbouring pairs (the first and the
+// last pair swap one half with the other end of the column, and with the
+// neighbouring row group through a shuffle); horizontal neighbours are the
+// same pair of the neighbouring lanes (one 64-bit shuffle each way), with the
+// block's outer columns cut by a 0/1 factor.  No shared memory and no barrier
+// inside the CG loop.  Warps are persistent over a contiguous range of tasks
+// (channel fastest, so the channels of one block are consecutive and share
+// its mask bits and local operator); the next task's halo tile is fetched with
+// cp.async while the current one is solved.
+//
+// Local problem (Section 3, Algorithm 2 step 2): plain CG on A_i v = R_i r
+// from v = 0, A_i the rows of A for the block's unknown pixels with couplings
+// to in-block neighbours only and alpha added to the diagonal for every
+// in-image neighbour across the block edge (Robin), image edges reflecting.
+// Vectors vanish on known pixels and outside the image, so the stencil reads
+// neighbours unconditionally and only its result is masked.
+template <int B>
+struct WarpTile {
+    static constexpr int G = 32 / B;       // row groups
+    static constexpr int R = B / G;        // rows per lane
+    static constexpr int NP = R / 2;       // packed pairs per lane
+    static constexpr int TH = B + 2;       // tile side with the one-pixel halo
+    static constexpr int P = B == 8 ? 12 : B + 2;  // tile pitch: row groups hit distinct banks
+    static constexpr int TILE = TH * P;
+};
+
+template <int B>
+__global__ void __launch_bounds__(32)
+k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
+            int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C,
+            int o, int nbx, int nby, float alpha, int iters, float rtol2,
+            float* __restrict__ u_out, float* __restrict__ planes, unsigned* __restrict__ maxupd,
+            int chan_inner) {
+    using WT = WarpTile<B>;
+    constexpr int G = WT::G, R = WT::R, NP = WT::NP, TH = WT::TH, P = WT::P, TILE = WT::TILE;
+    static_assert(G * B == 32 && R * G == B && NP * 2 == R, "warp shape");
+
+    extern __shared__ float smem[];
+    float* const s_u = smem;               // [2][TH][P]
+    float* const s_b = smem + 2 * TILE;    // [2][B][B], only when rhs_zero == 0
+
+    const int lane = threadIdx.x;
+    const int col = lane % B, g = lane / B;
     const int s = B - o;
-    const int kx = blockIdx.x % nbx, ky = blockIdx.x / nbx;
-    const int ch = blockIdx.y, C = gridDim.y;
-    const int x0 = kx * s, y0 = ky * s;
-    const int bw = min(B, w - x0), bh = min(B, h - y0);
     const size_t n = (size_t)w * h;
-    const float* uc = u_in + ch * n;
+    const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
 
-    __shared__ float s_u[B + 2][B + 3];
-    __shared__ uint8_t s_c[B][B + 4];
-    __shared__ float s_ztop[NS][B], s_zbot[NS][B];
-    __shared__ float s_red1[NW], s_red2[NW], s_max[NW];
-
-    const int t = threadIdx.x;
-    const int lx = t % B, strip = t / B;
-    const int lane = t & 31, warp = t >> 5;
-
-    for (int i = t; i < (B + 2) * (B + 2); i += T) {
-        const int yy = i / (B + 2), xx = i % (B + 2);
-        const int gy = y0 - 1 + yy, gx = x0 - 1 + xx;
-        float v = 0.f;
-        if (!zero_in && gy >= 0 && gy < h && gx >= 0 && gx < w) v = uc[(size_t)gy * w + gx];
-        s_u[yy][xx] = v;
-    }
-    for (int i = t; i < B * B; i += T) {
-        const int yy = i / B, xx = i % B;
-        s_c[yy][xx] = (yy < bh && xx < bw) ? (c[(size_t)(y0 + yy) * w + x0 + xx] != 0) : 1;
-    }
-    __syncthreads();
-
-    // Local operator A_i: every unknown pixel couples with -1 to its in-block
-    // 4-neighbours; its diagonal counts in-block neighbours (1 each) and
-    // in-image neighbours across the block edge (Robin: alpha each), while
-    // image edges add nothing (reflecting).  Search directions vanish on mask
-    // pixels and outside the block (z = D^-1 r with D^-1 = 0 there), so the
-    // stencil needs no per-neighbour coupling flags: only the lanes at the
-    // block's left and right edges drop the wrapped-around shuffle value.
-    float x[R], r[R], p[R], z[R], dg[R], di[R];
-    unsigned act = 0;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int ly = strip * R + i;
-        const int gx = x0 + lx, gy = y0 + ly;
-        x[i] = 0.f;
-        r[i] = 0.f;
-        dg[i] = 0.f;
-        di[i] = 0.f;
-        if (lx < bw && ly < bh && !s_c[ly][lx]) {
-            float diag = 0.f, nb = 0.f;
-            int deg = 0;
-            if (gx > 0) { ++deg; nb += s_u[ly + 1][lx]; diag += lx > 0 ? 1.f : alpha; }
-            if (gx < w - 1) { ++deg; nb += s_u[ly + 1][lx + 2]; diag += lx + 1 < bw ? 1.f : alpha; }
-            if (gy > 0) { ++deg; nb += s_u[ly][lx + 1]; diag += ly > 0 ? 1.f : alpha; }
-            if (gy < h - 1) { ++deg; nb += s_u[ly + 2][lx + 1]; diag += ly + 1 < bh ? 1.f : alpha; }
-            const float bb = rhs_zero ? 0.f : rhs[ch * n + (size_t)gy * w + gx];
-            r[i] = bb - ((float)deg * s_u[ly + 1][lx + 1] - nb);
-            dg[i] = diag;
-            di[i] = 1.f / diag;
-            act |= 1u << i;
+    // Task sequence of this warp.  chan_inner: blocks blockIdx.x, +gridDim.x,
+    // ... each with all channels back to back (warps running together cover a
+    // contiguous band of blocks, so halo re-reads hit L2, and a block's mask
+    // bits and operator serve all its channels); otherwise (fewer blocks than
+    // warps) tasks blockIdx.x, +gridDim.x, ... of the (block, channel) list.
+    const int nblk = nbx * nby;
+    auto task_of = [&](int i, int& blk, int& ch) {
+        if (chan_inner) {
+            blk = (int)blockIdx.x + (i / C) * (int)gridDim.x;
+            ch = i % C;
+        } else {
+            const int t = (int)blockIdx.x + i * (int)gridDim.x;
+            blk = t / C;
+            ch = t - blk * C;
         }
-    }
-    const float ml = lx > 0 ? 1.f : 0.f;
-    const float mr = lx < B - 1 ? 1.f : 0.f;
+        return blk < nblk;
+    };
 
-    // z = D^-1 r, p = z, rho = r.z
-    float rz = 0.f;
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        z[i] = di[i] * r[i];
-        p[i] = z[i];
-        rz += r[i] * z[i];
-    }
-    s_ztop[strip][lx] = z[0];
-    s_zbot[strip][lx] = z[R - 1];
-    rz = warp_sum(rz);
-    if (lane == 0) s_red2[warp] = rz;
-    __syncthreads();
-    rz = 0.f;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) rz += s_red2[i];
-    float pu = strip > 0 ? s_zbot[strip - 1][lx] : 0.f;       // p of the row above the strip
-    float pd = strip < NS - 1 ? s_ztop[strip + 1][lx] : 0.f;  // p of the row below
-    // Stop once r.z <= max(rtol2, 1e-14) * (r.z)_0.  1e-14 is the FP32
-    // floor (relative residual ~1e-7): iterating past it only feeds rounding
-    // noise back into x.  rz and pq are identical in every thread, so every
-    // exit below is taken by the whole block at once.
-    const float rz_stop = fmaxf(rtol2, 1e-14f) * rz;
-
-    for (int it = 0; it < iters; ++it) {
-        if (!(rz > rz_stop)) break;
-        float q[R];
-        float pq = 0.f;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const float left = __shfl_up_sync(kFull, p[i], 1, B);
-            const float right = __shfl_down_sync(kFull, p[i], 1, B);
-            const float up = i > 0 ? p[i - 1] : pu;
-            const float dn = i < R - 1 ? p[i + 1] : pd;
-            float nbs = up + dn;
-            nbs = fmaf(ml, left, nbs);
-            nbs = fmaf(mr, right, nbs);
-            q[i] = ((act >> i) & 1u) ? fmaf(dg[i], p[i], -nbs) : 0.f;
-            pq = fmaf(p[i], q[i], pq);
+    // Issue the copies of task t into buffer `bs` (and the mask words of its
+    // block into nlo/nhi when the block differs from `have_blk`).
+    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
+        const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
+        if (!zero_in) {
+            const float* src = u_in + ch * n;
+            float* dst = s_u + bs * TILE;
+#pragma unroll 4
+            for (int e = lane; e < TH * TH; e += 32) {
+                const int ty = e / TH, tx = e - ty * TH;
+                const int gy = py0 - 1 + ty, gx = px0 - 1 + tx;
+                const bool ok = gy >= 0 && gy < h && gx >= 0 && gx < w;
+                cp_async4(dst + ty * P + tx, ok ? src + (size_t)gy * w + gx : src, ok);
+            }
         }
-        pq = warp_sum(pq);
-        if (lane == 0) s_red1[warp] = pq;
-        __syncthreads();
-        pq = 0.f;
-#pragma unroll
-        for (int i = 0; i < NW; ++i) pq += s_red1[i];
-        if (!(pq > 0.f) || pq == INFINITY) break;
-        const float a = rz / pq;
-        float rzn = 0.f;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-            x[i] = fmaf(a, p[i], x[i]);
-            r[i] = fmaf(-a, q[i], r[i]);
-            z[i] = di[i] * r[i];
-            rzn = fmaf(r[i], z[i], rzn);
+        if (!rhs_zero) {
+            const float* src = rhs + ch * n;
+            float* dst = s_b + bs * B * B;
+#pragma unroll 4
+            for (int e = lane; e < B * B; e += 32) {
+                const int ly = e / B, lx = e - ly * B;
+                const int gy = py0 + ly, gx = px0 + lx;
+                const bool ok = gx < w && gy < h;
+                cp_async4(dst + e, ok ? src + (size_t)gy * w + gx : src, ok);
+            }
         }
-        s_ztop[strip][lx] = z[0];
-        s_zbot[strip][lx] = z[R - 1];
-        rzn = warp_sum(rzn);
-        if (lane == 0) s_red2[warp] = rzn;
-        __syncthreads();
-        rzn = 0.f;
-#pragma unroll
-        for (int i = 0; i < NW; ++i) rzn += s_red2[i];
-        const float beta = rzn / rz;
-        rz = rzn;
-#pragma unroll
-        for (int i = 0; i < R; ++i) p[i] = fmaf(beta, p[i], z[i]);
-        pu = strip > 0 ? fmaf(beta, pu, s_zbot[strip - 1][lx]) : 0.f;
-        pd = strip < NS - 1 ? fmaf(beta, pd, s_ztop[strip + 1][lx]) : 0.f;
-    }
+        cp_async_commit();
+        if (blk != have_blk && lane < B) {
+            const int gy = py0 + lane;
+            if (gy < h) {
+                const uint32_t* row = mbits + (size_t)gy * wpr + (px0 >> 5);
+                nlo = __ldg(row);
+                nhi = __ldg(row + 1);
+            } else {
+                nlo = nhi = 0xffffffffu;
+            }
+        }
+    };
 
-    // u_out = u_in + sum_i R_i^T D_i v_i: weight-1 pixels directly, shared
-    // pixels through the parity planes.
-    const int par = (kx & 1) | ((ky & 1) << 1);
-    float* plane = planes + ((size_t)par * C + ch) * n;
-    float* uo = u_out + ch * n;
-    const float wx = axis_weight(lx, kx, nbx, s, o);
+    int blk, ch;
+    if (!task_of(0, blk, ch)) return;  // warp-uniform
+    prefetch(blk, ch, 0, -1);
+    int buf = 0, cur_blk = -1;
+    // per-block state
+    uint32_t mb = 0;   // bit k: row gR + k of this lane's column is known or outside
+    f2 ndg[NP];        // -(diagonal of A_i) per pair
+    f2 ml2 = 0ull, mr2 = 0ull;  // 0/1: the left / right neighbour column is in the block
+    float wx = 0.f, dh = 0.f;
+    int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
     float vmax = 0.f;
+
+    for (int i = 0;; ++i) {
+        cp_async_wait_all();
+        __syncwarp();
+        const uint32_t mlo = nlo, mhi = nhi;
+        int nblk_, nch;
+        const bool more = task_of(i + 1, nblk_, nch);
+        if (more) prefetch(nblk_, nch, buf ^ 1, blk);
+
+        if (blk != cur_blk) {
+            cur_blk = blk;
+            kx = blk % nbx;
+            ky = blk / nbx;
+            x0 = kx * s;
+            y0 = ky * s;
+            const int bw = min(B, w - x0);
+            bh = min(B, h - y0);
+            // lane l < B holds the mask bits of block row l, columns x0 .. x0+31
+            const uint32_t rowm = __funnelshift_r(mlo, mhi, x0 & 31);
+            mb = 0;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int ly = strip * R + i;
-        if (lx < bw && ly < bh) {
-            const size_t gp = (size_t)(y0 + ly) * w + x0 + lx;
-            const float v = ((act >> i) & 1u) ? x[i] : 0.f;
-            const float d = wx * axis_weight(ly, ky, nby, s, o);
-            if (d == 1.f) uo[gp] = s_u[ly + 1][lx + 1] + v;
-            else if (d > 0.f) plane[gp] = d * v;
-            if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+            for (int rr = 0; rr < B; ++rr) {
+                const uint32_t v = __shfl_sync(kFull, rowm, rr);
+                const int k = rr - g * R;
+                if (k >= 0 && k < R) mb |= ((v >> col) & 1u) << k;
+            }
+            const int gx = x0 + col;
+            const float hc = (col > 0 ? 1.f : (gx > 0 ? alpha : 0.f)) +
+                             (col + 1 < bw ? 1.f : (gx < w - 1 ? alpha : 0.f));
+            dh = (float)((gx > 0) + (gx < w - 1));
+            const float ml = col > 0 ? 1.f : 0.f, mr = col < B - 1 ? 1.f : 0.f;
+            ml2 = pk(ml, ml);
+            mr2 = pk(mr, mr);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                float vc[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = g * R + k + e * NP, gy = y0 + ly;
+                    vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
+                            (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                }
+                ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
+            }
+            wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
         }
+
+        const float* tu = s_u + buf * TILE;
+        const float* tb = s_b + buf * B * B;
+
+        // initial residual r = R_i (b - A u), zero on known pixels
+        f2 x[NP], r[NP], p[NP], q[NP];
+        f2 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float rv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = g * R + k + e * NP, gy = y0 + ly;
+                float v = rhs_zero ? 0.f : tb[ly * B + col];
+                if (!zero_in) {
+                    const float* c0 = tu + (ly + 1) * P + col + 1;
+                    const float dv = (float)((gy > 0) + (gy < h - 1));
+                    v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                }
+                rv[e] = ((mb >> (k + e * NP)) & 1u) ? 0.f : v;
+            }
+            r[k] = pk(rv[0], rv[1]);
+            p[k] = r[k];
+            x[k] = 0ull;
+            if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+            else acc0 = fma2(r[k], r[k], acc0);
+        }
+        acc0 = add2(acc0, acc1);
+        float rr = warp_sum(lo2(acc0) + hi2(acc0));
+        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+
+        for (int it = 0; it < iters; ++it) {
+            if (!(rr > rr_stop)) break;  // rr is warp-uniform
+            // the rows just above / below this lane's row group
+            const float gu = __shfl_up_sync(kFull, hi2(p[NP - 1]), B);
+            const float gd = __shfl_down_sync(kFull, lo2(p[0]), B);
+            const f2 pu = pk(g > 0 ? gu : 0.f, lo2(p[NP - 1]));
+            const f2 pd = pk(hi2(p[0]), g < G - 1 ? gd : 0.f);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const f2 left = __shfl_up_sync(kFull, p[k], 1, B);
+                const f2 right = __shfl_down_sync(kFull, p[k], 1, B);
+                const f2 up = k > 0 ? p[k - 1] : pu;
+                const f2 dn = k < NP - 1 ? p[k + 1] : pd;
+                f2 nbs = add2(up, dn);
+                nbs = fma2(ml2, left, nbs);
+                nbs = fma2(mr2, right, nbs);
+                f2 qk = fma2(ndg[k], p[k], nbs);  // -(A_i p)
+                const float q0 = ((mb >> k) & 1u) ? 0.f : lo2(qk);
+                const float q1 = ((mb >> (k + NP)) & 1u) ? 0.f : hi2(qk);
+                qk = pk(q0, q1);
+                q[k] = qk;
+                if (k & 1) acc1 = fma2(p[k], qk, acc1);
+                else acc0 = fma2(p[k], qk, acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            const float pq = -warp_sum(lo2(acc0) + hi2(acc0));
+            if (!(pq > 0.f) || pq == INFINITY) break;
+            const float a = __fdividef(rr, pq);
+            const f2 a2 = pk(a, a);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                x[k] = fma2(a2, p[k], x[k]);
+                r[k] = fma2(a2, q[k], r[k]);  // r - a A p
+                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+                else acc0 = fma2(r[k], r[k], acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            const float rrn = warp_sum(lo2(acc0) + hi2(acc0));
+            const float beta = __fdividef(rrn, rr);
+            rr = rrn;
+            const f2 b2 = pk(beta, beta);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
+        }
+
+        // u_out = u_in + sum_i R_i^T D_i v_i: weight-1 pixels directly, shared
+        // pixels through the parity planes.
+        const int par = (kx & 1) | ((ky & 1) << 1);
+        float* plane = planes + ((size_t)par * C + ch) * n;
+        float* uo = u_out + ch * n;
+        const bool colok = x0 + col < w;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = g * R + k + e * NP;
+                if (ly >= bh || !colok) continue;
+                const float v = e ? hi2(x[k]) : lo2(x[k]);
+                const float d = wx * ramp_weight(ly, ky, nby, s, o, inv_o1);
+                const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
+                if (d == 1.f) uo[gp] = (zero_in ? 0.f : tu[(ly + 1) * P + col + 1]) + v;
+                else if (d > 0.f) plane[gp] = d * v;
+                if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+            }
+        }
+        if (!more) break;
+        blk = nblk_;
+        ch = nch;
+        buf ^= 1;
     }
     if (maxupd) {
         vmax = warp_max(vmax);
-        if (lane == 0) s_max[warp] = vmax;
-        __syncthreads();
-        if (t == 0) {
-            float m = 0.f;
-            for (int i = 0; i < NW; ++i) m = fmaxf(m, s_max[i]);
-            if (m > 0.f) atomicMax(maxupd, __float_as_uint(m));
-        }
+        if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
     }
 }
 
-__global__ void k_oras_combine(const float* __restrict__ u_in, int zero_in,
-                               const float* __restrict__ planes, int w, int h, int s, int o,
-                               int nbx, int nby, float* __restrict__ u_out) {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gy = blockIdx.y * blockDim.y + threadIdx.y;
-    const int ch = blockIdx.z, C = gridDim.z;
-    if (gx >= w || gy >= h) return;
-    int kx0, kx1, ky0, ky1;
-    const int nx = axis_contrib(gx, s, o, nbx, kx0, kx1);
-    const int ny = axis_contrib(gy, s, o, nby, ky0, ky1);
-    if (nx == 1 && ny == 1) return;  // written by the block pass
-    const size_t n = (size_t)w * h, gp = (size_t)gy * w + gx;
+// Pixels shared by two blocks along one axis are the open interior of each
+// overlap: local offsets 1 .. o-2 after the seam (o >= 3), or the single
+// overlap pixel when o = 1.  nsh is their count per seam.
+__host__ __device__ __forceinline__ int shared_per_seam(int o) { return o == 1 ? 1 : (o > 2 ? o - 2 : 0); }
+__host__ __device__ __forceinline__ int shared_first(int o) { return o == 1 ? 0 : 1; }
+
+// u_out = u_in + sum of the parked contributions at one shared pixel; kx0/kx1
+// (nx of them) and ky0/ky1 (ny) are the blocks with nonzero weight there.
+__device__ __forceinline__ void combine_px(const float* __restrict__ u_in, int zero_in,
+                                           const float* __restrict__ planes, float* __restrict__ u_out,
+                                           size_t n, int C, int ch, size_t gp, int nx, int kx0,
+                                           int kx1, int ny, int ky0, int ky1) {
     float acc = 0.f;
     for (int a = 0; a < ny; ++a) {
         const int ky = a ? ky1 : ky0;
@@ -549,28 +708,101 @@ __global__ void k_oras_combine(const float* __restrict__ u_in, int zero_in,
     u_out[ch * n + gp] = uo + acc;
 }
 
+// Shared rows (the interior rows of every horizontal overlap), full width.
+__global__ void __launch_bounds__(256)
+k_combine_rows(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
+               int w, int h, int s, int o, int nbx, int nby, float* __restrict__ u_out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.z, C = gridDim.z;
+    if (x >= w) return;
+    const int nsh = shared_per_seam(o);
+    const int seam = blockIdx.y / nsh + 1;             // vertical block index ky of the lower block
+    const int y = seam * s + shared_first(o) + (int)blockIdx.y % nsh;
+    if (y >= h) return;
+    int kx0, kx1;
+    const int nx = axis_contrib(x, s, o, nbx, kx0, kx1);
+    combine_px(u_in, zero_in, planes, u_out, (size_t)w * h, C, ch, (size_t)y * w + x, nx, kx0,
+               kx1, 2, seam - 1, seam);
+}
+
+// Shared columns (interior columns of every vertical overlap) in the rows that
+// are not shared along y; one thread per (row, strip column), columns fastest.
+__global__ void __launch_bounds__(256)
+k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
+               int w, int h, int s, int o, int nbx, int nby, float* __restrict__ u_out) {
+    const int nsh = shared_per_seam(o);
+    const int ncols = (nbx - 1) * nsh;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.z, C = gridDim.z;
+    if (idx >= (long long)ncols * h) return;
+    const int y = (int)(idx / ncols), ci = (int)(idx % ncols);
+    int ky0, ky1;
+    const int ny = axis_contrib(y, s, o, nby, ky0, ky1);
+    if (ny == 2) return;  // handled by k_combine_rows
+    const int seam = ci / nsh + 1;
+    const int x = seam * s + shared_first(o) + ci % nsh;
+    if (x >= w) return;
+    combine_px(u_in, zero_in, planes, u_out, (size_t)w * h, C, ch, (size_t)y * w + x, 2,
+               seam - 1, seam, 1, ky0, ky1);
+}
+
 inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
     return dim3((unsigned)((w + blk.x - 1) / blk.x), (unsigned)((h + blk.y - 1) / blk.y),
                 (unsigned)z);
 }
 
-template <int B, int R>
+template <int B>
 cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
-                          const uint8_t* c, int w, int h, int C, int o, float alpha, int iters,
-                          float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                          cudaStream_t s) {
+                          const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
+                          int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
+                          cudaStream_t s, cudaEvent_t* ev) {
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
-    dim3 grid((unsigned)(nbx * nby), (unsigned)C);
-    k_oras_block<B, R><<<grid, B * B / R, 0, s>>>(u_in, zero_in, rhs, rhs_zero, c, w, h, o, nbx,
-                                                  nby, alpha, iters, rtol2, u_out, planes,
-                                                  maxupd);
+    const int ntasks = nbx * nby * C;
+    constexpr int TILE = WarpTile<B>::TILE;
+    const size_t smem = (size_t)2 * TILE * sizeof(float) +
+                        (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
+    // persistent warps: as many as fit on the GPU at once
+    static int occ[2] = {0, 0};
+    static int nsm = 0;
+    int& oc = occ[rhs_zero ? 0 : 1];
+    if (oc == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_oras_warp<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * TILE * sizeof(float) + 2 * B * B * sizeof(float)));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_warp<B>, 32, smem);
+        if (oc < 1) oc = 1;
+    }
+    const int slots = nsm * oc;
+    const int nblk = nbx * nby;
+    const int chan_inner = nblk >= slots ? 1 : 0;
+    int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
+    if (grid < 1) grid = 1;
+    if (ev) cudaEventRecord(ev[0], s);
+    k_oras_warp<B><<<grid, 32, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
+                                          nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
+                                          chan_inner);
+    count();
+    if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // Overlap 2 gives 0/1 weights: no pixel is shared, the combine is empty.
-    if (o != 2 && (nbx > 1 || nby > 1)) {
-        dim3 blk(32, 8);
-        k_oras_combine<<<grid2(w, h, blk, C), blk, 0, s>>>(u_in, zero_in, planes, w, h, B - o, o,
-                                                           nbx, nby, u_out);
+    const int nsh = shared_per_seam(o);
+    if (nsh > 0 && nby > 1) {
+        dim3 grid_r((unsigned)((w + 255) / 256), (unsigned)((nby - 1) * nsh), (unsigned)C);
+        k_combine_rows<<<grid_r, 256, 0, s>>>(u_in, zero_in, planes, w, h, B - o, o, nbx, nby,
+                                             u_out);
+        count();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (nsh > 0 && nbx > 1) {
+        const long long cnt = (long long)(nbx - 1) * nsh * h;
+        dim3 grid_c((unsigned)((cnt + 255) / 256), 1, (unsigned)C);
+        k_combine_cols<<<grid_c, 256, 0, s>>>(u_in, zero_in, planes, w, h, B - o, o, nbx, nby,
+                                             u_out);
+        count();
         e = cudaGetLastError();
     }
     return e;
@@ -588,6 +820,7 @@ cudaError_t launch_count_mask(const uint8_t* c, size_t n, unsigned long long* ou
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
     k_count_mask<<<(unsigned)blocks, 256, 0, s>>>(c, n, out);
+    count();
     return cudaGetLastError();
 }
 
@@ -597,6 +830,7 @@ cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH,
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
     k_mask_down<<<grid2(wH, hH, blk), blk, 0, s>>>(c, w, h, cH, wH, hH, unknownH);
+    count();
     return cudaGetLastError();
 }
 
@@ -606,6 +840,7 @@ cudaError_t launch_values_down(const uint8_t* c, const float* b, int w, int h, i
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
     k_values_down<<<grid2(wH, hH, blk), blk, 0, s>>>(c, b, w, h, C, cH, bH, wH, hH, modified);
+    count();
     return cudaGetLastError();
 }
 
@@ -620,12 +855,14 @@ cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_
     dim3 grid = grid2(w, h, blk, C);
     *nparts = (int)(grid.x * grid.y);
     k_residual<<<grid, blk, 0, s>>>(u, zero_u, b, rhs_zero, c, w, h, r, partials);
+    count();
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, double* out,
                                    cudaStream_t s) {
     k_reduce<<<C, 256, 0, s>>>(partials, nparts, out);
+    count();
     return cudaGetLastError();
 }
 
@@ -635,6 +872,7 @@ cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const 
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
     k_restrict<<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, c, w, h, cH, rH, wH, hH);
+    count();
     return cudaGetLastError();
 }
 
@@ -651,6 +889,7 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
     if (gy < 1) gy = 1;
     if (gy < grid.y) grid.y = gy;
     k_prolong<<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode, mode == 1 ? maxupd : nullptr);
+    count();
     return cudaGetLastError();
 }
 
@@ -661,23 +900,34 @@ cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C,
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
     k_select<<<dim3((unsigned)blocks, (unsigned)C), 256, 0, s>>>(b, c, n, u);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cudaStream_t s) {
+    const long long warps = (long long)h * mask_words_per_row(w);
+    const long long threads = warps * 32;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    k_pack_mask<<<blocks, 256, 0, s>>>(c, w, h, bits, mask_words_per_row(w));
+    count();
     return cudaGetLastError();
 }
 
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
-                        const uint8_t* c, int w, int h, int C, int B, int o, float alpha,
+                        const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s) {
+                        cudaStream_t s, cudaEvent_t* ev) {
+    const int wpr = mask_words_per_row(w);
     switch (B) {
         case 32:
-            return launch_oras_t<32, 8>(u_in, zero_in, rhs, rhs_zero, c, w, h, C, o, alpha, iters,
-                                        rtol2, u_out, planes, maxupd, s);
+            return launch_oras_t<32>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
+                                     iters, rtol2, u_out, planes, maxupd, s, ev);
         case 16:
-            return launch_oras_t<16, 4>(u_in, zero_in, rhs, rhs_zero, c, w, h, C, o, alpha, iters,
-                                        rtol2, u_out, planes, maxupd, s);
+            return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
+                                     iters, rtol2, u_out, planes, maxupd, s, ev);
         case 8:
-            return launch_oras_t<8, 2>(u_in, zero_in, rhs, rhs_zero, c, w, h, C, o, alpha, iters,
-                                       rtol2, u_out, planes, maxupd, s);
+            return launch_oras_t<8>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
+                                    iters, rtol2, u_out, planes, maxupd, s, ev);
         default:
             return cudaErrorInvalidValue;
     }

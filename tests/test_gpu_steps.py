@@ -138,14 +138,14 @@ ORAS_CASES = [  # (h, w, block, overlap, iters)
 
 
 @pytest.mark.parametrize("h,w,B,o,K", ORAS_CASES)
-def test_oras_iteration_matches_oracle_pcg(di, h, w, B, o, K):
+def test_oras_iteration_matches_oracle_cg(di, h, w, B, o, K):
     f, fn, c = _case(h, w, 2, 0.06, h * 23 + w + B)
     g = np.random.default_rng(8)
     # an iterate that equals b on the mask (cascadic form, b = C f) ...
     u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
     with di.Context(block=B, overlap=o, alpha=0.5) as ctx:
         out = N(ctx.oras_iteration(T(u), T(fn), T(c), K, rhs_zero=True))
-        ref = M.oras_iteration(u, M.rhs(f, c), c, B, o, 0.5, ("pcg", K))
+        ref = M.oras_iteration(u, M.rhs(f, c), c, B, o, 0.5, ("cg", K))
         scale = np.abs(ref - u).max()
         assert np.abs(out - ref).max() < 1e-3 * scale + 2e-4
         assert np.array_equal(out[:, c == 1], u[:, c == 1])
@@ -153,7 +153,7 @@ def test_oras_iteration_matches_oracle_pcg(di, h, w, B, o, K):
         b = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
         e = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
         out = N(ctx.oras_iteration(T(e), T(b), T(c), K, rhs_zero=False))
-        ref = M.oras_iteration(e, b, c, B, o, 0.5, ("pcg", K))
+        ref = M.oras_iteration(e, b, c, B, o, 0.5, ("cg", K))
         scale = np.abs(ref - e).max()
         assert np.abs(out - ref).max() < 1e-3 * scale + 1e-5
 

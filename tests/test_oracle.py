@@ -341,12 +341,12 @@ def test_oras_fixed_point_and_convergence():
     assert np.all(np.diff(errs[5:]) <= 1e-12)
 
 
-def test_local_pcg_reaches_exact_local_solve():
+def test_local_cg_reaches_exact_local_solve():
     f, c = _rand_case(12, 12, 1, 0.1, 23)
     g = np.random.default_rng(0).normal(size=(1, 8, 8))
     rb = np.where(c[2:10, 3:11].astype(bool), 0.0, g)
     ex = M.solve_local_exact(c, 2, 10, 3, 11, 0.5, rb)
-    pc = M.solve_local_pcg(c, 2, 10, 3, 11, 0.5, rb, 64)
+    pc = M.solve_local_cg(c, 2, 10, 3, 11, 0.5, rb, 64)
     assert np.abs(ex - pc).max() < 1e-9
 
 
