@@ -387,6 +387,41 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernel(args):
+    """One launch of one step of the path on the first bench frame (for ncu
+    captures of a single kernel); prints a short JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06744_gb300 import build as _build
+
+    _build.build()
+    import paper_2401_06744_gb300 as di
+    import synth
+
+    dev = torch.device("cuda", 0)
+    d, kind = CASES[1]
+    f, c = synth.make_case(W4K, H4K, C4K, d, kind, _case_seed(1))
+    ft = torch.from_numpy(f).to(dev)
+    ct = torch.from_numpy(c).to(dev)
+    u0 = torch.from_numpy(np.where(c.astype(bool), f, 128.0).astype(np.float32)).to(dev)
+    out = {"kernel": args.kernel, "workload": "3840x2160x3, 4% edge-clustered mask"}
+    with di.Context(device=0) as ctx:
+        if args.kernel == "oras":
+            u1 = ctx.oras_iteration(u0, ft, ct, 8, rhs_zero=True)
+            out["max_update"] = float((u1 - u0).abs().max())
+        elif args.kernel == "prolong":
+            e = torch.ones(C4K, (H4K + 1) // 2, (W4K + 1) // 2, device=dev)
+            di.prolong(e, ct, 1, u=u0)
+        elif args.kernel == "restrict":
+            cH = di.mask_downsample(ct)
+            di.restrict_residual(u0, ft, ct, cH, rhs_zero=True)
+        elif args.kernel == "residual":
+            ctx.residual_norm(u0, ft, ct, rhs_zero=True)
+        torch.cuda.synchronize(dev)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,7 +429,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=6)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--kernel", choices=["oras", "prolong", "restrict", "residual"],
+                    help="run one launch of this step on one 4K RGB frame (for ncu) and exit")
     args = ap.parse_args()
+    if args.kernel:
+        run_kernel(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
