@@ -349,9 +349,8 @@ def _apply_local(diag, couple, cb, v):
 
 def solve_local_cg(c, y0, y1, x0, x1, alpha, rb: np.ndarray, iters: int) -> np.ndarray:
     """`iters` steps of plain conjugate gradients (Hestenes-Stiefel; Section
-    3.1 solves the local problems with "a simple conjugate gradient
-    algorithm") on A_i v = R_i r from v = 0, over the unknown pixels of the
-    block; v = r at mask pixels (the scheduler keeps r = 0 there).  Breakdown
+    3.1 solves the local problems with unpreconditioned CG) on A_i v = R_i r
+    from v = 0, over the unknown pixels of the block; v = r at mask pixels (the scheduler keeps r = 0 there).  Breakdown
     guards: a step with p.Ap <= 0 takes alpha = 0, and r.r = 0 gives beta = 0
     (both happen only when the block's residual is exactly zero).  The paper
     stops its local CG at a fraction of the global residual; a fixed step
