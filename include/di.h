@@ -187,6 +187,33 @@ di_status di_residual_norm(di_ctx *ctx, const float *u, const float *b, int rhs_
                            const uint8_t *c, int width, int height, int channels, float *r,
                            double *norm2, void *stream);
 
+/* The residual and squared norm of di_residual_norm, for callers that cannot
+ * allocate device memory when they call: real-time decoders that fix their
+ * device footprint before they start, code running while another component
+ * owns the device allocator, or paths that cannot afford the device-wide
+ * synchronisation cudaFree implies.  It takes no context and allocates
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine).
+ * The paper has no counterpart; this is a deployment variant.
+ *  Scratch: the per-CTA partial sums live in one array of
+ *    DI_NOALLOC_PARTIALS doubles (1 MiB) compiled into the library, which
+ *    every GPU that loads the library keeps until the process exits.
+ *  Limit: ceil(width/32) * ceil(height/8) * channels <= DI_NOALLOC_PARTIALS
+ *    (3840x2160 with up to 4 channels fits); a larger call returns
+ *    DI_ERR_INVALID_ARG before touching the GPU.
+ *  Set-up: the first call on a device looks up the array's device address
+ *    (with that device current), so make that first call before any stream
+ *    capture on the device.
+ *  Sharing: every call uses the same array and leaves its partial sums
+ *    there; nothing in it needs to start at zero.  Calls whose kernels
+ *    overlap on the GPU (different streams or host threads without ordering)
+ *    race on the array and can return wrong norms: order them on one stream
+ *    or synchronise between them.
+ * Other arguments and results as for di_residual_norm. */
+#define DI_NOALLOC_PARTIALS 131072
+di_status di_residual_norm_noalloc(const float *u, const float *b, int rhs_zero,
+                                   const uint8_t *c, int width, int height, int channels,
+                                   float *r, double *norm2, void *stream);
+
 /* Residual restriction (Algorithm 3 steps 2-3, Section 4.4): for every coarse
  * cell with cH == 0, rH = 4 * mean over its fine children of (b - A u) (the
  * factor 4 = (H/h)^2 rescales the unit-spacing stencil to the coarse

@@ -76,6 +76,7 @@ _SIGS = {
     "di_mask_downsample": (_I, [_P, _I, _I, _P, _P]),
     "di_values_downsample": (_I, [_P, _P, _I, _I, _I, _P, _P, _I, _P]),
     "di_residual_norm": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
+    "di_residual_norm_noalloc": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
     "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
@@ -273,6 +274,24 @@ def values_downsample(c, b, cH, modified=True, stream=None):
     _check(load().di_values_downsample(c.data_ptr(), b3.data_ptr(), W, H, C, cH.data_ptr(),
                                        bH.data_ptr(), int(bool(modified)), _stream(stream)))
     return bH
+
+
+NOALLOC_PARTIALS = 131072
+
+
+def residual_norm_noalloc(u, b, c, rhs_zero=False, want_r=True, stream=None):
+    """di_residual_norm_noalloc: residual and squared norm per channel without a
+    context; the library allocates nothing (the outputs here are the
+    caller's tensors)."""
+    u3, b3, c = _img(u, "u"), _img(b, "b"), _mask(c)
+    C, H, W = u3.shape
+    r = torch.empty_like(u3) if want_r else None
+    n2 = torch.empty(C, dtype=torch.float64, device=u3.device)
+    _check(load().di_residual_norm_noalloc(u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
+                                           c.data_ptr(), W, H, C,
+                                           r.data_ptr() if want_r else None, n2.data_ptr(),
+                                           _stream(stream)))
+    return r, n2
 
 
 def restrict_residual(u, b, c, cH, rhs_zero=False, stream=None):

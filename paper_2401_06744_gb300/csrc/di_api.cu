@@ -631,6 +631,19 @@ di_status di_residual_norm(di_ctx* ctx, const float* u, const float* b, int rhs_
     return DI_OK;
 }
 
+di_status di_residual_norm_noalloc(const float* u, const float* b, int rhs_zero,
+                                   const uint8_t* c, int width, int height, int channels,
+                                   float* r, double* norm2, void* stream) {
+    if (!u || !b || !c || !norm2 || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels)
+        return DI_ERR_INVALID_ARG;
+    const long long need = (long long)residual_partials_per_channel(width, height) * channels;
+    if (need > kNoAllocPartials || need > DI_NOALLOC_PARTIALS) return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_residual_noalloc(u, b, rhs_zero ? 1 : 0, c, width, height, channels, r,
+                                            norm2, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
 di_status di_restrict_residual(const float* u, const float* b, int rhs_zero, const uint8_t* c,
                                int width, int height, int channels, const uint8_t* cH,
                                float* rH, void* stream) {

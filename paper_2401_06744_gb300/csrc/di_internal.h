@@ -35,6 +35,13 @@ cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_
                             int* nparts, cudaStream_t s);
 size_t residual_partials_per_channel(int w, int h);
 
+// The same residual + norm with the partial sums in the library's static
+// device array (capacity kNoAllocPartials doubles, checked by the caller).
+constexpr long long kNoAllocPartials = 131072;
+cudaError_t launch_residual_noalloc(const float* u, const float* b, int rhs_zero,
+                                    const uint8_t* c, int w, int h, int C, float* r,
+                                    double* norm2, cudaStream_t s);
+
 // out[ch] = sum of partials[ch * nparts + i] in a fixed order.
 cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, double* out,
                                    cudaStream_t s);

@@ -34,6 +34,7 @@
 #include <cmath>
 
 #include <atomic>
+#include <mutex>
 
 namespace di {
 
@@ -857,6 +858,38 @@ cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_
     k_residual<<<grid, blk, 0, s>>>(u, zero_u, b, rhs_zero, c, w, h, r, partials);
     count();
     return cudaGetLastError();
+}
+
+// Fixed reduction scratch for callers that cannot allocate (see
+// di_residual_norm_noalloc in di.h).  Host code must not pass the symbol
+// itself to a kernel: on the host it names a stand-in, not device memory.
+// Its device address is looked up once per device, with that device current.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+cudaError_t launch_residual_noalloc(const float* u, const float* b, int rhs_zero,
+                                    const uint8_t* c, int w, int h, int C, float* r,
+                                    double* norm2, cudaStream_t s) {
+    static std::mutex mu;
+    static double* addr[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    double* scratch;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess) return e;
+            addr[dev] = static_cast<double*>(p);
+        }
+        scratch = addr[dev];
+    }
+    int nparts = 0;
+    e = launch_residual(u, 0, b, rhs_zero, c, w, h, C, r, scratch, &nparts, s);
+    if (e != cudaSuccess) return e;
+    return launch_reduce_partials(scratch, nparts, C, norm2, s);
 }
 
 cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, double* out,
