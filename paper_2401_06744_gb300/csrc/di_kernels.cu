@@ -257,10 +257,14 @@ k_reduce(const double* __restrict__ partials, int nparts, double* __restrict__ o
 // Grid transfers (Algorithm 3, Section 4.4)
 // ---------------------------------------------------------------------------
 
-__global__ void k_restrict(const float* __restrict__ u, const float* __restrict__ b,
-                           int rhs_zero, const uint8_t* __restrict__ c, int w, int h,
-                           const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH,
-                           int hH) {
+// One thread per coarse cell.  A coarse cell off the coarse mask has four
+// unknown children (max pooling), so their residuals need no mask loads: the
+// 4x4 patch of u around the children is read at once (zero outside the image)
+// and the in-image neighbour count gives the reflecting boundary.
+__global__ void __launch_bounds__(256)
+k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zero,
+           int w, int h, const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH,
+           int hH) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
@@ -268,48 +272,87 @@ __global__ void k_restrict(const float* __restrict__ u, const float* __restrict_
     const size_t n = (size_t)w * h, nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
     if (cH[P]) { rH[ch * nH + P] = 0.f; return; }
     const float* uc = u + ch * n;
-    const float* bc = b + ch * n;
+    const int x0 = 2 * X - 1, y0 = 2 * Y - 1;
+    float t[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int y = y0 + j;
+        const bool yok = y >= 0 && y < h;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int x = x0 + i;
+            const bool corner = (i == 0 || i == 3) && (j == 0 || j == 3);
+            t[j][i] = (!corner && yok && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
+        }
+    }
     float sum = 0.f;
     int cnt = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int x = 2 * X + (k & 1), y = 2 * Y + (k >> 1);
-        if (x >= w || y >= h) continue;
-        sum += residual_at(uc, 0, bc, rhs_zero, c, w, h, x, y);
-        ++cnt;
+    for (int j = 1; j <= 2; ++j) {
+#pragma unroll
+        for (int i = 1; i <= 2; ++i) {
+            const int x = x0 + i, y = y0 + j;
+            if (x >= w || y >= h) continue;
+            const int deg = (x > 0) + (x < w - 1) + (y > 0) + (y < h - 1);
+            const float lu = (float)deg * t[j][i] - (t[j][i - 1] + t[j][i + 1] + t[j - 1][i] + t[j + 1][i]);
+            const float rhs = rhs_zero ? 0.f : b[ch * n + (size_t)y * w + x];
+            sum += rhs - lu;
+            ++cnt;
+        }
     }
     rH[ch * nH + P] = 4.f * sum / (float)cnt;
 }
 
-// One thread per fine pixel column position; each CTA walks down rows with a
-// stride so the grid stays a few thousand CTAs and the per-CTA maximum of the
-// correction costs one atomic per CTA.
+// One thread per coarse cell: the (up to) 2x2 fine pixels it is the nearest
+// parent of, each 9/16 of it, 3/16 of its two edge neighbours on the child's
+// side and 1/16 of the diagonal one (coarse indices clamped at the border).
+// mode 0: u = c ? b : P uH;  mode 1: u += c ? 0 : P uH.
 __global__ void __launch_bounds__(256)
 k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
           const uint8_t* __restrict__ c, int w, int h, float* __restrict__ u, int mode,
           unsigned* __restrict__ maxupd) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
-    const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
-    const float* e = uH + ch * nH;
     float amax = 0.f;
-    if (x < w) {
-        const int X = x >> 1;
-        const int Xf = min(max((x & 1) ? X + 1 : X - 1, 0), wH - 1);
-        for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < h;
-             y += gridDim.y * blockDim.y) {
-            const size_t p = (size_t)y * w + x;
-            if (c[p]) {
-                if (mode == 0) u[ch * n + p] = b[ch * n + p];
-                continue;
+    if (X < wH && Y < hH) {
+        const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
+        const float* e = uH + ch * nH;
+        const int Xl = max(X - 1, 0), Xr = min(X + 1, wH - 1);
+        const int Yu = max(Y - 1, 0), Yd = min(Y + 1, hH - 1);
+        const float* ru = e + (size_t)Yu * wH;
+        const float* rc = e + (size_t)Y * wH;
+        const float* rd = e + (size_t)Yd * wH;
+        const float cu_l = ru[Xl], cu_c = ru[X], cu_r = ru[Xr];
+        const float cc_l = rc[Xl], cc_c = rc[X], cc_r = rc[Xr];
+        const float cd_l = rd[Xl], cd_c = rd[X], cd_r = rd[Xr];
+        // vertical blends for the upper (y = 2Y) and lower (y = 2Y+1) child rows
+        const float vu_l = 3.f * cc_l + cu_l, vu_c = 3.f * cc_c + cu_c, vu_r = 3.f * cc_r + cu_r;
+        const float vd_l = 3.f * cc_l + cd_l, vd_c = 3.f * cc_c + cd_c, vd_r = 3.f * cc_r + cd_r;
+        float val[2][2];
+        val[0][0] = (3.f * vu_c + vu_l) * (1.f / 16.f);
+        val[0][1] = (3.f * vu_c + vu_r) * (1.f / 16.f);
+        val[1][0] = (3.f * vd_c + vd_l) * (1.f / 16.f);
+        val[1][1] = (3.f * vd_c + vd_r) * (1.f / 16.f);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = 2 * Y + dy;
+            if (y >= h) continue;
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int x = 2 * X + dx;
+                if (x >= w) continue;
+                const size_t p = (size_t)y * w + x;
+                const float v = val[dy][dx];
+                if (c[p]) {
+                    if (mode == 0) u[ch * n + p] = b[ch * n + p];
+                } else if (mode == 0) {
+                    u[ch * n + p] = v;
+                } else {
+                    u[ch * n + p] += v;
+                    amax = fmaxf(amax, fabsf(v));
+                }
             }
-            const int Y = y >> 1;
-            const int Yf = min(max((y & 1) ? Y + 1 : Y - 1, 0), hH - 1);
-            const float v = (9.f * e[(size_t)Y * wH + X] + 3.f * e[(size_t)Y * wH + Xf] +
-                             3.f * e[(size_t)Yf * wH + X] + e[(size_t)Yf * wH + Xf]) *
-                            (1.f / 16.f);
-            if (mode == 0) u[ch * n + p] = v;
-            else { u[ch * n + p] += v; amax = fmaxf(amax, fabsf(v)); }
         }
     }
     if (maxupd) {
@@ -321,7 +364,9 @@ k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict_
         if (t == 0) {
             float m = 0.f;
             for (int i = 0; i < (int)(blockDim.x * blockDim.y) / 32; ++i) m = fmaxf(m, s_m[i]);
-            if (m > 0.f) atomicMax(maxupd, __float_as_uint(m));
+            // most CTAs see a maximum already at least as large: skip their atomic
+            if (m > __uint_as_float(*(volatile unsigned*)maxupd))
+                atomicMax(maxupd, __float_as_uint(m));
         }
     }
 }
@@ -352,6 +397,11 @@ __device__ __forceinline__ float hi2(f2 a) { return __uint_as_float((unsigned)(a
 __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     f2 d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
@@ -435,6 +485,11 @@ struct WarpTile {
     static constexpr int TH = B + 2;       // tile side with the one-pixel halo
     static constexpr int P = B == 8 ? 12 : B + 2;  // tile pitch: row groups hit distinct banks
     static constexpr int TILE = TH * P;
+    // per-warp shared memory (floats): two halo tiles, the 0/1 keep factors of
+    // every pair (NP x 32 lanes x 2), the row weights (B), then optionally
+    // two right-hand-side tiles (2 x B x B)
+    static constexpr int KEEP = NP * 32 * 2;
+    static constexpr int FIXED = 2 * TILE + KEEP + B;
 };
 
 template <int B>
@@ -449,8 +504,10 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
     static_assert(G * B == 32 && R * G == B && NP * 2 == R, "warp shape");
 
     extern __shared__ float smem[];
-    float* const s_u = smem;               // [2][TH][P]
-    float* const s_b = smem + 2 * TILE;    // [2][B][B], only when rhs_zero == 0
+    float* const s_u = smem;                                 // [2][TH][P]
+    f2* const s_keep = reinterpret_cast<f2*>(smem + 2 * TILE);  // [NP][32] keep factors
+    float* const s_wy = smem + 2 * TILE + WT::KEEP;          // [B] row weights of the block
+    float* const s_b = smem + WT::FIXED;                     // [2][B][B], only when rhs_zero == 0
 
     const int lane = threadIdx.x;
     const int col = lane % B, g = lane / B;
@@ -482,14 +539,21 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
     auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
         if (!zero_in) {
+            // lane l copies tile column l of every row (and column 32 + l for
+            // l < TH - 32); addresses advance by one image row per tile row
             const float* src = u_in + ch * n;
             float* dst = s_u + bs * TILE;
-#pragma unroll 4
-            for (int e = lane; e < TH * TH; e += 32) {
-                const int ty = e / TH, tx = e - ty * TH;
-                const int gy = py0 - 1 + ty, gx = px0 - 1 + tx;
-                const bool ok = gy >= 0 && gy < h && gx >= 0 && gx < w;
-                cp_async4(dst + ty * P + tx, ok ? src + (size_t)gy * w + gx : src, ok);
+            const int gxa = px0 - 1 + lane, gxb = gxa + 32;
+            const bool oka = lane < TH && gxa >= 0 && gxa < w;
+            const bool okb = lane + 32 < TH && gxb < w;
+            const float* row = src + (ptrdiff_t)(py0 - 1) * w;
+#pragma unroll 2
+            for (int ty = 0; ty < TH; ++ty, row += w) {
+                const int gy = py0 - 1 + ty;
+                const bool rok = gy >= 0 && gy < h;
+                if (lane < TH) cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
+                if (lane + 32 < TH) cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src,
+                                              rok && okb);
             }
         }
         if (!rhs_zero) {
@@ -572,6 +636,12 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
             }
             wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                s_keep[k * 32 + lane] = pk(((mb >> k) & 1u) ? 0.f : 1.f,
+                                          ((mb >> (k + NP)) & 1u) ? 0.f : 1.f);
+            if (lane < B) s_wy[lane] = ramp_weight(lane, ky, nby, s, o, inv_o1);
+            __syncwarp();
         }
 
         const float* tu = s_u + buf * TILE;
@@ -592,9 +662,9 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
                     const float dv = (float)((gy > 0) + (gy < h - 1));
                     v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
                 }
-                rv[e] = ((mb >> (k + e * NP)) & 1u) ? 0.f : v;
+                rv[e] = v;
             }
-            r[k] = pk(rv[0], rv[1]);
+            r[k] = mul2(pk(rv[0], rv[1]), s_keep[k * 32 + lane]);
             p[k] = r[k];
             x[k] = 0ull;
             if (k & 1) acc1 = fma2(r[k], r[k], acc1);
@@ -622,10 +692,8 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 f2 nbs = add2(up, dn);
                 nbs = fma2(ml2, left, nbs);
                 nbs = fma2(mr2, right, nbs);
-                f2 qk = fma2(ndg[k], p[k], nbs);  // -(A_i p)
-                const float q0 = ((mb >> k) & 1u) ? 0.f : lo2(qk);
-                const float q1 = ((mb >> (k + NP)) & 1u) ? 0.f : hi2(qk);
-                qk = pk(q0, q1);
+                // -(A_i p), zero on known pixels
+                const f2 qk = mul2(fma2(ndg[k], p[k], nbs), s_keep[k * 32 + lane]);
                 q[k] = qk;
                 if (k & 1) acc1 = fma2(p[k], qk, acc1);
                 else acc0 = fma2(p[k], qk, acc0);
@@ -666,7 +734,7 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 const int ly = g * R + k + e * NP;
                 if (ly >= bh || !colok) continue;
                 const float v = e ? hi2(x[k]) : lo2(x[k]);
-                const float d = wx * ramp_weight(ly, ky, nby, s, o, inv_o1);
+                const float d = wx * s_wy[ly];
                 const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
                 if (d == 1.f) uo[gp] = (zero_in ? 0.f : tu[(ly + 1) * P + col + 1]) + v;
                 else if (d > 0.f) plane[gp] = d * v;
@@ -676,6 +744,269 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
         if (!more) break;
         blk = nblk_;
         ch = nch;
+        buf ^= 1;
+    }
+    if (maxupd) {
+        vmax = warp_max(vmax);
+        if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
+    }
+}
+
+// One ORAS iteration for 32x32 blocks with two warps per block (one per half
+// of the rows), so every lane keeps 8 packed pairs per CG vector instead of
+// 16 and twice as many warps fit on an SM.  Warp wi owns rows 16wi .. 16wi+15
+// of every column; pair k of a lane = rows (16wi + k, 16wi + k + 8).  The row
+// pair at the seam (15 | 16) is exchanged through shared memory: each warp
+// publishes its seam row of r with the r.r partial sum, and rebuilds the
+// partner's seam row of p = r + beta p from it.  Two 64-thread barriers per CG
+// step (p.Ap and r.r).  Everything else as in k_oras_warp.
+struct Tile2W {
+    static constexpr int B = 32, TH = 34, P = 34, TILE = TH * P;
+    // shared floats: two halo tiles, row weights, two rhs tiles (optional)
+    static constexpr int FIXED = 2 * TILE + B;
+};
+
+__global__ void __launch_bounds__(64, 8)
+k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
+          int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
+          int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
+          float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner) {
+    constexpr int B = 32, NP = 8, TH = Tile2W::TH, P = Tile2W::P, TILE = Tile2W::TILE;
+    extern __shared__ float smem[];
+    float* const s_u = smem;                     // [2][TH][P]
+    float* const s_wy = smem + 2 * TILE;         // [B]
+    float* const s_b = smem + Tile2W::FIXED;     // [2][B][B] if rhs_zero == 0
+    __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
+
+    const int t = threadIdx.x;
+    const int lane = t & 31, wi = t >> 5;
+    const int col = lane;
+    const int row0 = 16 * wi;
+    const int s = B - o;
+    const size_t n = (size_t)w * h;
+    const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
+    const int nblk = nbx * nby;
+    auto task_of = [&](int i, int& blk, int& ch) {
+        if (chan_inner) {
+            blk = (int)blockIdx.x + (i / C) * (int)gridDim.x;
+            ch = i % C;
+        } else {
+            const int tt = (int)blockIdx.x + i * (int)gridDim.x;
+            blk = tt / C;
+            ch = tt - blk * C;
+        }
+        return blk < nblk;
+    };
+
+    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
+        const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
+        if (!zero_in) {
+            // thread t copies tile column lane of the rows ty = wi, wi + 2, ...
+            // (and column 32 + lane for lane < 2)
+            const float* src = u_in + ch * n;
+            float* dst = s_u + bs * TILE;
+            const int gxa = px0 - 1 + lane, gxb = gxa + 32;
+            const bool oka = gxa >= 0 && gxa < w;
+            const bool okb = lane < TH - 32 && gxb < w;
+#pragma unroll 2
+            for (int ty = wi; ty < TH; ty += 2) {
+                const int gy = py0 - 1 + ty;
+                const bool rok = gy >= 0 && gy < h;
+                const float* row = src + (ptrdiff_t)gy * w;
+                cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
+                if (lane < TH - 32)
+                    cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
+            }
+        }
+        if (!rhs_zero) {
+            const float* src = rhs + ch * n;
+            float* dst = s_b + bs * B * B;
+            const int gx = px0 + lane;
+#pragma unroll 4
+            for (int ly = wi; ly < B; ly += 2) {
+                const int gy = py0 + ly;
+                const bool ok = gx < w && gy < h;
+                cp_async4(dst + ly * B + lane, ok ? src + (size_t)gy * w + gx : src, ok);
+            }
+        }
+        cp_async_commit();
+        if (blk != have_blk && lane < 16) {
+            const int gy = py0 + row0 + lane;
+            if (gy < h) {
+                const uint32_t* row = mbits + (size_t)gy * wpr + (px0 >> 5);
+                nlo = __ldg(row);
+                nhi = __ldg(row + 1);
+            } else {
+                nlo = nhi = 0xffffffffu;
+            }
+        }
+    };
+
+    int blk, ch;
+    if (!task_of(0, blk, ch)) return;  // block-uniform
+    prefetch(blk, ch, 0, -1);
+    int buf = 0, cur_blk = -1;
+    f2 ndg[NP], keep[NP];
+    f2 ml2 = 0ull, mr2 = 0ull;
+    float wx = 0.f, dh = 0.f;
+    int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
+    float vmax = 0.f;
+
+    for (int i = 0;; ++i) {
+        cp_async_wait_all();
+        __syncthreads();
+        const uint32_t mlo = nlo, mhi = nhi;
+        int nb2, nc2;
+        const bool more = task_of(i + 1, nb2, nc2);
+        if (more) prefetch(nb2, nc2, buf ^ 1, blk);
+
+        if (blk != cur_blk) {
+            cur_blk = blk;
+            kx = blk % nbx;
+            ky = blk / nbx;
+            x0 = kx * s;
+            y0 = ky * s;
+            const int bw = min(B, w - x0);
+            bh = min(B, h - y0);
+            const uint32_t rowm = __funnelshift_r(mlo, mhi, x0 & 31);  // lane < 16: row row0+lane
+            uint32_t mb = 0;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                const uint32_t v = __shfl_sync(kFull, rowm, rr);
+                mb |= ((v >> col) & 1u) << rr;
+            }
+            const int gx = x0 + col;
+            const float hc = (col > 0 ? 1.f : (gx > 0 ? alpha : 0.f)) +
+                             (col + 1 < bw ? 1.f : (gx < w - 1 ? alpha : 0.f));
+            dh = (float)((gx > 0) + (gx < w - 1));
+            const float ml = col > 0 ? 1.f : 0.f, mr = col < B - 1 ? 1.f : 0.f;
+            ml2 = pk(ml, ml);
+            mr2 = pk(mr, mr);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                float vc[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                    vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
+                            (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                }
+                ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
+                keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
+            }
+            wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
+            if (t < B) s_wy[t] = ramp_weight(t, ky, nby, s, o, inv_o1);
+            // s_wy is read only after the barriers of the CG below
+        }
+
+        const float* tu = s_u + buf * TILE;
+        const float* tb = s_b + buf * B * B;
+
+        f2 x[NP], r[NP], p[NP], q[NP];
+        f2 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float rv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                float v = rhs_zero ? 0.f : tb[ly * B + col];
+                if (!zero_in) {
+                    const float* c0 = tu + (ly + 1) * P + col + 1;
+                    const float dv = (float)((gy > 0) + (gy < h - 1));
+                    v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                }
+                rv[e] = v;
+            }
+            r[k] = mul2(pk(rv[0], rv[1]), keep[k]);
+            p[k] = r[k];
+            x[k] = 0ull;
+            if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+            else acc0 = fma2(r[k], r[k], acc0);
+        }
+        acc0 = add2(acc0, acc1);
+        // seam rows: warp 0 publishes its row 15 (hi of pair 7), warp 1 its row 16 (lo of pair 0)
+        s_seam[wi][lane] = wi == 0 ? hi2(r[NP - 1]) : lo2(r[0]);
+        float part = warp_sum(lo2(acc0) + hi2(acc0));
+        if (lane == 0) s_red2[wi] = part;
+        __syncthreads();
+        float rr = s_red2[0] + s_red2[1];
+        float pb = s_seam[wi ^ 1][lane];  // partner's seam row of p
+        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+
+        for (int it = 0; it < iters; ++it) {
+            if (!(rr > rr_stop)) break;  // rr is identical in both warps
+            const f2 pu = wi == 0 ? pk(0.f, lo2(p[NP - 1])) : pk(pb, lo2(p[NP - 1]));
+            const f2 pd = wi == 0 ? pk(hi2(p[0]), pb) : pk(hi2(p[0]), 0.f);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const f2 left = __shfl_up_sync(kFull, p[k], 1);
+                const f2 right = __shfl_down_sync(kFull, p[k], 1);
+                const f2 up = k > 0 ? p[k - 1] : pu;
+                const f2 dn = k < NP - 1 ? p[k + 1] : pd;
+                f2 nbs = add2(up, dn);
+                nbs = fma2(ml2, left, nbs);
+                nbs = fma2(mr2, right, nbs);
+                const f2 qk = mul2(fma2(ndg[k], p[k], nbs), keep[k]);  // -(A_i p), 0 on the mask
+                q[k] = qk;
+                if (k & 1) acc1 = fma2(p[k], qk, acc1);
+                else acc0 = fma2(p[k], qk, acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red1[wi] = part;
+            __syncthreads();
+            const float pq = -(s_red1[0] + s_red1[1]);
+            if (!(pq > 0.f) || pq == INFINITY) break;
+            const float a = __fdividef(rr, pq);
+            const f2 a2 = pk(a, a);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                x[k] = fma2(a2, p[k], x[k]);
+                r[k] = fma2(a2, q[k], r[k]);
+                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+                else acc0 = fma2(r[k], r[k], acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            s_seam[wi][lane] = wi == 0 ? hi2(r[NP - 1]) : lo2(r[0]);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red2[wi] = part;
+            __syncthreads();
+            const float rrn = s_red2[0] + s_red2[1];
+            const float beta = __fdividef(rrn, rr);
+            rr = rrn;
+            const f2 b2 = pk(beta, beta);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
+            pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
+        }
+
+        const int par = (kx & 1) | ((ky & 1) << 1);
+        float* plane = planes + ((size_t)par * C + ch) * n;
+        float* uo = u_out + ch * n;
+        const bool colok = x0 + col < w;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = row0 + k + 8 * e;
+                if (ly >= bh || !colok) continue;
+                const float v = e ? hi2(x[k]) : lo2(x[k]);
+                const float d = wx * s_wy[ly];
+                const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
+                if (d == 1.f) uo[gp] = (zero_in ? 0.f : tu[(ly + 1) * P + col + 1]) + v;
+                else if (d > 0.f) plane[gp] = d * v;
+                if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+            }
+        }
+        if (!more) break;
+        blk = nb2;
+        ch = nc2;
         buf ^= 1;
     }
     if (maxupd) {
@@ -752,6 +1083,45 @@ inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
                 (unsigned)z);
 }
 
+cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
+                           int B, int o, int nbx, int nby, float* u_out, cudaStream_t s);
+
+cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
+                           const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
+                           int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
+                           cudaStream_t s, cudaEvent_t* ev) {
+    constexpr int B = 32;
+    const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
+    const int ntasks = nbx * nby * C;
+    const size_t smem = (size_t)Tile2W::FIXED * sizeof(float) +
+                        (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
+    static int occ[2] = {0, 0};
+    static int nsm = 0;
+    int& oc = occ[rhs_zero ? 0 : 1];
+    if (oc == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_oras_2w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(Tile2W::FIXED * sizeof(float) + 2 * B * B * sizeof(float)));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_2w, 64, smem);
+        if (oc < 1) oc = 1;
+    }
+    const int slots = nsm * oc;
+    const int nblk = nbx * nby;
+    const int chan_inner = nblk >= slots ? 1 : 0;
+    int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
+    if (grid < 1) grid = 1;
+    if (ev) cudaEventRecord(ev[0], s);
+    k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, nbx,
+                                     nby, alpha, iters, rtol2, u_out, planes, maxupd, chan_inner);
+    count();
+    if (ev) cudaEventRecord(ev[1], s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);
+}
+
 template <int B>
 cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                           const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
@@ -759,8 +1129,8 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
                           cudaStream_t s, cudaEvent_t* ev) {
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
-    constexpr int TILE = WarpTile<B>::TILE;
-    const size_t smem = (size_t)2 * TILE * sizeof(float) +
+    constexpr int FIXED = WarpTile<B>::FIXED;
+    const size_t smem = (size_t)FIXED * sizeof(float) +
                         (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
     // persistent warps: as many as fit on the GPU at once
     static int occ[2] = {0, 0};
@@ -771,7 +1141,7 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_oras_warp<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * TILE * sizeof(float) + 2 * B * B * sizeof(float)));
+                             (int)(FIXED * sizeof(float) + 2 * B * B * sizeof(float)));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_warp<B>, 32, smem);
         if (oc < 1) oc = 1;
     }
@@ -788,6 +1158,12 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);
+}
+
+cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
+                           int B, int o, int nbx, int nby, float* u_out, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
     // Overlap 2 gives 0/1 weights: no pixel is shared, the combine is empty.
     const int nsh = shared_per_seam(o);
     if (nsh > 0 && nby > 1) {
@@ -901,10 +1277,11 @@ cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, do
 
 cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const uint8_t* c,
                             int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s) {
+    (void)c;  // children of an unmasked coarse cell are unknown by construction
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    k_restrict<<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, c, w, h, cH, rH, wH, hH);
+    k_restrict<<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
     count();
     return cudaGetLastError();
 }
@@ -914,14 +1291,8 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    dim3 grid = grid2(w, h, blk, C);
-    // about 16 CTAs of 256 threads per SM in total; each walks rows with a stride
-    const unsigned target = 152u * 16u;
-    const unsigned per_row = grid.x * grid.z;
-    unsigned gy = (target + per_row - 1) / per_row;
-    if (gy < 1) gy = 1;
-    if (gy < grid.y) grid.y = gy;
-    k_prolong<<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode, mode == 1 ? maxupd : nullptr);
+    k_prolong<<<grid2(wH, hH, blk, C), blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
+                                                    mode == 1 ? maxupd : nullptr);
     count();
     return cudaGetLastError();
 }
@@ -953,8 +1324,8 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
     const int wpr = mask_words_per_row(w);
     switch (B) {
         case 32:
-            return launch_oras_t<32>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                     iters, rtol2, u_out, planes, maxupd, s, ev);
+            return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
+                                  iters, rtol2, u_out, planes, maxupd, s, ev);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev);
