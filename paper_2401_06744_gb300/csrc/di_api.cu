@@ -167,8 +167,8 @@ di_status ensure_workspace(di_ctx* ctx, int w, int h, int C) {
     const int L = num_levels(nw, nh, ctx->cfg.block);
     cudaError_t e = cudaMalloc(&ctx->pool, pool_bytes(nw, nh, nc, L));
     if (e != cudaSuccess) { ctx->pool = nullptr; return cuda_fail(ctx, e, "cudaMalloc(pool)"); }
-    const size_t n0 = (size_t)nw * nh;
-    e = cudaMalloc(&ctx->planes, 4 * n0 * nc * sizeof(float));
+    e = cudaMalloc(&ctx->planes,
+                   oras_scratch_floats(nw, nh, nc, ctx->cfg.block, ctx->cfg.overlap) * sizeof(float));
     if (e != cudaSuccess) { free_workspace(ctx); return cuda_fail(ctx, e, "cudaMalloc(planes)"); }
     ctx->partials_cap = residual_partials_per_channel(nw, nh) * nc;
     e = cudaMalloc(&ctx->partials, ctx->partials_cap * sizeof(double));
@@ -348,9 +348,9 @@ di_status di_plan(const di_config* cfg, int width, int height, int channels,
         coarse_dims(lw, lh, &lw, &lh);
     }
     out->local_problems = (long long)out->blocks_x[0] * out->blocks_y[0] * channels;
-    const size_t n0 = (size_t)width * height;
     out->workspace_bytes = (long long)(pool_bytes(width, height, channels, L) +
-                                       4 * n0 * channels * sizeof(float) +
+                                       oras_scratch_floats(width, height, channels, c.block,
+                                                           c.overlap) * sizeof(float) +
                                        residual_partials_per_channel(width, height) * channels *
                                            sizeof(double));
     return DI_OK;

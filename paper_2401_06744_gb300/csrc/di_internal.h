@@ -10,6 +10,12 @@ namespace di {
 
 constexpr int kMaxChannels = 4;
 
+inline int axis_blocks_decl(int n, int B, int o) {
+    const int s = B - o;
+    const int nb = (n - o + s - 1) / s;
+    return nb < 1 ? 1 : nb;
+}
+
 // Kernels enqueued by the launch wrappers below (process-wide counter).
 long long launch_count();
 constexpr int kMaxLevels = 24;
@@ -62,7 +68,15 @@ cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C,
 // Bit-packed mask (see mask_words_per_row) of c.
 cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cudaStream_t s);
 
-// One ORAS iteration u_in -> u_out (planes: 4*C*w*h floats of workspace;
+// Floats of ORAS scratch for an image of w x h x C: four parity planes of
+// pixels shared along y, then the compact strips of pixels shared along x only.
+inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
+    const int nsh = o == 1 ? 1 : (o > 2 ? o - 2 : 0);
+    const int nbx = axis_blocks_decl(w, B, o);
+    return 4 * (size_t)w * h * C + 2 * (size_t)C * (nbx > 1 ? nbx - 1 : 0) * h * (nsh > 0 ? nsh : 1);
+}
+
+// One ORAS iteration u_in -> u_out (planes: oras_scratch_floats of workspace;
 // mbits: the packed mask of this level).  Each local CG runs `iters` steps or
 // until r.r <= max(rtol2, 1e-14) * (r.r)_0.  max |v_i| over pixels with
 // nonzero weight is folded into *maxupd (nullable).

@@ -63,11 +63,20 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Block index k = min(g / s, nb - 1) without an integer division: a float
+// estimate from the reciprocal, corrected by one step either way.
+__device__ __forceinline__ int block_of(int g, int s, float inv_s, int nb) {
+    int k = __float2int_rd(((float)g + 0.5f) * inv_s);
+    if (k * s > g) --k;
+    else if ((k + 1) * s <= g) ++k;
+    return k > nb - 1 ? nb - 1 : k;
+}
+
 // Blocks with nonzero weight at global coordinate g along one axis: returns
 // 1 (k0) or 2 (k0 < k1).
-__device__ __forceinline__ int axis_contrib(int g, int s, int o, int nb, int& k0, int& k1) {
-    int k = g / s;
-    if (k > nb - 1) k = nb - 1;
+__device__ __forceinline__ int axis_contrib(int g, int s, int o, int nb, int& k0, int& k1,
+                                            float inv_s) {
+    const int k = block_of(g, s, inv_s, nb);
     const int j = g - k * s;
     k1 = k;
     if (k > 0 && j < o) {
@@ -426,6 +435,12 @@ __device__ __forceinline__ float ramp_weight(int l, int k, int nb, int s, int o,
     return wgt;
 }
 
+// Pixels shared by two blocks along one axis are the open interior of each
+// overlap: local offsets 1 .. o-2 after the seam (o >= 3), or the single
+// overlap pixel when o = 1.  nsh is their count per seam.
+__host__ __device__ __forceinline__ int shared_per_seam(int o) { return o == 1 ? 1 : (o > 2 ? o - 2 : 0); }
+__host__ __device__ __forceinline__ int shared_first(int o) { return o == 1 ? 0 : 1; }
+
 // ---- asynchronous global -> shared copies (4-byte, zero fill) ----------------
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
@@ -723,6 +738,20 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
 
         // u_out = u_in + sum_i R_i^T D_i v_i: weight-1 pixels directly, shared
         // pixels through the parity planes.
+        // x-only shared pixels go to the compact seam strips that follow the
+        // four parity planes: strip[side][ch][seam - 1][y][j], side 0 = left block
+        const int nsh = shared_per_seam(o), first = shared_first(o);
+        int sx_seam = -1, sx_side = 0, sx_j = 0;
+        if (kx > 0 && col >= first && col < first + nsh) {
+            sx_seam = kx; sx_side = 1; sx_j = col - first;
+        } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
+            sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
+        }
+        float* strip = sx_seam > 0
+                           ? planes + 4 * (size_t)C * n +
+                                 (((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h) *
+                                     nsh + sx_j
+                           : planes;
         const int par = (kx & 1) | ((ky & 1) << 1);
         float* plane = planes + ((size_t)par * C + ch) * n;
         float* uo = u_out + ch * n;
@@ -736,8 +765,22 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 const float v = e ? hi2(x[k]) : lo2(x[k]);
                 const float d = wx * s_wy[ly];
                 const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
-                if (d == 1.f) uo[gp] = (zero_in ? 0.f : tu[(ly + 1) * P + col + 1]) + v;
-                else if (d > 0.f) plane[gp] = d * v;
+                // the first contributor of a shared pixel (smallest block
+                // index along each shared axis) also carries u_in, so the
+                // combine passes only add parked values
+                const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
+                if (d == 1.f) {
+                    uo[gp] = uold + v;
+                } else if (d > 0.f) {
+                    const float wyr = s_wy[ly];
+                    const bool xfirst = sx_seam < 0 || sx_side == 0;  // no left partner on x
+                    if (wyr < 1.f) {
+                        const bool yfirst = ly >= s;  // upper block of its row overlap
+                        plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
+                    } else {
+                        strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
+                    }
+                }
                 if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
             }
         }
@@ -785,6 +828,11 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     const int s = B - o;
     const size_t n = (size_t)w * h;
     const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
+    // Task sequence of this CTA.  chan_inner: blocks blockIdx.x, +gridDim.x,
+    // ... each with all channels back to back (the CTAs running together cover
+    // a contiguous band of blocks, so halo re-reads hit L2, and a block's mask
+    // bits and operator serve all its channels); otherwise (fewer blocks than
+    // CTA slots) tasks blockIdx.x, +gridDim.x, ... of the (block, channel) list.
     const int nblk = nbx * nby;
     auto task_of = [&](int i, int& blk, int& ch) {
         if (chan_inner) {
@@ -797,7 +845,6 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         }
         return blk < nblk;
     };
-
     uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
     auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
@@ -986,6 +1033,20 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
         }
 
+        // x-only shared pixels go to the compact seam strips that follow the
+        // four parity planes: strip[side][ch][seam - 1][y][j], side 0 = left block
+        const int nsh = shared_per_seam(o), first = shared_first(o);
+        int sx_seam = -1, sx_side = 0, sx_j = 0;
+        if (kx > 0 && col >= first && col < first + nsh) {
+            sx_seam = kx; sx_side = 1; sx_j = col - first;
+        } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
+            sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
+        }
+        float* strip = sx_seam > 0
+                           ? planes + 4 * (size_t)C * n +
+                                 (((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h) *
+                                     nsh + sx_j
+                           : planes;
         const int par = (kx & 1) | ((ky & 1) << 1);
         float* plane = planes + ((size_t)par * C + ch) * n;
         float* uo = u_out + ch * n;
@@ -999,8 +1060,22 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 const float v = e ? hi2(x[k]) : lo2(x[k]);
                 const float d = wx * s_wy[ly];
                 const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
-                if (d == 1.f) uo[gp] = (zero_in ? 0.f : tu[(ly + 1) * P + col + 1]) + v;
-                else if (d > 0.f) plane[gp] = d * v;
+                // the first contributor of a shared pixel (smallest block
+                // index along each shared axis) also carries u_in, so the
+                // combine passes only add parked values
+                const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
+                if (d == 1.f) {
+                    uo[gp] = uold + v;
+                } else if (d > 0.f) {
+                    const float wyr = s_wy[ly];
+                    const bool xfirst = sx_seam < 0 || sx_side == 0;  // no left partner on x
+                    if (wyr < 1.f) {
+                        const bool yfirst = ly >= s;  // upper block of its row overlap
+                        plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
+                    } else {
+                        strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
+                    }
+                }
                 if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
             }
         }
@@ -1015,67 +1090,60 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     }
 }
 
-// Pixels shared by two blocks along one axis are the open interior of each
-// overlap: local offsets 1 .. o-2 after the seam (o >= 3), or the single
-// overlap pixel when o = 1.  nsh is their count per seam.
-__host__ __device__ __forceinline__ int shared_per_seam(int o) { return o == 1 ? 1 : (o > 2 ? o - 2 : 0); }
-__host__ __device__ __forceinline__ int shared_first(int o) { return o == 1 ? 0 : 1; }
 
-// u_out = u_in + sum of the parked contributions at one shared pixel; kx0/kx1
-// (nx of them) and ky0/ky1 (ny) are the blocks with nonzero weight there.
-__device__ __forceinline__ void combine_px(const float* __restrict__ u_in, int zero_in,
-                                           const float* __restrict__ planes, float* __restrict__ u_out,
-                                           size_t n, int C, int ch, size_t gp, int nx, int kx0,
-                                           int kx1, int ny, int ky0, int ky1) {
-    float acc = 0.f;
-    for (int a = 0; a < ny; ++a) {
-        const int ky = a ? ky1 : ky0;
-        for (int bb = 0; bb < nx; ++bb) {
-            const int kx = bb ? kx1 : kx0;
-            const int par = (kx & 1) | ((ky & 1) << 1);
-            acc += planes[((size_t)par * C + ch) * n + gp];
-        }
-    }
-    const float uo = zero_in ? 0.f : u_in[ch * n + gp];
-    u_out[ch * n + gp] = uo + acc;
-}
-
-// Shared rows (the interior rows of every horizontal overlap), full width.
+// Shared rows (the interior rows of every horizontal overlap), full width:
+// contributions from the parity planes (two block rows; two block columns
+// where the pixel is also shared along x).
 __global__ void __launch_bounds__(256)
 k_combine_rows(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
-               int w, int h, int s, int o, int nbx, int nby, float* __restrict__ u_out) {
+               int w, int h, int s, int o, int nbx, int nby, float inv_s,
+               float* __restrict__ u_out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ch = blockIdx.z, C = gridDim.z;
     if (x >= w) return;
     const int nsh = shared_per_seam(o);
-    const int seam = blockIdx.y / nsh + 1;             // vertical block index ky of the lower block
+    const int seam = blockIdx.y / nsh + 1;             // lower block row of the overlap
     const int y = seam * s + shared_first(o) + (int)blockIdx.y % nsh;
     if (y >= h) return;
     int kx0, kx1;
-    const int nx = axis_contrib(x, s, o, nbx, kx0, kx1);
-    combine_px(u_in, zero_in, planes, u_out, (size_t)w * h, C, ch, (size_t)y * w + x, nx, kx0,
-               kx1, 2, seam - 1, seam);
+    const int nx = axis_contrib(x, s, o, nbx, kx0, kx1, inv_s);
+    const size_t n = (size_t)w * h, gp = (size_t)y * w + x;
+    const size_t cs = (size_t)C * n;
+    const float* pl = planes + ch * n + gp;
+    const int pu = (seam - 1) & 1, pdn = seam & 1;  // y parity of the upper / lower block
+    // the first term (upper-left block) already carries u_in
+    float acc = pl[(size_t)((kx0 & 1) | (pu << 1)) * cs];
+    if (nx == 2) acc += pl[(size_t)((kx1 & 1) | (pu << 1)) * cs];
+    acc += pl[(size_t)((kx0 & 1) | (pdn << 1)) * cs];
+    if (nx == 2) acc += pl[(size_t)((kx1 & 1) | (pdn << 1)) * cs];
+    u_out[ch * n + gp] = acc;
 }
 
-// Shared columns (interior columns of every vertical overlap) in the rows that
-// are not shared along y; one thread per (row, strip column), columns fastest.
-__global__ void __launch_bounds__(256)
+// Pixels shared along x only: one thread per (row, seam) adds the two
+// contiguous strip entries of the left and right block.
+__global__ void __launch_bounds__(128)
 k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
-               int w, int h, int s, int o, int nbx, int nby, float* __restrict__ u_out) {
-    const int nsh = shared_per_seam(o);
-    const int ncols = (nbx - 1) * nsh;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+               int w, int h, int s, int o, int nbx, int nby, float inv_s,
+               float* __restrict__ u_out) {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    const int seam = (int)blockIdx.y + 1;
     const int ch = blockIdx.z, C = gridDim.z;
-    if (idx >= (long long)ncols * h) return;
-    const int y = (int)(idx / ncols), ci = (int)(idx % ncols);
+    if (y >= h) return;
     int ky0, ky1;
-    const int ny = axis_contrib(y, s, o, nby, ky0, ky1);
-    if (ny == 2) return;  // handled by k_combine_rows
-    const int seam = ci / nsh + 1;
-    const int x = seam * s + shared_first(o) + ci % nsh;
-    if (x >= w) return;
-    combine_px(u_in, zero_in, planes, u_out, (size_t)w * h, C, ch, (size_t)y * w + x, 2,
-               seam - 1, seam, 1, ky0, ky1);
+    if (axis_contrib(y, s, o, nby, ky0, ky1, inv_s) == 2) return;  // shared row: k_combine_rows
+    const int nsh = shared_per_seam(o);
+    const size_t n = (size_t)w * h;
+    const float* strips = planes + 4 * (size_t)C * n;
+    const size_t side = (size_t)C * (nbx - 1) * h * nsh;
+    const float* L = strips + (((size_t)ch * (nbx - 1) + (seam - 1)) * h + y) * nsh;
+    const float* R = L + side;
+    const int xb = seam * s + shared_first(o);
+    const size_t rowp = (size_t)y * w;
+    for (int j = 0; j < nsh; ++j) {  // L (left block) already carries u_in
+        const int x = xb + j;
+        if (x >= w) break;
+        u_out[ch * n + rowp + x] = L[j] + R[j];
+    }
 }
 
 inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
@@ -1093,19 +1161,27 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     constexpr int B = 32;
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
-    const size_t smem = (size_t)Tile2W::FIXED * sizeof(float) +
-                        (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
-    static int occ[2] = {0, 0};
+    const size_t smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) *
+                        sizeof(float);
+    // occupancy per shared-memory size (cached; sizes repeat across calls)
     static int nsm = 0;
-    int& oc = occ[rhs_zero ? 0 : 1];
-    if (oc == 0) {
+    static size_t occ_key[8] = {};
+    static int occ_val[8] = {};
+    if (nsm == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_oras_2w, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(Tile2W::FIXED * sizeof(float) + 2 * B * B * sizeof(float)));
+        const size_t mx = ((size_t)Tile2W::FIXED + (size_t)2 * B * B) * sizeof(float);
+        cudaFuncSetAttribute(k_oras_2w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    }
+    int oc = 0;
+    for (int i = 0; i < 8; ++i)
+        if (occ_key[i] == smem) oc = occ_val[i];
+    if (oc == 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_2w, 64, smem);
         if (oc < 1) oc = 1;
+        for (int i = 0; i < 8; ++i)
+            if (occ_key[i] == 0) { occ_key[i] = smem; occ_val[i] = oc; break; }
     }
     const int slots = nsm * oc;
     const int nblk = nbx * nby;
@@ -1166,18 +1242,20 @@ cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w,
     cudaError_t e = cudaSuccess;
     // Overlap 2 gives 0/1 weights: no pixel is shared, the combine is empty.
     const int nsh = shared_per_seam(o);
+    const int sb = B - o;
+    const float inv_s = 1.f / (float)sb;
     if (nsh > 0 && nby > 1) {
         dim3 grid_r((unsigned)((w + 255) / 256), (unsigned)((nby - 1) * nsh), (unsigned)C);
-        k_combine_rows<<<grid_r, 256, 0, s>>>(u_in, zero_in, planes, w, h, B - o, o, nbx, nby,
+        k_combine_rows<<<grid_r, 256, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby, inv_s,
                                              u_out);
         count();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (nsh > 0 && nbx > 1) {
-        const long long cnt = (long long)(nbx - 1) * nsh * h;
-        dim3 grid_c((unsigned)((cnt + 255) / 256), 1, (unsigned)C);
-        k_combine_cols<<<grid_c, 256, 0, s>>>(u_in, zero_in, planes, w, h, B - o, o, nbx, nby,
+    const int nseams = nbx - 1;
+    if (nsh > 0 && nbx > 1 && nseams > 0) {
+        dim3 grid_c((unsigned)((h + 127) / 128), (unsigned)nseams, (unsigned)C);
+        k_combine_cols<<<grid_c, 128, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby, inv_s,
                                              u_out);
         count();
         e = cudaGetLastError();
