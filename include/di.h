@@ -152,6 +152,70 @@ const char *di_status_string(di_status s);
 const char *di_last_error(const di_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Batched and served decoding.  The paper decodes one image at a time; these
+ * schedule many di_inpaint calls over a pool of worker slots, each with its
+ * own context (resident pyramids and workspace), CUDA stream and host thread,
+ * so frames overlap on the GPU.  A frame's result does not depend on what
+ * else runs: it is bit-identical to decoding it alone.
+ * ------------------------------------------------------------------------ */
+
+/* One image of a batch: device pointers as for di_inpaint; status and cycles
+ * are written back. */
+typedef struct {
+    const float *f;
+    const uint8_t *c;
+    int width, height, channels;
+    float tol;
+    float *u;
+    int status; /* out: di_status of this image */
+    int cycles; /* out: V-cycles used */
+} di_image;
+
+/* Decode n images with up to `concurrency` slots (0 = 4), largest first.
+ * The work starts after what is already queued on `stream` and the call
+ * returns when every image is done (`stream` then also waits for it).
+ * Returns DI_OK, or the first non-OK image status. */
+di_status di_inpaint_batch(const di_config *cfg, int device, di_image *imgs, int n,
+                           int concurrency, void *stream);
+
+/* Time every (block, overlap) pair of the given lists on the sample images
+ * (`reps` timed passes after one warm-up pass, CUDA events) and return the
+ * fastest configuration whose decodes all converge, with its mean time per
+ * pass.  Pairs that are not valid configurations are skipped.  Returns
+ * DI_ERR_NOT_CONVERGED if no pair qualifies. */
+di_status di_autotune(const di_config *base, int device, const di_image *sample, int n,
+                      const int *blocks, int nblocks, const int *overlaps, int noverlaps,
+                      int reps, di_config *best, double *best_ms);
+
+/* Serving loop: requests with HOST buffers (f, c in; u out) are queued FIFO
+ * and started on a free slot once their device footprint (di_plan workspace
+ * plus device copies of f, c, u) fits within `mem_budget` bytes next to the
+ * requests in flight (0 = no limit; a lone request always starts).  Each
+ * slot copies its request in, decodes and copies the result out on its own
+ * stream. */
+typedef struct di_server di_server;
+
+typedef struct {
+    int status;               /* di_status of the request */
+    int cycles;               /* V-cycles used */
+    double latency_ms;        /* submit to completion */
+    double queue_ms;          /* submit to start */
+    long long footprint_bytes; /* device bytes charged against the budget */
+} di_request_info;
+
+di_status di_server_create(const di_config *cfg, int device, int slots, long long mem_budget,
+                           di_server **out);
+/* Queue one request; the host buffers must stay valid until di_server_wait
+ * returns for its ticket. */
+di_status di_server_submit(di_server *srv, const float *f, const uint8_t *c, int width,
+                           int height, int channels, float tol, float *u, long long *ticket);
+/* Block until the request finished; fills *info (nullable).  Each ticket can
+ * be waited for once. */
+di_status di_server_wait(di_server *srv, long long ticket, di_request_info *info);
+/* Finish the queued requests, stop the workers and free everything. */
+void di_server_destroy(di_server *srv);
+
+/* ------------------------------------------------------------------------
  * Single steps of the path.  Each runs one kernel (or one kernel pair) of the
  * solver on caller buffers; di_inpaint composes them.  They exist so each step
  * can be checked on its own.

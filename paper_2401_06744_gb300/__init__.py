@@ -14,8 +14,8 @@ from ._lib import (  # noqa: F401
     CUDA_ERROR, EMPTY_MASK, INVALID_ARG, NOT_CONVERGED, OK, OOM, STOP_ERROR_ESTIMATE,
     STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
     exported_symbols, load, mask_downsample, plan, prolong, residual_norm_noalloc,
-    restrict_residual, status_string, values_downsample)
+    restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server)
 
 __all__ = ["Context", "DiError", "load", "plan", "mask_downsample", "values_downsample",
-           "residual_norm_noalloc",
+           "residual_norm_noalloc", "inpaint_batch", "autotune", "Server",
            "restrict_residual", "prolong", "status_string", "exported_symbols", "LIB_PATH"]

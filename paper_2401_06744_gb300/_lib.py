@@ -50,6 +50,18 @@ class di_profile(ctypes.Structure):
                 ("oras_l0_cg_steps", ctypes.c_longlong), ("reserved", ctypes.c_longlong * 4)]
 
 
+class di_image(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_void_p), ("c", ctypes.c_void_p), ("width", ctypes.c_int),
+                ("height", ctypes.c_int), ("channels", ctypes.c_int), ("tol", ctypes.c_float),
+                ("u", ctypes.c_void_p), ("status", ctypes.c_int), ("cycles", ctypes.c_int)]
+
+
+class di_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_longlong)]
+
+
 class DiError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(msg)
@@ -71,6 +83,16 @@ _SIGS = {
     "di_get_stats": (_I, [_P, ctypes.POINTER(di_stats)]),
     "di_get_profile": (_I, [_P, ctypes.POINTER(di_profile)]),
     "di_reset_profile": (_I, [_P]),
+    "di_inpaint_batch": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I, _I,
+                              _P]),
+    "di_autotune": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I,
+                         ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I,
+                         ctypes.POINTER(di_config), ctypes.POINTER(ctypes.c_double)]),
+    "di_server_create": (_I, [ctypes.POINTER(di_config), _I, _I, ctypes.c_longlong,
+                              ctypes.POINTER(_P)]),
+    "di_server_submit": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, ctypes.POINTER(ctypes.c_longlong)]),
+    "di_server_wait": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(di_request_info)]),
+    "di_server_destroy": (None, [_P]),
     "di_status_string": (ctypes.c_char_p, [_I]),
     "di_last_error": (ctypes.c_char_p, [_P]),
     "di_mask_downsample": (_I, [_P, _I, _I, _P, _P]),
@@ -319,3 +341,105 @@ def prolong(uH, c, mode, b=None, u=None, stream=None):
     _check(load().di_prolong(uH3.data_ptr(), bp, c.data_ptr(), W, H, C, out.data_ptr(),
                              int(mode), _stream(stream)))
     return out
+
+
+# -- batched and served decoding ---------------------------------------------
+
+def _images(items):
+    """items: iterable of (f, c, tol[, out]) with CUDA tensors -> (array, outputs)."""
+    items = list(items)
+    arr = (di_image * max(1, len(items)))()
+    outs = []
+    for i, it in enumerate(items):
+        f, c, tol = it[0], it[1], it[2]
+        f3, c2 = _img(f, "f"), _mask(c)
+        u = it[3] if len(it) > 3 and it[3] is not None else torch.empty_like(f3)
+        C, H, W = f3.shape
+        arr[i] = di_image(f3.data_ptr(), c2.data_ptr(), W, H, C, float(tol), u.data_ptr(), 0, 0)
+        outs.append(u)
+    return arr, outs
+
+
+def inpaint_batch(items, device=None, concurrency=0, stream=None, **config):
+    """Decode a list of (f, c, tol) on one GPU with overlapping worker slots.
+    Returns (outputs, statuses, cycles)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    cfg = make_config(**config)
+    arr, outs = _images(items)
+    n = len(outs)
+    load().di_inpaint_batch(ctypes.byref(cfg), int(device), arr, n, int(concurrency),
+                            _stream(stream))
+    return outs, [arr[i].status for i in range(n)], [arr[i].cycles for i in range(n)]
+
+
+def autotune(items, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=2, device=None, **config):
+    """Fastest converging (block, overlap) on the sample (f, c, tol) list:
+    returns (config dict, ms per pass)."""
+    if device is None:
+        device = torch.cuda.current_device()
+    base = make_config(**config)
+    arr, _ = _images(items)
+    bl = (ctypes.c_int * len(blocks))(*blocks)
+    ov = (ctypes.c_int * len(overlaps))(*overlaps)
+    best = di_config()
+    ms = ctypes.c_double()
+    _check(load().di_autotune(ctypes.byref(base), int(device), arr, len(items), bl, len(blocks),
+                              ov, len(overlaps), int(reps), ctypes.byref(best), ctypes.byref(ms)))
+    return {k: getattr(best, k) for k, _ in di_config._fields_ if k != "reserved"}, ms.value
+
+
+class Server:
+    """Serving loop over host buffers (di_server_*): submit numpy arrays, wait
+    for the result.  Requests overlap on the GPU across `slots` worker slots and
+    are admitted by device footprint within `mem_budget` bytes (0 = unlimited)."""
+
+    def __init__(self, slots=4, mem_budget=0, device=None, **config):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.config = make_config(**config)
+        h = _P()
+        self._h = None
+        _check(load().di_server_create(ctypes.byref(self.config), int(device), int(slots),
+                                       int(mem_budget), ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, f, c, tol=0.05):
+        import numpy as np
+
+        f = np.ascontiguousarray(f, dtype=np.float32)
+        if f.ndim == 2:
+            f = f[None]
+        c = np.ascontiguousarray(c, dtype=np.uint8)
+        C, H, W = f.shape
+        u = np.empty_like(f)
+        t = ctypes.c_longlong()
+        _check(load().di_server_submit(self._h, f.ctypes.data, c.ctypes.data, W, H, C, float(tol),
+                                       u.ctypes.data, ctypes.byref(t)))
+        self._live[t.value] = (f, c, u)
+        return t.value
+
+    def wait(self, ticket):
+        info = di_request_info()
+        st = load().di_server_wait(self._h, int(ticket), ctypes.byref(info))
+        f, c, u = self._live.pop(ticket)
+        return u, {"status": st, "cycles": info.cycles, "latency_ms": info.latency_ms,
+                   "queue_ms": info.queue_ms, "footprint_bytes": info.footprint_bytes}
+
+    def close(self):
+        if self._h:
+            load().di_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

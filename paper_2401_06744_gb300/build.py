@@ -18,10 +18,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdi.so")
-SOURCES = ["di_kernels.cu", "di_api.cu"]
+SOURCES = ["di_kernels.cu", "di_api.cu", "di_serve.cu"]
 HEADERS = [os.path.join(CSRC, "di_internal.h"), os.path.join(ROOT, "include", "di.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "-Xcompiler", "-pthread",
          "-I", os.path.join(ROOT, "include")]
 
 
@@ -63,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         raise RuntimeError("nvcc failed: " + " | ".join(" ".join(c) for c in failed))
     if force or procs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

@@ -1164,6 +1164,8 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     const size_t smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) *
                         sizeof(float);
     // occupancy per shared-memory size (cached; sizes repeat across calls)
+    static std::mutex occ_mu;
+    std::lock_guard<std::mutex> occ_lock(occ_mu);
     static int nsm = 0;
     static size_t occ_key[8] = {};
     static int occ_val[8] = {};
@@ -1209,6 +1211,8 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     const size_t smem = (size_t)FIXED * sizeof(float) +
                         (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
     // persistent warps: as many as fit on the GPU at once
+    static std::mutex occ_mu;
+    std::lock_guard<std::mutex> occ_lock(occ_mu);
     static int occ[2] = {0, 0};
     static int nsm = 0;
     int& oc = occ[rhs_zero ? 0 : 1];

@@ -1,0 +1,411 @@
+// Batched decoding, the block-size / overlap autotuner and the serving loop,
+// on top of di_inpaint.  Host code only: every decode still runs the library's
+// kernels; this file schedules them.
+//
+// Concurrency model: a pool of worker slots, each with its own decoder
+// context (so its pyramids and ORAS workspace stay resident between frames),
+// its own non-blocking CUDA stream and its own host thread.  A decode blocks
+// its thread once per V-cycle for the stop test, so several slots keep the GPU
+// busy with overlapping frames: the kernels of different frames interleave on
+// the device.  Every frame's arithmetic is independent of the others, so a
+// frame decoded in a batch or under load is bit-identical to the same frame
+// decoded alone.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/di.h"
+#include "di_internal.h"
+
+namespace {
+
+struct Slot {
+    di_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+di_status make_slot(const di_config* cfg, int device, Slot* s) {
+    if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    di_status st = di_create(cfg, device, &s->ctx);
+    if (st != DI_OK) return st;
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess)
+        return DI_ERR_CUDA;
+    return DI_OK;
+}
+
+void free_slot(Slot* s) {
+    if (s->done) cudaEventDestroy(s->done);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    di_destroy(s->ctx);
+    *s = Slot();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Batched decoding
+// ---------------------------------------------------------------------------
+
+extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image* imgs, int n,
+                                      int concurrency, void* stream) {
+    if (!imgs || n < 0 || concurrency < 0) return DI_ERR_INVALID_ARG;
+    if (n == 0) return DI_OK;
+    for (int i = 0; i < n; ++i) {
+        const di_image& im = imgs[i];
+        if (!im.f || !im.c || !im.u || im.width < 1 || im.height < 1 || im.channels < 1 ||
+            im.channels > di::kMaxChannels || !(im.tol > 0.f))
+            return DI_ERR_INVALID_ARG;
+    }
+    int P = concurrency > 0 ? concurrency : 4;
+    if (P > n) P = n;
+    if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    // work starts after everything already queued on the caller's stream
+    cudaEvent_t start;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return DI_ERR_CUDA;
+    cudaEventRecord(start, caller);
+
+    std::vector<Slot> slots(P);
+    di_status st = DI_OK;
+    for (int k = 0; k < P && st == DI_OK; ++k) st = make_slot(cfg, device, &slots[k]);
+    if (st != DI_OK) {
+        for (auto& s : slots) free_slot(&s);
+        cudaEventDestroy(start);
+        return st;
+    }
+    // largest images first: better packing of the slots
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)imgs[a].width * imgs[a].height * imgs[a].channels >
+               (long long)imgs[b].width * imgs[b].height * imgs[b].channels;
+    });
+    std::atomic<int> next{0};
+    auto worker = [&](int k) {
+        Slot& s = slots[k];
+        cudaSetDevice(device);
+        cudaStreamWaitEvent(s.stream, start, 0);
+        for (;;) {
+            const int j = next.fetch_add(1);
+            if (j >= n) break;
+            di_image& im = imgs[order[j]];
+            im.status = di_inpaint(s.ctx, im.f, im.c, im.width, im.height, im.channels, im.tol,
+                                   im.u, s.stream);
+            di_stats ss;
+            di_get_stats(s.ctx, &ss);
+            im.cycles = ss.cycles;
+        }
+        cudaEventRecord(s.done, s.stream);
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < P; ++k) th.emplace_back(worker, k);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (auto& s : slots) cudaStreamWaitEvent(caller, s.done, 0);
+    cudaStreamSynchronize(caller);
+    for (auto& s : slots) free_slot(&s);
+    cudaEventDestroy(start);
+    di_status worst = DI_OK;
+    for (int i = 0; i < n; ++i)
+        if (imgs[i].status != DI_OK && worst == DI_OK) worst = (di_status)imgs[i].status;
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner over block size and overlap
+// ---------------------------------------------------------------------------
+
+extern "C" di_status di_autotune(const di_config* base, int device, const di_image* sample, int n,
+                                 const int* blocks, int nblocks, const int* overlaps,
+                                 int noverlaps, int reps, di_config* best, double* best_ms) {
+    if (!sample || n < 1 || !best || !blocks || nblocks < 1 || !overlaps || noverlaps < 1 ||
+        reps < 1)
+        return DI_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    di_config b;
+    std::memset(&b, 0, sizeof b);
+    if (base) b = *base;
+    double best_t = 1e300;
+    bool found = false;
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return DI_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int bi = 0; bi < nblocks; ++bi) {
+        for (int oi = 0; oi < noverlaps; ++oi) {
+            di_config c = b;
+            c.block = blocks[bi];
+            c.overlap = overlaps[oi];
+            di_plan_info plan;
+            if (di_plan(&c, 1, 1, 1, &plan) != DI_OK) continue;  // invalid (B, o) pair
+            di_ctx* ctx = nullptr;
+            if (di_create(&c, device, &ctx) != DI_OK) continue;
+            bool ok = true;
+            // warm-up (allocates the workspace), then timed repetitions
+            for (int i = 0; i < n && ok; ++i)
+                ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width, sample[i].height,
+                                sample[i].channels, sample[i].tol, sample[i].u, s) == DI_OK;
+            double t = 0.0;
+            for (int r = 0; r < reps && ok; ++r) {
+                cudaEventRecord(e0, s);
+                for (int i = 0; i < n && ok; ++i)
+                    ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width,
+                                    sample[i].height, sample[i].channels, sample[i].tol,
+                                    sample[i].u, s) == DI_OK;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t += ms;
+            }
+            di_destroy(ctx);
+            if (!ok) continue;  // did not converge or failed: not a candidate
+            t /= reps;
+            if (t < best_t) {
+                best_t = t;
+                *best = c;
+                found = true;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (best_ms) *best_ms = found ? best_t : -1.0;
+    return found ? DI_OK : DI_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// Serving loop
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Request {
+    long long ticket;
+    const float* f;  // host
+    const uint8_t* c;
+    float* u;
+    int w, h, ch;
+    float tol;
+    size_t bytes;  // device footprint while in flight
+    std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+    di_status status = DI_OK;
+    int cycles = 0;
+    bool done = false;
+};
+
+struct ServerSlot {
+    Slot s;
+    float* f_dev = nullptr;
+    uint8_t* c_dev = nullptr;
+    float* u_dev = nullptr;
+    size_t cap = 0;  // pixel-channels of the device buffers
+    size_t cap_px = 0;
+};
+
+}  // namespace
+
+struct di_server {
+    di_config cfg;
+    int device = 0;
+    size_t budget = 0;
+    std::vector<ServerSlot> slots;
+    std::vector<std::thread> threads;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::unordered_map<long long, Request*> reqs;
+    size_t in_flight_bytes = 0;
+    long long next_ticket = 1;
+    bool stop = false;
+    long long completed = 0;
+};
+
+namespace {
+
+size_t footprint(const di_config& cfg, int w, int h, int C) {
+    di_plan_info p;
+    if (di_plan(&cfg, w, h, C, &p) != DI_OK) return 0;
+    // workspace + the request's own device copies of f, c and u
+    return (size_t)p.workspace_bytes + (size_t)w * h * (2 * C * sizeof(float) + 1);
+}
+
+bool ensure_buffers(ServerSlot& sl, size_t pxch, size_t px) {
+    if (pxch <= sl.cap && px <= sl.cap_px) return true;
+    if (sl.f_dev) cudaFree(sl.f_dev);
+    if (sl.u_dev) cudaFree(sl.u_dev);
+    if (sl.c_dev) cudaFree(sl.c_dev);
+    sl.f_dev = sl.u_dev = nullptr;
+    sl.c_dev = nullptr;
+    sl.cap = sl.cap_px = 0;
+    if (cudaMalloc(&sl.f_dev, pxch * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&sl.u_dev, pxch * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&sl.c_dev, px) != cudaSuccess)
+        return false;
+    sl.cap = pxch;
+    sl.cap_px = px;
+    return true;
+}
+
+void serve_loop(di_server* srv, int k) {
+    ServerSlot& sl = srv->slots[k];
+    cudaSetDevice(srv->device);
+    for (;;) {
+        Request* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            // admission: the queue head runs once its footprint fits the budget
+            // next to what is already in flight (a lone request always runs)
+            srv->cv_work.wait(lock, [&] {
+                if (srv->stop) return true;
+                if (srv->queue.empty()) return false;
+                Request* head = srv->queue.front();
+                return srv->in_flight_bytes == 0 ||
+                       srv->in_flight_bytes + head->bytes <= srv->budget;
+            });
+            if (srv->stop && srv->queue.empty()) return;
+            if (srv->queue.empty()) continue;
+            r = srv->queue.front();
+            srv->queue.pop_front();
+            srv->in_flight_bytes += r->bytes;
+        }
+        r->t_start = std::chrono::steady_clock::now();
+        const size_t px = (size_t)r->w * r->h, pxch = px * r->ch;
+        di_status st = DI_OK;
+        if (!ensure_buffers(sl, pxch, px)) st = DI_ERR_OOM;
+        if (st == DI_OK) {
+            cudaMemcpyAsync(sl.f_dev, r->f, pxch * sizeof(float), cudaMemcpyHostToDevice,
+                            sl.s.stream);
+            cudaMemcpyAsync(sl.c_dev, r->c, px, cudaMemcpyHostToDevice, sl.s.stream);
+            st = di_inpaint(sl.s.ctx, sl.f_dev, sl.c_dev, r->w, r->h, r->ch, r->tol, sl.u_dev,
+                            sl.s.stream);
+            if (st == DI_OK || st == DI_ERR_NOT_CONVERGED) {
+                cudaMemcpyAsync(r->u, sl.u_dev, pxch * sizeof(float), cudaMemcpyDeviceToHost,
+                                sl.s.stream);
+                if (cudaStreamSynchronize(sl.s.stream) != cudaSuccess) st = DI_ERR_CUDA;
+            }
+        }
+        di_stats ss;
+        di_get_stats(sl.s.ctx, &ss);
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            r->status = st;
+            r->cycles = ss.cycles;
+            r->t_done = std::chrono::steady_clock::now();
+            r->done = true;
+            srv->in_flight_bytes -= r->bytes;
+            ++srv->completed;
+        }
+        srv->cv_done.notify_all();
+        srv->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" di_status di_server_create(const di_config* cfg, int device, int slots,
+                                      long long mem_budget, di_server** out) {
+    if (!out || slots < 1 || slots > 64 || mem_budget < 0) return DI_ERR_INVALID_ARG;
+    *out = nullptr;
+    di_server* srv = new (std::nothrow) di_server();
+    if (!srv) return DI_ERR_OOM;
+    std::memset(&srv->cfg, 0, sizeof srv->cfg);
+    if (cfg) srv->cfg = *cfg;
+    srv->device = device;
+    srv->budget = mem_budget > 0 ? (size_t)mem_budget : (size_t)-1;
+    srv->slots.resize(slots);
+    for (int k = 0; k < slots; ++k) {
+        di_status st = make_slot(&srv->cfg, device, &srv->slots[k].s);
+        if (st != DI_OK) {
+            for (auto& sl : srv->slots) free_slot(&sl.s);
+            delete srv;
+            return st;
+        }
+    }
+    for (int k = 0; k < slots; ++k) srv->threads.emplace_back(serve_loop, srv, k);
+    *out = srv;
+    return DI_OK;
+}
+
+extern "C" di_status di_server_submit(di_server* srv, const float* f, const uint8_t* c, int width,
+                                      int height, int channels, float tol, float* u,
+                                      long long* ticket) {
+    if (!srv || !f || !c || !u || !ticket || width < 1 || height < 1 || channels < 1 ||
+        channels > di::kMaxChannels || !(tol > 0.f))
+        return DI_ERR_INVALID_ARG;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return DI_ERR_OOM;
+    r->f = f;
+    r->c = c;
+    r->u = u;
+    r->w = width;
+    r->h = height;
+    r->ch = channels;
+    r->tol = tol;
+    r->bytes = footprint(srv->cfg, width, height, channels);
+    r->t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        r->ticket = srv->next_ticket++;
+        srv->reqs[r->ticket] = r;
+        srv->queue.push_back(r);
+    }
+    *ticket = r->ticket;
+    srv->cv_work.notify_all();
+    return DI_OK;
+}
+
+extern "C" di_status di_server_wait(di_server* srv, long long ticket, di_request_info* info) {
+    if (!srv) return DI_ERR_INVALID_ARG;
+    Request* r = nullptr;
+    {
+        std::unique_lock<std::mutex> lock(srv->mu);
+        auto it = srv->reqs.find(ticket);
+        if (it == srv->reqs.end()) return DI_ERR_INVALID_ARG;
+        r = it->second;
+        srv->cv_done.wait(lock, [&] { return r->done; });
+        srv->reqs.erase(it);
+    }
+    if (info) {
+        using ms = std::chrono::duration<double, std::milli>;
+        info->status = r->status;
+        info->cycles = r->cycles;
+        info->latency_ms = ms(r->t_done - r->t_submit).count();
+        info->queue_ms = ms(r->t_start - r->t_submit).count();
+        info->footprint_bytes = (long long)r->bytes;
+    }
+    di_status st = r->status;
+    delete r;
+    return st;
+}
+
+extern "C" void di_server_destroy(di_server* srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    for (auto& t : srv->threads) t.join();
+    cudaSetDevice(srv->device);
+    for (auto& sl : srv->slots) {
+        if (sl.f_dev) cudaFree(sl.f_dev);
+        if (sl.u_dev) cudaFree(sl.u_dev);
+        if (sl.c_dev) cudaFree(sl.c_dev);
+        free_slot(&sl.s);
+    }
+    for (auto& kv : srv->reqs) delete kv.second;
+    delete srv;
+}
