@@ -180,7 +180,8 @@ def run_ours(args):
     f_dev = [torch.from_numpy(f).to(dev) for f, _ in cases]
     c_dev = [torch.from_numpy(c).to(dev) for _, c in cases]
     u_dev = torch.empty_like(f_dev[0])
-    ctx = di.Context(device=local, profile=1)
+    prec = {"fp32": di.PREC_FP32, "fp16": di.PREC_FP16, "bf16": di.PREC_BF16}[args.precision]
+    ctx = di.Context(device=local, profile=1, precision=prec)
     stream = torch.cuda.current_stream(dev)
 
     def step(i):
@@ -321,10 +322,13 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"f32 ({args.precision} local iterates)",
+        "data": "synthetic",
         "config": {"workload": "3840x2160x3 frames, masks {10,4,1}% x {edge-clustered, "
                                "uniform} in rotation, tol 0.05 gray (error-estimate stop rule)",
                    "block": 32, "overlap": 6, "local_iters": 8, "frames": len(cases),
+                   "precision": args.precision,
                    "l2": "inputs larger than L2 (6 rotating frames, 650 MB), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "latency_ms": {"p50": round(lat[len(lat) // 2], 4),
@@ -429,6 +433,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=6)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
+                    help="storage of the block-local CG iterates (default fp32)")
     ap.add_argument("--kernel", choices=["oras", "prolong", "restrict", "residual"],
                     help="run one launch of this step on one 4K RGB frame (for ncu) and exit")
     args = ap.parse_args()

@@ -56,6 +56,13 @@ typedef enum {
  * DI_STOP_FIXED_CYCLES: exactly max_cycles V-cycles. */
 enum { DI_STOP_ERROR_ESTIMATE = 0, DI_STOP_RELATIVE_RESIDUAL = 1, DI_STOP_FIXED_CYCLES = 2 };
 
+/* Precision of the block-local CG iterates.  DI_PREC_FP16 / DI_PREC_BF16:
+ * vectors, stencil and updates of every local solve in packed 16-bit
+ * arithmetic with FP32 dot products; the block residual is normalised before
+ * it is narrowed; the FP32 outer iteration refines the result.  Applies to
+ * 32x32 blocks; other block sizes compute in FP32. */
+enum { DI_PREC_FP32 = 0, DI_PREC_FP16 = 1, DI_PREC_BF16 = 2 };
+
 /* Solver configuration; a zero field takes the default in brackets. */
 typedef struct {
     int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
@@ -72,7 +79,10 @@ typedef struct {
     int stop_rule;    /* DI_STOP_* [DI_STOP_ERROR_ESTIMATE] */
     int profile;      /* 1: time every finest-level ORAS block launch with CUDA events
                          recorded on the call's stream (see di_get_profile) [0] */
-    int reserved[4];
+    int precision;    /* DI_PREC_*: storage of the local CG iterates of 32x32 blocks
+                         [DI_PREC_FP32]; the residual that starts each local solve and
+                         the update of u are FP32 in every mode */
+    int reserved[3];
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

@@ -11,7 +11,8 @@ in hand-written CUDA kernels for sm_103a behind the C ABI of include/di.h.
     u, status = ctx.inpaint(f_cuda_float32_CHW, mask_cuda_uint8_HW, tol=0.05)
 """
 from ._lib import (  # noqa: F401
-    CUDA_ERROR, EMPTY_MASK, INVALID_ARG, NOT_CONVERGED, OK, OOM, STOP_ERROR_ESTIMATE,
+    CUDA_ERROR, EMPTY_MASK, INVALID_ARG, NOT_CONVERGED, OK, OOM, PREC_BF16, PREC_FP16, PREC_FP32,
+    STOP_ERROR_ESTIMATE,
     STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
     exported_symbols, load, mask_downsample, plan, prolong, residual_norm_noalloc,
     restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server)

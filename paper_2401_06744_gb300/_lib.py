@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdi.so")
 
 OK, INVALID_ARG, EMPTY_MASK, OOM, NOT_CONVERGED, CUDA_ERROR, TIMEOUT = range(7)
 STOP_ERROR_ESTIMATE, STOP_RELATIVE_RESIDUAL, STOP_FIXED_CYCLES = range(3)
+PREC_FP32, PREC_FP16, PREC_BF16 = range(3)
 
 
 class di_config(ctypes.Structure):
@@ -27,7 +28,7 @@ class di_config(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("min_cycles", ctypes.c_int),
                 ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class di_stats(ctypes.Structure):

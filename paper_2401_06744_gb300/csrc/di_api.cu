@@ -102,6 +102,7 @@ bool config_ok(const di_config& c) {
     if (c.downsample != 0 && c.downsample != 1) return false;
     if (c.stop_rule < 0 || c.stop_rule > 2) return false;
     if (c.profile != 0 && c.profile != 1) return false;
+    if (c.precision < 0 || c.precision > 2) return false;
     return true;
 }
 
@@ -261,7 +262,7 @@ struct Sched {
         }
         DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.mbits, v.w, v.h, C, ctx->cfg.block,
                                  ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
-                                 ctx->planes, maxupd, s, ev));
+                                 ctx->planes, maxupd, s, ev, ctx->cfg.precision));
         return DI_OK;
     }
 
@@ -683,7 +684,7 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, s));
     DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels,
                              ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
-                             u_out, ctx->planes, nullptr, s));
+                             u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision));
     return DI_OK;
 }
 

@@ -81,11 +81,12 @@ inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
 // until r.r <= max(rtol2, 1e-14) * (r.r)_0.  max |v_i| over pixels with
 // nonzero weight is folded into *maxupd (nullable).
 // ev (nullable): two events recorded on `s` right before and right after the
-// block kernel (the combine kernels follow the second one).
+// block kernel (the combine kernels follow the second one).  precision: 0
+// FP32, 1 FP16, 2 BF16 local CG iterates (32x32 blocks; other sizes use FP32).
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s, cudaEvent_t* ev = nullptr);
+                        cudaStream_t s, cudaEvent_t* ev = nullptr, int precision = 0);
 
 // Host-side geometry shared with the kernels.
 inline int axis_blocks(int n, int B, int o) {

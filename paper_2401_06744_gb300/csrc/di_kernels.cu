@@ -36,6 +36,9 @@
 #include <atomic>
 #include <mutex>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 namespace di {
 
 static std::atomic<long long> g_launches{0};
@@ -1091,6 +1094,329 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 }
 
 
+// ---- 16-bit storage variant of k_oras_2w ------------------------------------
+// The CG vectors, the stencil and the vector updates of each local solve run
+// in packed FP16 or BF16 (one 32-bit register per pixel pair, so half the
+// registers and one shuffle per pair); the dot products accumulate in FP32,
+// the residual that starts each local solve and the update of u stay FP32
+// (the outer FP32 iteration refines whatever the narrow local solve leaves).
+// The block residual is normalised by its maximum (times 1/64 for FP16, whose
+// range is small) before it is narrowed.  A block whose narrow iterate stops
+// being finite contributes no correction in this iteration.
+struct HalfT {
+    typedef __half2 T2;
+    static constexpr float kScale = 1.f / 64.f;
+    __device__ static __forceinline__ T2 make(float lo, float hi) { return __floats2half2_rn(lo, hi); }
+    __device__ static __forceinline__ float lo(T2 a) { return __low2float(a); }
+    __device__ static __forceinline__ float hi(T2 a) { return __high2float(a); }
+    __device__ static __forceinline__ f2 wide(T2 a) {
+        const float2 v = __half22float2(a);
+        return pk(v.x, v.y);
+    }
+};
+struct Bf16T {
+    typedef __nv_bfloat162 T2;
+    static constexpr float kScale = 1.f;
+    __device__ static __forceinline__ T2 make(float lo, float hi) { return __floats2bfloat162_rn(lo, hi); }
+    __device__ static __forceinline__ float lo(T2 a) { return __low2float(a); }
+    __device__ static __forceinline__ float hi(T2 a) { return __high2float(a); }
+    __device__ static __forceinline__ f2 wide(T2 a) {
+        const float2 v = __bfloat1622float2(a);
+        return pk(v.x, v.y);
+    }
+};
+
+template <class H>
+__global__ void __launch_bounds__(64, 10)
+k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
+            int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
+            int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
+            float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner) {
+    typedef typename H::T2 T2;
+    constexpr int B = 32, NP = 8, TH = Tile2W::TH, P = Tile2W::P, TILE = Tile2W::TILE;
+    extern __shared__ float smem[];
+    float* const s_u = smem;
+    float* const s_wy = smem + 2 * TILE;
+    float* const s_b = smem + Tile2W::FIXED;
+    __shared__ float s_red1[2], s_red2[2], s_seam[2][32], s_mx[2];
+
+    const int t = threadIdx.x;
+    const int lane = t & 31, wi = t >> 5;
+    const int col = lane;
+    const int row0 = 16 * wi;
+    const int s = B - o;
+    const size_t n = (size_t)w * h;
+    const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
+    const int nblk = nbx * nby;
+    auto task_of = [&](int i, int& blk, int& ch) {
+        if (chan_inner) {
+            blk = (int)blockIdx.x + (i / C) * (int)gridDim.x;
+            ch = i % C;
+        } else {
+            const int tt = (int)blockIdx.x + i * (int)gridDim.x;
+            blk = tt / C;
+            ch = tt - blk * C;
+        }
+        return blk < nblk;
+    };
+    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
+        const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
+        if (!zero_in) {
+            const float* src = u_in + ch * n;
+            float* dst = s_u + bs * TILE;
+            const int gxa = px0 - 1 + lane, gxb = gxa + 32;
+            const bool oka = gxa >= 0 && gxa < w;
+            const bool okb = lane < TH - 32 && gxb < w;
+#pragma unroll 2
+            for (int ty = wi; ty < TH; ty += 2) {
+                const int gy = py0 - 1 + ty;
+                const bool rok = gy >= 0 && gy < h;
+                const float* row = src + (ptrdiff_t)gy * w;
+                cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
+                if (lane < TH - 32)
+                    cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
+            }
+        }
+        if (!rhs_zero) {
+            const float* src = rhs + ch * n;
+            float* dst = s_b + bs * B * B;
+            const int gx = px0 + lane;
+#pragma unroll 4
+            for (int ly = wi; ly < B; ly += 2) {
+                const int gy = py0 + ly;
+                const bool ok = gx < w && gy < h;
+                cp_async4(dst + ly * B + lane, ok ? src + (size_t)gy * w + gx : src, ok);
+            }
+        }
+        cp_async_commit();
+        if (blk != have_blk && lane < 16) {
+            const int gy = py0 + row0 + lane;
+            if (gy < h) {
+                const uint32_t* row = mbits + (size_t)gy * wpr + (px0 >> 5);
+                nlo = __ldg(row);
+                nhi = __ldg(row + 1);
+            } else {
+                nlo = nhi = 0xffffffffu;
+            }
+        }
+    };
+
+    int blk, ch;
+    if (!task_of(0, blk, ch)) return;
+    prefetch(blk, ch, 0, -1);
+    int buf = 0, cur_blk = -1;
+    T2 ndg[NP], keep[NP];
+    T2 ml2 = H::make(0.f, 0.f), mr2 = H::make(0.f, 0.f);
+    float wx = 0.f, dh = 0.f;
+    int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
+    float vmax = 0.f;
+
+    for (int i = 0;; ++i) {
+        cp_async_wait_all();
+        __syncthreads();
+        const uint32_t mlo = nlo, mhi = nhi;
+        int nb2, nc2;
+        const bool more = task_of(i + 1, nb2, nc2);
+        if (more) prefetch(nb2, nc2, buf ^ 1, blk);
+
+        if (blk != cur_blk) {
+            cur_blk = blk;
+            kx = blk % nbx;
+            ky = blk / nbx;
+            x0 = kx * s;
+            y0 = ky * s;
+            const int bw = min(B, w - x0);
+            bh = min(B, h - y0);
+            const uint32_t rowm = __funnelshift_r(mlo, mhi, x0 & 31);
+            uint32_t mb = 0;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                const uint32_t v = __shfl_sync(kFull, rowm, rr);
+                mb |= ((v >> col) & 1u) << rr;
+            }
+            const int gx = x0 + col;
+            const float hc = (col > 0 ? 1.f : (gx > 0 ? alpha : 0.f)) +
+                             (col + 1 < bw ? 1.f : (gx < w - 1 ? alpha : 0.f));
+            dh = (float)((gx > 0) + (gx < w - 1));
+            const float ml = col > 0 ? 1.f : 0.f, mr = col < B - 1 ? 1.f : 0.f;
+            ml2 = H::make(ml, ml);
+            mr2 = H::make(mr, mr);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                float vc[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                    vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
+                            (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                }
+                ndg[k] = H::make(-(hc + vc[0]), -(hc + vc[1]));
+                keep[k] = H::make(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
+            }
+            wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
+            if (t < B) s_wy[t] = ramp_weight(t, ky, nby, s, o, inv_o1);
+        }
+
+        const float* tu = s_u + buf * TILE;
+        const float* tb = s_b + buf * B * B;
+
+        // FP32 residual of the block, then its maximum for the normalisation
+        float rv[NP][2];
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                float v = rhs_zero ? 0.f : tb[ly * B + col];
+                if (!zero_in) {
+                    const float* c0 = tu + (ly + 1) * P + col + 1;
+                    const float dv = (float)((gy > 0) + (gy < h - 1));
+                    v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                }
+                v *= e ? H::hi(keep[k]) : H::lo(keep[k]);
+                rv[k][e] = v;
+                mx = fmaxf(mx, fabsf(v));
+            }
+        }
+        mx = warp_max(mx);
+        if (lane == 0) s_mx[wi] = mx;
+        __syncthreads();
+        mx = fmaxf(s_mx[0], s_mx[1]);
+        const float sc = mx > 0.f ? mx / H::kScale : 1.f;  // r = sc * r_narrow
+        const float isc = 1.f / sc;
+
+        T2 x[NP], r[NP], p[NP], q[NP];
+        f2 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            r[k] = H::make(rv[k][0] * isc, rv[k][1] * isc);
+            p[k] = r[k];
+            x[k] = H::make(0.f, 0.f);
+            const f2 rw = H::wide(r[k]);
+            if (k & 1) acc1 = fma2(rw, rw, acc1);
+            else acc0 = fma2(rw, rw, acc0);
+        }
+        acc0 = add2(acc0, acc1);
+        s_seam[wi][lane] = wi == 0 ? H::hi(r[NP - 1]) : H::lo(r[0]);
+        float part = warp_sum(lo2(acc0) + hi2(acc0));
+        if (lane == 0) s_red2[wi] = part;
+        __syncthreads();
+        float rr = s_red2[0] + s_red2[1];
+        float pb = s_seam[wi ^ 1][lane];
+        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+        bool bad = !(rr < INFINITY);
+
+        for (int it = 0; it < iters; ++it) {
+            if (!(rr > rr_stop) || bad) break;  // identical in both warps
+            const T2 pu = wi == 0 ? H::make(0.f, H::lo(p[NP - 1])) : H::make(pb, H::lo(p[NP - 1]));
+            const T2 pd = wi == 0 ? H::make(H::hi(p[0]), pb) : H::make(H::hi(p[0]), 0.f);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const T2 left = __shfl_up_sync(kFull, p[k], 1);
+                const T2 right = __shfl_down_sync(kFull, p[k], 1);
+                const T2 up = k > 0 ? p[k - 1] : pu;
+                const T2 dn = k < NP - 1 ? p[k + 1] : pd;
+                T2 nbs = __hadd2(up, dn);
+                nbs = __hfma2(ml2, left, nbs);
+                nbs = __hfma2(mr2, right, nbs);
+                const T2 qk = __hmul2(__hfma2(ndg[k], p[k], nbs), keep[k]);
+                q[k] = qk;
+                if (k & 1) acc1 = fma2(H::wide(p[k]), H::wide(qk), acc1);
+                else acc0 = fma2(H::wide(p[k]), H::wide(qk), acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red1[wi] = part;
+            __syncthreads();
+            const float pq = -(s_red1[0] + s_red1[1]);
+            if (!(pq > 0.f) || !(pq < INFINITY)) {
+                bad = !(pq < INFINITY) || pq != pq;
+                break;
+            }
+            const float a = __fdividef(rr, pq);
+            const T2 a2 = H::make(a, a);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                x[k] = __hfma2(a2, p[k], x[k]);
+                r[k] = __hfma2(a2, q[k], r[k]);
+                const f2 rw = H::wide(r[k]);
+                if (k & 1) acc1 = fma2(rw, rw, acc1);
+                else acc0 = fma2(rw, rw, acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            s_seam[wi][lane] = wi == 0 ? H::hi(r[NP - 1]) : H::lo(r[0]);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red2[wi] = part;
+            __syncthreads();
+            const float rrn = s_red2[0] + s_red2[1];
+            if (!(rrn < INFINITY)) { bad = true; break; }
+            const float beta = __fdividef(rrn, rr);
+            rr = rrn;
+            const T2 b2 = H::make(beta, beta);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) p[k] = __hfma2(b2, p[k], r[k]);
+            pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
+        }
+
+        const int par = (kx & 1) | ((ky & 1) << 1);
+        float* plane = planes + ((size_t)par * C + ch) * n;
+        float* uo = u_out + ch * n;
+        const bool colok = x0 + col < w;
+        const int nsh = shared_per_seam(o), first = shared_first(o);
+        int sx_seam = -1, sx_side = 0, sx_j = 0;
+        if (kx > 0 && col >= first && col < first + nsh) {
+            sx_seam = kx; sx_side = 1; sx_j = col - first;
+        } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
+            sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
+        }
+        float* strip = sx_seam > 0
+                           ? planes + 4 * (size_t)C * n +
+                                 (((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h) *
+                                     nsh + sx_j
+                           : planes;
+        const float vs = bad ? 0.f : sc;  // a non-finite narrow iterate gives no correction
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = row0 + k + 8 * e;
+                if (ly >= bh || !colok) continue;
+                const float v = (e ? H::hi(x[k]) : H::lo(x[k])) * vs;
+                const float d = wx * s_wy[ly];
+                const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
+                const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
+                if (d == 1.f) {
+                    uo[gp] = uold + v;
+                } else if (d > 0.f) {
+                    const float wyr = s_wy[ly];
+                    const bool xfirst = sx_seam < 0 || sx_side == 0;
+                    if (wyr < 1.f) {
+                        const bool yfirst = ly >= s;
+                        plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
+                    } else {
+                        strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
+                    }
+                }
+                if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+            }
+        }
+        if (!more) break;
+        blk = nb2;
+        ch = nc2;
+        buf ^= 1;
+    }
+    if (maxupd) {
+        vmax = warp_max(vmax);
+        if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
+    }
+}
+
 // Shared rows (the interior rows of every horizontal overlap), full width:
 // contributions from the parity planes (two block rows; two block columns
 // where the pixel is also shared along x).
@@ -1154,36 +1480,52 @@ inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
 cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
                            int B, int o, int nbx, int nby, float* u_out, cudaStream_t s);
 
+typedef void (*Oras2wKernel)(const float*, int, const float*, int, const uint32_t*, int, int, int,
+                             int, int, int, int, float, int, float, float*, float*, unsigned*,
+                             int);
+
+// precision: 0 FP32, 1 FP16, 2 BF16 local iterates
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                           cudaStream_t s, cudaEvent_t* ev) {
+                           cudaStream_t s, cudaEvent_t* ev, int precision) {
     constexpr int B = 32;
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
     const size_t smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) *
                         sizeof(float);
-    // occupancy per shared-memory size (cached; sizes repeat across calls)
+    const Oras2wKernel kern = precision == 1 ? k_oras_2w_h<HalfT>
+                              : precision == 2 ? k_oras_2w_h<Bf16T>
+                                               : k_oras_2w;
+    // occupancy per (kernel, shared-memory size), cached
     static std::mutex occ_mu;
-    std::lock_guard<std::mutex> occ_lock(occ_mu);
     static int nsm = 0;
-    static size_t occ_key[8] = {};
-    static int occ_val[8] = {};
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const size_t mx = ((size_t)Tile2W::FIXED + (size_t)2 * B * B) * sizeof(float);
-        cudaFuncSetAttribute(k_oras_2w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    }
+    static const void* occ_fn[12] = {};
+    static size_t occ_key[12] = {};
+    static int occ_val[12] = {};
     int oc = 0;
-    for (int i = 0; i < 8; ++i)
-        if (occ_key[i] == smem) oc = occ_val[i];
-    if (oc == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_2w, 64, smem);
-        if (oc < 1) oc = 1;
-        for (int i = 0; i < 8; ++i)
-            if (occ_key[i] == 0) { occ_key[i] = smem; occ_val[i] = oc; break; }
+    {
+        std::lock_guard<std::mutex> occ_lock(occ_mu);
+        if (nsm == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        }
+        for (int i = 0; i < 12; ++i)
+            if (occ_fn[i] == (const void*)kern && occ_key[i] == smem) oc = occ_val[i];
+        if (oc == 0) {
+            const size_t mx = ((size_t)Tile2W::FIXED + (size_t)2 * B * B) * sizeof(float);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, kern, 64, smem);
+            if (oc < 1) oc = 1;
+            for (int i = 0; i < 12; ++i)
+                if (occ_fn[i] == nullptr) {
+                    occ_fn[i] = (const void*)kern;
+                    occ_key[i] = smem;
+                    occ_val[i] = oc;
+                    break;
+                }
+        }
     }
     const int slots = nsm * oc;
     const int nblk = nbx * nby;
@@ -1191,8 +1533,8 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
     if (grid < 1) grid = 1;
     if (ev) cudaEventRecord(ev[0], s);
-    k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, nbx,
-                                     nby, alpha, iters, rtol2, u_out, planes, maxupd, chan_inner);
+    kern<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, nbx, nby,
+                                alpha, iters, rtol2, u_out, planes, maxupd, chan_inner);
     count();
     if (ev) cudaEventRecord(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -1402,12 +1744,12 @@ cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cud
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s, cudaEvent_t* ev) {
+                        cudaStream_t s, cudaEvent_t* ev, int precision) {
     const int wpr = mask_words_per_row(w);
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                  iters, rtol2, u_out, planes, maxupd, s, ev);
+                                  iters, rtol2, u_out, planes, maxupd, s, ev, precision);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev);
