@@ -426,6 +426,90 @@ def run_kernel(args):
     print(json.dumps(out), flush=True)
 
 
+COMPARE_DENSITIES = (0.005, 0.01, 0.02, 0.05, 0.10)
+RESOLUTIONS = ((480, 270), (960, 540), (1920, 1080), (3840, 2160))
+# schedule x smoother of the comparison methods (Section 5)
+METHODS = ("multigrid_oras", "full_fmg_oras", "multilevel_oras", "multigrid_cg",
+           "multilevel_cg", "global_cg")
+
+
+def _method_config(di, name):
+    sched = {"multigrid": di.SCHED_REDUCED_FMG, "full_fmg": di.SCHED_FULL_FMG,
+             "multilevel": di.SCHED_MULTILEVEL, "global": di.SCHED_SINGLE}
+    head, smoother = name.rsplit("_", 1)
+    return {"schedule": sched[head],
+            "smoother": di.SMOOTH_ORAS if smoother == "oras" else di.SMOOTH_CG}
+
+
+def run_compare(args):
+    """Comparison tables of Section 5 on synthetic frames: every method to a
+    relative residual of 1e-3 (the paper's criterion for this comparison) over
+    edge-clustered mask densities at 4K RGB (`--compare methods`), or over
+    frame sizes at 5 % density (`--compare resolution`).  One JSON line per
+    row: median ms of `reps` timed solves (inputs resident, CUDA events), the
+    cycles taken and the error against a fully converged solution (12 fixed
+    V-cycles of the multigrid ORAS decoder)."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06744_gb300 import build as _build
+
+    _build.build()
+    import paper_2401_06744_gb300 as di
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    reps = max(1, args.steps if args.steps != 60 else 3)
+    if args.compare == "methods":
+        rows = [(W4K, H4K, d) for d in COMPARE_DENSITIES]
+        methods = METHODS
+    else:
+        rows = [(w, h, 0.05) for (w, h) in RESOLUTIONS]
+        methods = ("multigrid_oras", "multilevel_oras", "multigrid_cg", "multilevel_cg")
+    s = torch.cuda.current_stream(dev)
+    for i, (w, h, d) in enumerate(rows):
+        f, c = synth.make_case(w, h, C4K, d, "edge", _case_seed(40 + i))
+        ft = torch.from_numpy(f).to(dev)
+        ct = torch.from_numpy(c).to(dev)
+        with di.Context(device=0, stop_rule=di.STOP_FIXED_CYCLES, max_cycles=12,
+                        min_cycles=12) as ctx:
+            ref, _ = ctx.inpaint(ft, ct, tol=TOL)
+        torch.cuda.synchronize(dev)
+        variants = [(m, "rel_residual", 1e-3) for m in methods]
+        variants.append(("multigrid_oras", "error_estimate", TOL))
+        for m, rule, tol in variants:
+            cfg = _method_config(di, m)
+            if rule == "rel_residual":
+                cfg.update(stop_rule=di.STOP_RELATIVE_RESIDUAL, max_cycles=4000)
+            else:
+                cfg.update(max_cycles=64)
+            with di.Context(device=0, **cfg) as ctx:
+                u = torch.empty_like(ft)
+                ctx.inpaint(ft, ct, tol=tol, out=u, check=False)  # warm-up, workspace
+                times = []
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    e0.record(s)
+                    _, st = ctx.inpaint(ft, ct, tol=tol, out=u, check=False)
+                    e1.record(s)
+                    torch.cuda.synchronize(dev)
+                    times.append(e0.elapsed_time(e1))
+                stats = ctx.stats()
+            err = (u.double() - ref.double()).abs()
+            ms = statistics.median(times)
+            print(json.dumps({
+                "mode": args.compare, "width": w, "height": h, "channels": C4K,
+                "density": d, "mask": "edge", "method": m, "stop": rule, "tol": tol,
+                "status": int(st), "ms": round(ms, 3), "fps": round(1000.0 / ms, 2),
+                "cycles": stats["cycles"],
+                "rel_residual": [round(x, 6) for x in stats["rel_residual"][:C4K]],
+                "max_err": round(float(err.max()), 4),
+                "rms_err": round(float(err.pow(2).mean().sqrt()), 5)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -437,7 +521,13 @@ def main():
                     help="storage of the block-local CG iterates (default fp32)")
     ap.add_argument("--kernel", choices=["oras", "prolong", "restrict", "residual"],
                     help="run one launch of this step on one 4K RGB frame (for ncu) and exit")
+    ap.add_argument("--compare", choices=["methods", "resolution"],
+                    help="print the comparison table of the schedules and smoothers "
+                         "(one JSON line per row) and exit")
     args = ap.parse_args()
+    if args.compare:
+        run_compare(args)
+        return
     if args.kernel:
         run_kernel(args)
         return

@@ -63,6 +63,25 @@ enum { DI_STOP_ERROR_ESTIMATE = 0, DI_STOP_RELATIVE_RESIDUAL = 1, DI_STOP_FIXED_
  * 32x32 blocks; other block sizes compute in FP32. */
 enum { DI_PREC_FP32 = 0, DI_PREC_FP16 = 1, DI_PREC_BF16 = 2 };
 
+/* Schedules (Sections 4.2 and 5).  REDUCED_FMG: the cascade with one
+ * smoothing step per level, then V-cycles on the finest level (the paper's
+ * method).  FULL_FMG: a V-cycle on every level of the cascade (Fig. 3), then
+ * V-cycles.  MULTILEVEL: the cascade, then smoothing steps on the finest level
+ * without coarse corrections (the multilevel solver of the comparison).
+ * SINGLE: no hierarchy; smoothing steps on the finest level from u = f on the
+ * mask, 0 elsewhere.  For the last two a "cycle" of the stop rule is one
+ * smoothing step. */
+enum { DI_SCHED_REDUCED_FMG = 0, DI_SCHED_FULL_FMG = 1, DI_SCHED_MULTILEVEL = 2,
+       DI_SCHED_SINGLE = 3 };
+
+/* Smoothers.  ORAS: one ORAS iteration (Algorithm 2).  CG: local_iters steps
+ * of global conjugate gradients on the level's reduced system (the CG
+ * counterparts of Section 5).  With DI_SCHED_SINGLE and DI_SCHED_MULTILEVEL
+ * one CG run continues across the steps on the finest level (global CG from
+ * the cascade's guess); inside V-cycles every smoothing call starts afresh.
+ * The single-block solve of the coarsest level always uses the block solver. */
+enum { DI_SMOOTH_ORAS = 0, DI_SMOOTH_CG = 1 };
+
 /* Solver configuration; a zero field takes the default in brackets. */
 typedef struct {
     int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
@@ -82,7 +101,9 @@ typedef struct {
     int precision;    /* DI_PREC_*: storage of the local CG iterates of 32x32 blocks
                          [DI_PREC_FP32]; the residual that starts each local solve and
                          the update of u are FP32 in every mode */
-    int reserved[3];
+    int schedule;     /* DI_SCHED_* [DI_SCHED_REDUCED_FMG] */
+    int smoother;     /* DI_SMOOTH_* [DI_SMOOTH_ORAS] */
+    int reserved[1];
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

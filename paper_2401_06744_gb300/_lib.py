@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdi.so")
 OK, INVALID_ARG, EMPTY_MASK, OOM, NOT_CONVERGED, CUDA_ERROR, TIMEOUT = range(7)
 STOP_ERROR_ESTIMATE, STOP_RELATIVE_RESIDUAL, STOP_FIXED_CYCLES = range(3)
 PREC_FP32, PREC_FP16, PREC_BF16 = range(3)
+SCHED_REDUCED_FMG, SCHED_FULL_FMG, SCHED_MULTILEVEL, SCHED_SINGLE = range(4)
+SMOOTH_ORAS, SMOOTH_CG = range(2)
 
 
 class di_config(ctypes.Structure):
@@ -28,7 +30,8 @@ class di_config(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("min_cycles", ctypes.c_int),
                 ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("smoother", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class di_stats(ctypes.Structure):

@@ -64,6 +64,10 @@ struct di_ctx {
     int ev_used = 0;
     di_profile prof = {};
     long long launch_base = 0;
+    // global-CG smoother state (cfg.smoother == DI_SMOOTH_CG): r, p, q, x
+    float* cg[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* cg_sc = nullptr;
+    int cg_par = 0;
 };
 
 namespace {
@@ -103,6 +107,8 @@ bool config_ok(const di_config& c) {
     if (c.stop_rule < 0 || c.stop_rule > 2) return false;
     if (c.profile != 0 && c.profile != 1) return false;
     if (c.precision < 0 || c.precision > 2) return false;
+    if (c.schedule < 0 || c.schedule > 3) return false;
+    if (c.smoother < 0 || c.smoother > 1) return false;
     return true;
 }
 
@@ -129,6 +135,10 @@ void prof_flush(di_ctx* ctx) {
     } while (0)
 
 void free_workspace(di_ctx* ctx) {
+    for (int k = 0; k < 4; ++k) {
+        if (ctx->cg[k]) cudaFree(ctx->cg[k]);
+        ctx->cg[k] = nullptr;
+    }
     if (ctx->pool) cudaFree(ctx->pool);
     if (ctx->planes) cudaFree(ctx->planes);
     if (ctx->partials) cudaFree(ctx->partials);
@@ -174,6 +184,12 @@ di_status ensure_workspace(di_ctx* ctx, int w, int h, int C) {
     ctx->partials_cap = residual_partials_per_channel(nw, nh) * nc;
     e = cudaMalloc(&ctx->partials, ctx->partials_cap * sizeof(double));
     if (e != cudaSuccess) { free_workspace(ctx); return cuda_fail(ctx, e, "cudaMalloc(partials)"); }
+    if (ctx->cfg.smoother == DI_SMOOTH_CG) {
+        for (int k = 0; k < 4; ++k) {
+            e = cudaMalloc(&ctx->cg[k], (size_t)nw * nh * nc * sizeof(float));
+            if (e != cudaSuccess) { free_workspace(ctx); return cuda_fail(ctx, e, "cudaMalloc(cg)"); }
+        }
+    }
     ctx->cap_w = nw;
     ctx->cap_h = nh;
     ctx->cap_c = nc;
@@ -231,19 +247,23 @@ struct Sched {
     int C;
     int Leff;   // levels that carry unknown pixels (recursion depth)
     cudaStream_t s;
-    bool vcycle_phase = false;
+    int root = 0;  // level whose own problem is being solved (the others solve A e = r)
 
-    // right-hand side of level l: level 0 solves A u = C f (the right-hand side
-    // is zero at unknown pixels); coarse levels in the cascade solve
-    // A u = b_l (zero off the mask) and in the V-cycles A e = r_l.
+    // Right-hand side of level l: the root level solves A u = b_l (level 0:
+    // b = C f; coarse levels: the downsampled mask values), whose right-hand
+    // side is zero at unknown pixels; the levels below it solve A e = r_l.
+    const float* rhs_of(int l, int* rhs_zero) const {
+        const Level& v = ctx->lv[l];
+        if (l == root) { *rhs_zero = 1; return v.b; }
+        *rhs_zero = 0;
+        return v.r;
+    }
+
     di_status run_oras(int l, const float* in, int zero_in, float* out, int iters,
                        unsigned* maxupd, float rtol2 = 0.f) {
         const Level& v = ctx->lv[l];
-        const float* rhs;
         int rhs_zero;
-        if (l == 0) { rhs = v.b; rhs_zero = 1; }
-        else if (vcycle_phase) { rhs = v.r; rhs_zero = 0; }
-        else { rhs = v.b; rhs_zero = 1; }
+        const float* rhs = rhs_of(l, &rhs_zero);
         cudaEvent_t* ev = nullptr;
         if (l == 0 && ctx->cfg.profile) {
             if (!ctx->ev_made) {
@@ -266,6 +286,24 @@ struct Sched {
         return DI_OK;
     }
 
+    // One smoothing call on level l (in -> out): an ORAS iteration, or
+    // local_iters steps of global CG (restart = false continues the previous
+    // CG call on the same level).
+    di_status smooth(int l, const float* in, int zero_in, float* out, unsigned* maxupd,
+                     bool restart = true) {
+        const di_config& cfg = ctx->cfg;
+        if (cfg.smoother == DI_SMOOTH_ORAS)
+            return run_oras(l, in, zero_in, out, cfg.local_iters, maxupd);
+        const Level& v = ctx->lv[l];
+        int rhs_zero;
+        const float* rhs = rhs_of(l, &rhs_zero);
+        DI_CUDA(ctx, launch_cg_smooth(in, zero_in, rhs, rhs_zero, v.c, v.w, v.h, C,
+                                      cfg.local_iters, restart ? 1 : 0, ctx->cg[0], ctx->cg[1],
+                                      ctx->cg[2], ctx->cg[3], ctx->partials, ctx->cg_sc,
+                                      &ctx->cg_par, out, maxupd, s));
+        return DI_OK;
+    }
+
     // V-cycle on level l.  The iterate starts in lv[l].u[0] (or is zero) and
     // ends in lv[l].u[*which].  upd: per-step max-update slots (level 0 only).
     di_status vcycle(int l, bool zero_init, int* which, unsigned* upd) {
@@ -285,8 +323,7 @@ struct Sched {
         int slot = 0;
         bool zero = zero_init;
         for (int k = 0; k < cfg.pre; ++k) {
-            st = run_oras(l, v.u[cur], zero ? 1 : 0, v.u[cur ^ 1], cfg.local_iters,
-                          upd ? &upd[slot] : nullptr);
+            st = smooth(l, v.u[cur], zero ? 1 : 0, v.u[cur ^ 1], upd ? &upd[slot] : nullptr);
             if (st) return st;
             ++slot;
             cur ^= 1;
@@ -298,9 +335,9 @@ struct Sched {
         }
         if (l + 1 < Leff) {
             Level& cv = ctx->lv[l + 1];
-            const float* rhs = l == 0 ? v.b : v.r;
-            DI_CUDA(ctx, launch_restrict(v.u[cur], rhs, l == 0 ? 1 : 0, v.c, v.w, v.h, C, cv.c,
-                                         cv.r, s));
+            int rz;
+            const float* rhs = rhs_of(l, &rz);
+            DI_CUDA(ctx, launch_restrict(v.u[cur], rhs, rz, v.c, v.w, v.h, C, cv.c, cv.r, s));
             int cw = 0;
             st = vcycle(l + 1, true, &cw, nullptr);
             if (st) return st;
@@ -309,8 +346,7 @@ struct Sched {
         }
         ++slot;
         for (int k = 0; k < cfg.post; ++k) {
-            st = run_oras(l, v.u[cur], 0, v.u[cur ^ 1], cfg.local_iters,
-                          upd ? &upd[slot] : nullptr);
+            st = smooth(l, v.u[cur], 0, v.u[cur ^ 1], upd ? &upd[slot] : nullptr);
             if (st) return st;
             ++slot;
             cur ^= 1;
@@ -354,6 +390,8 @@ di_status di_plan(const di_config* cfg, int width, int height, int channels,
                                                            c.overlap) * sizeof(float) +
                                        residual_partials_per_channel(width, height) * channels *
                                            sizeof(double));
+    if (c.smoother == DI_SMOOTH_CG)  // r, p, q, x of the global CG smoother
+        out->workspace_bytes += 4LL * width * height * channels * (long long)sizeof(float);
     return DI_OK;
 }
 
@@ -376,6 +414,7 @@ di_status di_create(const di_config* cfg, int device, di_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->norm2, kMaxChannels * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counts, (kMaxLevels + 1) * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->upd, kMaxUpdSlots * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->cg_sc, 4 * kMaxChannels * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host, 4096);
     if (e != cudaSuccess) {
         di_status st = cuda_fail(ctx, e, "di_create");
@@ -396,6 +435,7 @@ void di_destroy(di_ctx* ctx) {
     if (ctx->norm2) cudaFree(ctx->norm2);
     if (ctx->counts) cudaFree(ctx->counts);
     if (ctx->upd) cudaFree(ctx->upd);
+    if (ctx->cg_sc) cudaFree(ctx->cg_sc);
     if (ctx->host) cudaFreeHost(ctx->host);
     delete ctx;
 }
@@ -493,31 +533,55 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     }
 
     Sched S{ctx, C, Leff, s};
-    // 2. cascade
-    int top;
-    if (Leff == L) {
-        top = L - 1;
-        Level& v = ctx->lv[top];
-        DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s));
-        st = S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2);
-        if (st) return st;
+    Level& v0 = ctx->lv[0];
+    float* const caller_u = v0.u[0];
+    if (cfg.schedule == DI_SCHED_SINGLE) {
+        // no hierarchy: u = f on the mask, 0 elsewhere, then smoothing on level 0
+        DI_CUDA(ctx, launch_select(f, c, width, height, C, v0.u[0], s));
     } else {
-        top = Leff;  // fully known level: u = b there
-        Level& v = ctx->lv[top];
-        DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s));
-    }
-    for (int l = top - 1; l >= 0; --l) {
-        Level& v = ctx->lv[l];
-        Level& cv = ctx->lv[l + 1];
-        DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s));
-        st = S.run_oras(l, v.u[1], 0, v.u[0], cfg.local_iters, nullptr);
-        if (st) return st;
+        // 2. cascade (one-way multigrid from the coarsest level)
+        int top;
+        if (Leff == L) {
+            top = L - 1;
+            Level& v = ctx->lv[top];
+            S.root = top;
+            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s));
+            st = S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2);
+            if (st) return st;
+        } else {
+            top = Leff;  // fully known level: u = b there
+            Level& v = ctx->lv[top];
+            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s));
+        }
+        for (int l = top - 1; l >= 0; --l) {
+            Level& v = ctx->lv[l];
+            Level& cv = ctx->lv[l + 1];
+            S.root = l;
+            if (cfg.schedule == DI_SCHED_FULL_FMG) {
+                // full FMG: a V-cycle on every level of the cascade
+                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[0], 0, nullptr, s));
+                int which = 0;
+                st = S.vcycle(l, false, &which, nullptr);
+                if (st) return st;
+                if (which != 0) std::swap(v.u[0], v.u[1]);
+            } else {
+                // reduced FMG and multilevel: one smoothing step per level
+                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s));
+                st = S.smooth(l, v.u[1], 0, v.u[0], nullptr);
+                if (st) return st;
+            }
+        }
     }
 
-    // 3. V-cycles with the stop test
-    S.vcycle_phase = true;
-    Level& v0 = ctx->lv[0];
-    const int nslots = cfg.pre + 1 + cfg.post;
+    // 3. cycles on the finest level with the stop test: V-cycles (FMG
+    // schedules) or single smoothing steps (multilevel, single level)
+    S.root = 0;
+    const bool vcycles = cfg.schedule == DI_SCHED_REDUCED_FMG || cfg.schedule == DI_SCHED_FULL_FMG;
+    // CG smoothing on the finest level continues one CG run across the steps
+    // of the multilevel and single-level schedules (multilevel: from the
+    // cascade's level-0 call, which solves the same system)
+    bool cg_continue = cfg.schedule == DI_SCHED_MULTILEVEL;
+    const int nslots = vcycles ? cfg.pre + 1 + cfg.post : 1;
     float prevU = -1.f, prevQ = -1.f;
     int cycles = 0;
     bool converged = false;
@@ -537,12 +601,16 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     while (cycles < cfg.max_cycles) {
         DI_CUDA(ctx, cudaMemsetAsync(ctx->upd, 0, kMaxUpdSlots * sizeof(unsigned), s));
         int which = 0;
-        // The iterate lives in v0.u[0] (the caller's buffer) between cycles.
-        st = S.vcycle(0, false, &which, ctx->upd);
+        // the iterate lives in v0.u[0] between cycles (buffers swap by pointer)
+        if (vcycles) {
+            st = S.vcycle(0, false, &which, ctx->upd);
+        } else {
+            st = S.smooth(0, v0.u[0], 0, v0.u[1], ctx->upd, !cg_continue);
+            cg_continue = true;
+            which = 1;
+        }
         if (st) return st;
-        if (which != 0)
-            DI_CUDA(ctx, cudaMemcpyAsync(v0.u[0], v0.u[1], v0.n * C * sizeof(float),
-                                         cudaMemcpyDeviceToDevice, s));
+        if (which != 0) std::swap(v0.u[0], v0.u[1]);
         ++cycles;
         if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) continue;
         if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE) {
@@ -587,6 +655,11 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         DI_CUDA(ctx, cudaStreamSynchronize(s));
         converged = true;
     }
+    if (v0.u[0] != caller_u)
+        DI_CUDA(ctx, cudaMemcpyAsync(caller_u, v0.u[0], v0.n * C * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
+    if (cfg.stop_rule == DI_STOP_FIXED_CYCLES || v0.u[0] != caller_u)
+        DI_CUDA(ctx, cudaStreamSynchronize(s));
     prof_flush(ctx);
     ctx->stats.cycles = cycles;
     ctx->stats.converged = converged ? 1 : 0;

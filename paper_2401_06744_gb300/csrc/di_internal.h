@@ -88,6 +88,15 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev = nullptr, int precision = 0);
 
+// Global CG smoother: `steps` CG steps on the level's reduced system from the
+// iterate `in`, out = in + correction; restart = 0 continues the previous
+// call's CG state (r, p, sc, *step_par) on the same level.  r, p, q, x: C*w*h
+// floats each; sc: 4*C doubles; partials as for launch_residual.
+cudaError_t launch_cg_smooth(const float* in, int zero_in, const float* b, int rhs_zero,
+                             const uint8_t* c, int w, int h, int C, int steps, int restart,
+                             float* r, float* p, float* q, float* x, double* partials, double* sc,
+                             int* step_par, float* out, unsigned* maxupd, cudaStream_t s);
+
 // Host-side geometry shared with the kernels.
 inline int axis_blocks(int n, int B, int o) {
     const int s = B - o;

@@ -235,10 +235,11 @@ k_residual(const float* __restrict__ u, int zero_u, const float* __restrict__ b,
         rv = residual_at(u + ch * n, zero_u, b + ch * n, rhs_zero, c, w, h, x, y);
         if (r) r[ch * n + (size_t)y * w + x] = rv;
     }
+    // FP32 within the warp, FP64 across the warps and CTAs (fixed order)
     __shared__ double s_part[kResBX * kResBY / 32];
     const int t = threadIdx.y * kResBX + threadIdx.x;
-    double v = warp_sum_d((double)rv * (double)rv);
-    if ((t & 31) == 0) s_part[t >> 5] = v;
+    const float v = warp_sum(rv * rv);
+    if ((t & 31) == 0) s_part[t >> 5] = (double)v;
     __syncthreads();
     if (t == 0) {
         double s = 0.0;
@@ -262,6 +263,169 @@ k_reduce(const double* __restrict__ partials, int nparts, double* __restrict__ o
         double t = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
         out[ch] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Global CG on one level, the comparison smoother of Section 5 (CG in place of
+// ORAS, and single-level CG).  x is the correction of the iterate, r = b - A(u
+// + x) is kept by recurrence; p and r vanish on known pixels.  Per channel
+// the device keeps sc[ch * 4 + 0/1] = r.r of even/odd steps and sc[ch*4 + 2] =
+// p.Ap, so a step needs no host round trip.
+//
+// The kernels stride over 32x8 pixel tiles with a fixed number of CTAs per
+// channel (kCgCtas in total), so a dot product leaves one partial per CTA.
+// Products are summed in FP32 within a thread and a warp and in FP64 across
+// the warps and CTAs, all in a fixed order: GB300 issues FP64 at a small
+// fraction of its FP32 rate, and per-element FP64 arithmetic would dominate
+// these memory-bound passes.
+// ---------------------------------------------------------------------------
+
+constexpr int kCgBX = 32, kCgBY = 8, kCgCtas = 152 * 8;
+
+// Sum of one float per thread of a 256-thread CTA, written to
+// partials[ch * nparts + blockIdx.x]: FP32 within each warp, FP64 across the
+// eight warps in warp order.
+__device__ __forceinline__ void block_partial(float v, double* __restrict__ partials, int ch,
+                                              int nparts) {
+    __shared__ double s_p[kCgBX * kCgBY / 32];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    v = warp_sum(v);
+    if ((t & 31) == 0) s_p[t >> 5] = (double)v;
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0;
+        for (int i = 0; i < kCgBX * kCgBY / 32; ++i) a += s_p[i];
+        partials[(size_t)ch * nparts + blockIdx.x] = a;
+    }
+}
+
+struct CgTiles {
+    int w, h, tiles_x, ntiles;
+    __device__ __forceinline__ void pixel(int t, int* X, int* Y) const {
+        const int ty = t / tiles_x;
+        *X = (t - ty * tiles_x) * kCgBX + threadIdx.x;
+        *Y = ty * kCgBY + threadIdx.y;
+    }
+};
+
+__global__ void __launch_bounds__(kCgBX * kCgBY)
+k_cg_init(CgTiles g, const float* __restrict__ u, int zero_u, const float* __restrict__ b,
+          int rhs_zero, const uint8_t* __restrict__ c, float* __restrict__ r,
+          float* __restrict__ p, float* __restrict__ x, double* __restrict__ partials) {
+    const int ch = blockIdx.y;
+    const size_t n = (size_t)g.w * g.h;
+    float acc = 0.f;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        int X, Y;
+        g.pixel(t, &X, &Y);
+        if (X >= g.w || Y >= g.h) continue;
+        const size_t pix = (size_t)Y * g.w + X, i = ch * n + pix;
+        float rv = 0.f;
+        if (!c[pix])
+            rv = residual_at(u + ch * n, zero_u, b + ch * n, rhs_zero, c, g.w, g.h, X, Y);
+        r[i] = rv;
+        p[i] = rv;
+        x[i] = 0.f;
+        acc = fmaf(rv, rv, acc);
+    }
+    block_partial(acc, partials, ch, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kCgBX * kCgBY)
+k_cg_matvec(CgTiles g, const float* __restrict__ p, const uint8_t* __restrict__ c,
+            float* __restrict__ q, double* __restrict__ partials) {
+    const int ch = blockIdx.y;
+    const int w = g.w, h = g.h;
+    const size_t n = (size_t)w * h;
+    const float* pc = p + ch * n;
+    float acc = 0.f;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        int X, Y;
+        g.pixel(t, &X, &Y);
+        if (X >= w || Y >= h) continue;
+        const size_t pix = (size_t)Y * w + X;
+        float qv = 0.f;
+        if (!c[pix]) {
+            const float pv = pc[pix];
+            float sn = 0.f;
+            int deg = 0;
+            if (X > 0) { ++deg; sn += pc[pix - 1]; }
+            if (X < w - 1) { ++deg; sn += pc[pix + 1]; }
+            if (Y > 0) { ++deg; sn += pc[pix - w]; }
+            if (Y < h - 1) { ++deg; sn += pc[pix + w]; }
+            qv = (float)deg * pv - sn;  // known neighbours have p = 0
+            acc = fmaf(pv, qv, acc);
+        }
+        q[ch * n + pix] = qv;
+    }
+    block_partial(acc, partials, ch, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kCgBX * kCgBY)
+k_cg_update(CgTiles g, const float* __restrict__ p, const float* __restrict__ q,
+            float* __restrict__ x, float* __restrict__ r, const double* __restrict__ sc, int par,
+            double* __restrict__ partials) {
+    const int ch = blockIdx.y;
+    const size_t n = (size_t)g.w * g.h;
+    const double rr = sc[ch * 4 + par], pq = sc[ch * 4 + 2];
+    const float a = pq > 0.0 ? (float)(rr / pq) : 0.f;
+    float acc = 0.f;
+    for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+        int X, Y;
+        g.pixel(t, &X, &Y);
+        if (X >= g.w || Y >= g.h) continue;
+        const size_t i = ch * n + (size_t)Y * g.w + X;
+        x[i] = fmaf(a, p[i], x[i]);
+        const float rv = fmaf(-a, q[i], r[i]);
+        r[i] = rv;
+        acc = fmaf(rv, rv, acc);
+    }
+    block_partial(acc, partials, ch, gridDim.x);
+}
+
+__global__ void k_cg_direction(float* __restrict__ p, const float* __restrict__ r, size_t n,
+                               const double* __restrict__ sc, int par) {
+    const int ch = blockIdx.y;
+    const double rr_old = sc[ch * 4 + par], rr_new = sc[ch * 4 + (par ^ 1)];
+    const float beta = rr_old > 0.0 ? (float)(rr_new / rr_old) : 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        p[ch * n + i] = fmaf(beta, p[ch * n + i], r[ch * n + i]);
+}
+
+// out = in + x (in may be zero); the largest |x| goes into *maxupd (nullable)
+__global__ void k_cg_finish(const float* __restrict__ in, int zero_in,
+                            const float* __restrict__ x, float* __restrict__ out, size_t n,
+                            unsigned* __restrict__ maxupd) {
+    const int ch = blockIdx.y;
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float xv = x[ch * n + i];
+        out[ch * n + i] = (zero_in ? 0.f : in[ch * n + i]) + xv;
+        m = fmaxf(m, fabsf(xv));
+    }
+    if (maxupd) {
+        m = warp_max(m);
+        if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(maxupd, __float_as_uint(m));
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_reduce_slot(const double* __restrict__ partials, int nparts, double* __restrict__ sc, int slot) {
+    const int ch = blockIdx.x;
+    const double* pp = partials + (size_t)ch * nparts;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += pp[i];
+    __shared__ double s_w[8];
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
+        sc[ch * 4 + slot] = t;
     }
 }
 
@@ -1728,6 +1892,56 @@ cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C,
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
     k_select<<<dim3((unsigned)blocks, (unsigned)C), 256, 0, s>>>(b, c, n, u);
+    count();
+    return cudaGetLastError();
+}
+
+// Global CG smoother on one level: `steps` CG steps on A x = b - A in (known
+// pixels fixed), out = in + x.  With restart == 0 the state in (r, p, sc) of
+// the previous call on the same level continues (single-level CG).
+cudaError_t launch_cg_smooth(const float* in, int zero_in, const float* b, int rhs_zero,
+                             const uint8_t* c, int w, int h, int C, int steps, int restart,
+                             float* r, float* p, float* q, float* x, double* partials, double* sc,
+                             int* step_par, float* out, unsigned* maxupd, cudaStream_t s) {
+    CgTiles g;
+    g.w = w;
+    g.h = h;
+    g.tiles_x = (w + kCgBX - 1) / kCgBX;
+    g.ntiles = g.tiles_x * ((h + kCgBY - 1) / kCgBY);
+    int per_ch = kCgCtas / C;
+    if (per_ch > g.ntiles) per_ch = g.ntiles;
+    if (per_ch < 1) per_ch = 1;
+    const dim3 grid((unsigned)per_ch, (unsigned)C), blk(kCgBX, kCgBY);
+    const size_t n = (size_t)w * h;
+    size_t nb = (n + 255) / 256;
+    if (nb > 8192) nb = 8192;
+    cudaError_t e;
+    if (restart) {
+        k_cg_init<<<grid, blk, 0, s>>>(g, in, zero_in, b, rhs_zero, c, r, p, x, partials);
+        count();
+        k_reduce_slot<<<C, 256, 0, s>>>(partials, per_ch, sc, 0);
+        count();
+        *step_par = 0;
+    } else {
+        // continue: the correction restarts from zero on top of the new iterate
+        e = cudaMemsetAsync(x, 0, n * C * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 0; k < steps; ++k) {
+        const int par = *step_par;
+        k_cg_matvec<<<grid, blk, 0, s>>>(g, p, c, q, partials);
+        count();
+        k_reduce_slot<<<C, 256, 0, s>>>(partials, per_ch, sc, 2);
+        count();
+        k_cg_update<<<grid, blk, 0, s>>>(g, p, q, x, r, sc, par, partials);
+        count();
+        k_reduce_slot<<<C, 256, 0, s>>>(partials, per_ch, sc, par ^ 1);
+        count();
+        k_cg_direction<<<dim3((unsigned)nb, (unsigned)C), 256, 0, s>>>(p, r, n, sc, par);
+        count();
+        *step_par = par ^ 1;
+    }
+    k_cg_finish<<<dim3((unsigned)nb, (unsigned)C), 256, 0, s>>>(in, zero_in, x, out, n, maxupd);
     count();
     return cudaGetLastError();
 }
