@@ -287,7 +287,7 @@ def run_ours(args):
     steps_per = prof["oras_l0_cg_steps"] / n_l
     flop = (FLOP_PER_STEP * steps_per + FLOP_PER_LAUNCH) * pxch
     achieved = flop / (avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_oras_warp<32> (finest level)",
+    roofline = {"bound": "alu", "kernel": "k_oras_2w (32x32 ORAS blocks, finest level)",
                 "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "traffic": ORAS_TRAFFIC_BYTES, "avg_launch_us": round(avg_ms * 1e3, 1),

@@ -86,8 +86,8 @@ enum { DI_SMOOTH_ORAS = 0, DI_SMOOTH_CG = 1 };
 typedef struct {
     int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
     int overlap;      /* o, overlap of neighbouring blocks, 1..B/2 [6] (Section 3.1) */
-    int local_iters;  /* Jacobi-PCG steps of each local block solve [8] (Section 3.1) */
-    int coarse_iters; /* cap on the PCG steps of the single-block solve of the coarsest
+    int local_iters;  /* CG steps of each local block solve [8] (Section 3.1) */
+    int coarse_iters; /* cap on the CG steps of the single-block solve of the coarsest
                          level, which otherwise runs to a relative residual of ~1e-6 [2048] */
     int pre;          /* ORAS pre-smoothing iterations per V-cycle [1] (Section 4.4) */
     int post;         /* ORAS post-smoothing iterations per V-cycle [1] (Section 4.4) */

@@ -499,21 +499,21 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     // 1. pyramids and unknown counts
     unsigned long long* cnt = ctx->counts;
     DI_CUDA(ctx, cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s));
-    DI_CUDA(ctx, launch_count_mask(c, n0, cnt, s));  // cnt[0] known, cnt[1] unknown (level 0)
-    DI_CUDA(ctx, launch_pack_mask(c, width, height, ctx->lv[0].mbits, s));
+    // cnt[1 + l]: unknown pixels of level l
+    DI_CUDA(ctx, launch_pack_mask(c, width, height, ctx->lv[0].mbits, cnt + 1, s));
     for (int l = 1; l < L; ++l) {
         Level& f_ = ctx->lv[l - 1];
         Level& cv = ctx->lv[l];
-        DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), cnt + 1 + l, s));
+        DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), s));
         DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
                                         const_cast<float*>(cv.b), cfg.downsample == 0 ? 1 : 0, s));
-        DI_CUDA(ctx, launch_pack_mask(cv.c, cv.w, cv.h, cv.mbits, s));
+        DI_CUDA(ctx, launch_pack_mask(cv.c, cv.w, cv.h, cv.mbits, cnt + 1 + l, s));
     }
     unsigned long long* hcnt = static_cast<unsigned long long*>(ctx->host);
     DI_CUDA(ctx, cudaMemcpyAsync(hcnt, cnt, (L + 1) * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost, s));
     DI_CUDA(ctx, cudaStreamSynchronize(s));
-    if (hcnt[0] == 0) return DI_ERR_EMPTY_MASK;
+    if (hcnt[1] == (unsigned long long)n0) return DI_ERR_EMPTY_MASK;
     ctx->lv[0].unknowns = (long long)hcnt[1];
     int Leff = L;
     for (int l = 1; l < L; ++l) {
@@ -673,7 +673,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
 di_status di_mask_downsample(const uint8_t* c, int width, int height, uint8_t* cH,
                              void* stream) {
     if (!c || !cH || width < 1 || height < 1) return DI_ERR_INVALID_ARG;
-    cudaError_t e = launch_mask_down(c, width, height, cH, nullptr, static_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_mask_down(c, width, height, cH, static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
 }
 
@@ -754,7 +754,7 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     bind_levels(ctx, b, c, u_out, width, height, channels);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint32_t* bits = ctx->lv[0].mbits;
-    DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, s));
+    DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, nullptr, s));
     DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels,
                              ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
                              u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision));

@@ -21,14 +21,8 @@ long long launch_count();
 constexpr int kMaxLevels = 24;
 constexpr int kMaxUpdSlots = 16;
 
-// Count known (nonzero) and unknown pixels of a mask: out[0] += known,
-// out[1] += unknown.  out must be zeroed by the caller.
-cudaError_t launch_count_mask(const uint8_t* c, size_t n, unsigned long long* out,
-                              cudaStream_t s);
-
-// cH = 2x2 max pool of c; *unknownH += number of zero entries of cH (nullable).
-cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH,
-                             unsigned long long* unknownH, cudaStream_t s);
+// cH = 2x2 max pool of c.
+cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH, cudaStream_t s);
 
 // bH from (c, b, cH): modified (1) or naive (0) mask-value downsampling.
 cudaError_t launch_values_down(const uint8_t* c, const float* b, int w, int h, int C,
@@ -65,8 +59,10 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
                           cudaStream_t s);
 
-// Bit-packed mask (see mask_words_per_row) of c.
-cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cudaStream_t s);
+// Bit-packed mask (see mask_words_per_row) of c; *unknown (nullable, zeroed
+// by the caller) gains the number of unknown pixels.
+cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,
+                             unsigned long long* unknown, cudaStream_t s);
 
 // Floats of ORAS scratch for an image of w x h x C: four parity planes of
 // pixels shared along y, then the compact strips of pixels shared along x only.

@@ -97,48 +97,22 @@ __device__ __forceinline__ int axis_contrib(int g, int s, int o, int nb, int& k0
 // Mask pyramid (Section 4.3)
 // ---------------------------------------------------------------------------
 
-__global__ void k_count_mask(const uint8_t* __restrict__ c, size_t n,
-                             unsigned long long* __restrict__ out) {
-    unsigned known = 0, unknown = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        if (c[i]) ++known; else ++unknown;
-    }
-    for (int d = 16; d > 0; d >>= 1) {
-        known += __shfl_xor_sync(kFull, known, d);
-        unknown += __shfl_xor_sync(kFull, unknown, d);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (known) atomicAdd(&out[0], (unsigned long long)known);
-        if (unknown) atomicAdd(&out[1], (unsigned long long)unknown);
-    }
-}
-
 __global__ void k_mask_down(const uint8_t* __restrict__ c, int w, int h,
-                            uint8_t* __restrict__ cH, int wH, int hH,
-                            unsigned long long* __restrict__ unknownH) {
+                            uint8_t* __restrict__ cH, int wH, int hH) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-    bool unk = false;
-    if (X < wH && Y < hH) {
-        const int x = 2 * X, y = 2 * Y;
-        const bool x1 = x + 1 < w, y1 = y + 1 < h;
-        const uint8_t* row = c + (size_t)y * w;
-        bool m = row[x] != 0;
-        if (x1) m |= row[x + 1] != 0;
-        if (y1) {
-            const uint8_t* row2 = row + w;
-            m |= row2[x] != 0;
-            if (x1) m |= row2[x + 1] != 0;
-        }
-        cH[(size_t)Y * wH + X] = m ? 1 : 0;
-        unk = !m;
+    if (X >= wH || Y >= hH) return;
+    const int x = 2 * X, y = 2 * Y;
+    const bool x1 = x + 1 < w, y1 = y + 1 < h;
+    const uint8_t* row = c + (size_t)y * w;
+    bool m = row[x] != 0;
+    if (x1) m |= row[x + 1] != 0;
+    if (y1) {
+        const uint8_t* row2 = row + w;
+        m |= row2[x] != 0;
+        if (x1) m |= row2[x + 1] != 0;
     }
-    if (unknownH) {
-        const unsigned bal = __ballot_sync(kFull, unk);
-        const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-        if (lane == 0 && bal) atomicAdd(unknownH, (unsigned long long)__popc(bal));
-    }
+    cH[(size_t)Y * wH + X] = m ? 1 : 0;
 }
 
 // One coarse cell: weights of its (up to four) fine children.
@@ -624,18 +598,50 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Bit-packed mask: row y, word k covers columns [32k, 32k + 32); bit set =
 // known pixel or a column beyond the image.  wpr = words per row, including
-// one padding word so that two consecutive words can always be read.
-__global__ void k_pack_mask(const uint8_t* __restrict__ c, int w, int h,
-                            uint32_t* __restrict__ bits, int wpr) {
+// one padding word so that two consecutive words can always be read.  One
+// warp per word (lane = column), four words in flight per warp, persistent
+// warps; *unknown (nullable) gains the number of unknown pixels, with one
+// atomic per CTA.
+__global__ void __launch_bounds__(256)
+k_pack_mask(const uint8_t* __restrict__ c, int w, int h, uint32_t* __restrict__ bits, int wpr,
+            unsigned long long* __restrict__ unknown) {
     const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long total = (long long)h * wpr;
-    if (wid >= total) return;  // whole warp: wid is warp-uniform
-    const int y = (int)(wid / wpr), k = (int)(wid % wpr);
-    const int x = 32 * k + lane;
-    const bool known = x >= w || c[(size_t)y * w + x] != 0;
-    const unsigned word = __ballot_sync(kFull, known);
-    if (lane == 0) bits[wid] = word;
+    const int total = h * wpr;
+    const int nwarps = (int)gridDim.x * (int)(blockDim.x >> 5);
+    unsigned unk = 0;
+    for (int wid = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+         wid < total; wid += 4 * nwarps) {
+        bool known[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int wk = wid + k * nwarps;
+            known[k] = true;
+            if (wk < total) {
+                const int y = wk / wpr;
+                const int x = 32 * (wk - y * wpr) + lane;
+                known[k] = x >= w || c[(size_t)y * w + x] != 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int wk = wid + k * nwarps;
+            const unsigned word = __ballot_sync(kFull, known[k]);
+            if (wk < total) {  // warp-uniform
+                if (lane == 0) bits[wk] = word;
+                unk += (unsigned)__popc(~word);
+            }
+        }
+    }
+    if (unknown) {
+        __shared__ unsigned s_u[8];
+        if (lane == 0) s_u[threadIdx.x >> 5] = unk;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long a = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += s_u[i];
+            if (a) atomicAdd(unknown, a);
+        }
+    }
 }
 
 // One ORAS iteration, one warp per (block, channel) task.
@@ -1609,31 +1615,29 @@ k_combine_rows(const float* __restrict__ u_in, int zero_in, const float* __restr
     u_out[ch * n + gp] = acc;
 }
 
-// Pixels shared along x only: one thread per (row, seam) adds the two
-// contiguous strip entries of the left and right block.
-__global__ void __launch_bounds__(128)
+// Pixels shared along x only: thread (j, row) adds the strip entries of the
+// left and right block for pixel j of the seam's shared run in that row (j
+// fastest, so the strip reads of a warp are contiguous).
+__global__ void __launch_bounds__(256)
 k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
                int w, int h, int s, int o, int nbx, int nby, float inv_s,
                float* __restrict__ u_out) {
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = threadIdx.x;
+    const int y = blockIdx.x * blockDim.y + threadIdx.y;
     const int seam = (int)blockIdx.y + 1;
     const int ch = blockIdx.z, C = gridDim.z;
     if (y >= h) return;
+    const int x = seam * s + shared_first(o) + j;
+    if (x >= w) return;
     int ky0, ky1;
     if (axis_contrib(y, s, o, nby, ky0, ky1, inv_s) == 2) return;  // shared row: k_combine_rows
     const int nsh = shared_per_seam(o);
     const size_t n = (size_t)w * h;
     const float* strips = planes + 4 * (size_t)C * n;
     const size_t side = (size_t)C * (nbx - 1) * h * nsh;
-    const float* L = strips + (((size_t)ch * (nbx - 1) + (seam - 1)) * h + y) * nsh;
-    const float* R = L + side;
-    const int xb = seam * s + shared_first(o);
-    const size_t rowp = (size_t)y * w;
-    for (int j = 0; j < nsh; ++j) {  // L (left block) already carries u_in
-        const int x = xb + j;
-        if (x >= w) break;
-        u_out[ch * n + rowp + x] = L[j] + R[j];
-    }
+    const size_t at = (((size_t)ch * (nbx - 1) + (seam - 1)) * h + y) * nsh + j;
+    // the left block's entry already carries u_in
+    u_out[ch * n + (size_t)y * w + x] = strips[at] + strips[at + side];
 }
 
 inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
@@ -1764,9 +1768,11 @@ cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w,
     }
     const int nseams = nbx - 1;
     if (nsh > 0 && nbx > 1 && nseams > 0) {
-        dim3 grid_c((unsigned)((h + 127) / 128), (unsigned)nseams, (unsigned)C);
-        k_combine_cols<<<grid_c, 128, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby, inv_s,
-                                             u_out);
+        const int rows = 256 / nsh > 0 ? 256 / nsh : 1;
+        dim3 blk_c((unsigned)nsh, (unsigned)rows);
+        dim3 grid_c((unsigned)((h + rows - 1) / rows), (unsigned)nseams, (unsigned)C);
+        k_combine_cols<<<grid_c, blk_c, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby,
+                                               inv_s, u_out);
         count();
         e = cudaGetLastError();
     }
@@ -1779,22 +1785,11 @@ cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w,
 // Launch wrappers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_count_mask(const uint8_t* c, size_t n, unsigned long long* out,
-                              cudaStream_t s) {
-    size_t blocks = (n + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
-    k_count_mask<<<(unsigned)blocks, 256, 0, s>>>(c, n, out);
-    count();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH,
-                             unsigned long long* unknownH, cudaStream_t s) {
+cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH, cudaStream_t s) {
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    k_mask_down<<<grid2(wH, hH, blk), blk, 0, s>>>(c, w, h, cH, wH, hH, unknownH);
+    k_mask_down<<<grid2(wH, hH, blk), blk, 0, s>>>(c, w, h, cH, wH, hH);
     count();
     return cudaGetLastError();
 }
@@ -1946,11 +1941,15 @@ cudaError_t launch_cg_smooth(const float* in, int zero_in, const float* b, int r
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits, cudaStream_t s) {
-    const long long warps = (long long)h * mask_words_per_row(w);
-    const long long threads = warps * 32;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
-    k_pack_mask<<<blocks, 256, 0, s>>>(c, w, h, bits, mask_words_per_row(w));
+cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,
+                             unsigned long long* unknown, cudaStream_t s) {
+    const int wpr = mask_words_per_row(w);
+    const long long words = (long long)h * wpr;
+    if (words > 0x7fffffffLL) return cudaErrorInvalidValue;
+    long long blocks = (words + 31) / 32;  // 8 warps x 4 words per CTA pass
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    k_pack_mask<<<(unsigned)blocks, 256, 0, s>>>(c, w, h, bits, wpr, unknown);
     count();
     return cudaGetLastError();
 }
