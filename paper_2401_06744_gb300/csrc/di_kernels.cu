@@ -453,53 +453,64 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
     rH[ch * nH + P] = 4.f * sum / (float)cnt;
 }
 
-// One thread per coarse cell: the (up to) 2x2 fine pixels it is the nearest
-// parent of, each 9/16 of it, 3/16 of its two edge neighbours on the child's
-// side and 1/16 of the diagonal one (coarse indices clamped at the border).
-// mode 0: u = c ? b : P uH;  mode 1: u += c ? 0 : P uH.
+// Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
+// coarse cell, 3/16 of each of the two edge neighbours of the parent on the
+// child's side and 1/16 of the diagonal one (coarse indices clamped at the
+// border).  One thread per pair of fine pixels (2X, 2X+1) of one fine row y:
+// both have parent column X; the row blend takes coarse row Y = y/2 three
+// times and its neighbour on the child's side once, the column blend the
+// same with X-1 (left child) or X+1 (right child).
+// mode 0: u = c ? b : P uH;  mode 1: u += c ? 0 : P uH (largest |P uH| over
+// the updated pixels into *maxupd).  VEC: the pair is one 8-byte word of u
+// and b and one 2-byte word of c (w even, aligned base pointers).
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
           const uint8_t* __restrict__ c, int w, int h, float* __restrict__ u, int mode,
           unsigned* __restrict__ maxupd) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     float amax = 0.f;
-    if (X < wH && Y < hH) {
+    if (X < wH && y < h) {
         const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
-        const float* e = uH + ch * nH;
+        const int Y = y >> 1;
+        const int Yn = (y & 1) ? min(Y + 1, hH - 1) : max(Y - 1, 0);
+        const float* rc = uH + ch * nH + (size_t)Y * wH;
+        const float* rn = uH + ch * nH + (size_t)Yn * wH;
         const int Xl = max(X - 1, 0), Xr = min(X + 1, wH - 1);
-        const int Yu = max(Y - 1, 0), Yd = min(Y + 1, hH - 1);
-        const float* ru = e + (size_t)Yu * wH;
-        const float* rc = e + (size_t)Y * wH;
-        const float* rd = e + (size_t)Yd * wH;
-        const float cu_l = ru[Xl], cu_c = ru[X], cu_r = ru[Xr];
-        const float cc_l = rc[Xl], cc_c = rc[X], cc_r = rc[Xr];
-        const float cd_l = rd[Xl], cd_c = rd[X], cd_r = rd[Xr];
-        // vertical blends for the upper (y = 2Y) and lower (y = 2Y+1) child rows
-        const float vu_l = 3.f * cc_l + cu_l, vu_c = 3.f * cc_c + cu_c, vu_r = 3.f * cc_r + cu_r;
-        const float vd_l = 3.f * cc_l + cd_l, vd_c = 3.f * cc_c + cd_c, vd_r = 3.f * cc_r + cd_r;
-        float val[2][2];
-        val[0][0] = (3.f * vu_c + vu_l) * (1.f / 16.f);
-        val[0][1] = (3.f * vu_c + vu_r) * (1.f / 16.f);
-        val[1][0] = (3.f * vd_c + vd_l) * (1.f / 16.f);
-        val[1][1] = (3.f * vd_c + vd_r) * (1.f / 16.f);
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            const int y = 2 * Y + dy;
-            if (y >= h) continue;
+        const float v_l = 3.f * rc[Xl] + rn[Xl];
+        const float v_c = 3.f * rc[X] + rn[X];
+        const float v_r = 3.f * rc[Xr] + rn[Xr];
+        const float a0 = (3.f * v_c + v_l) * (1.f / 16.f);
+        const float a1 = (3.f * v_c + v_r) * (1.f / 16.f);
+        const int x = 2 * X;
+        const size_t p = (size_t)y * w + x;
+        float* uc = u + ch * n;
+        if (VEC) {
+            const uchar2 cm = *reinterpret_cast<const uchar2*>(c + p);
+            float2* up = reinterpret_cast<float2*>(uc + p);
+            if (mode == 0) {
+                float2 bv = make_float2(0.f, 0.f);
+                if (cm.x | cm.y) bv = *reinterpret_cast<const float2*>(b + ch * n + p);
+                *up = make_float2(cm.x ? bv.x : a0, cm.y ? bv.y : a1);
+            } else {
+                float2 uv = *up;
+                if (!cm.x) { uv.x += a0; amax = fabsf(a0); }
+                if (!cm.y) { uv.y += a1; amax = fmaxf(amax, fabsf(a1)); }
+                *up = uv;
+            }
+        } else {
 #pragma unroll
             for (int dx = 0; dx < 2; ++dx) {
-                const int x = 2 * X + dx;
-                if (x >= w) continue;
-                const size_t p = (size_t)y * w + x;
-                const float v = val[dy][dx];
-                if (c[p]) {
-                    if (mode == 0) u[ch * n + p] = b[ch * n + p];
+                if (x + dx >= w) break;
+                const float v = dx ? a1 : a0;
+                if (c[p + dx]) {
+                    if (mode == 0) uc[p + dx] = b[ch * n + p + dx];
                 } else if (mode == 0) {
-                    u[ch * n + p] = v;
+                    uc[p + dx] = v;
                 } else {
-                    u[ch * n + p] += v;
+                    uc[p + dx] += v;
                     amax = fmaxf(amax, fabsf(v));
                 }
             }
@@ -1874,8 +1885,16 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    k_prolong<<<grid2(wH, hH, blk, C), blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
-                                                    mode == 1 ? maxupd : nullptr);
+    const dim3 grid = grid2(wH, h, blk, C);  // one thread per fine pixel pair
+    const bool vec = (w % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) |
+                                       reinterpret_cast<uintptr_t>(b)) % 8 == 0) &&
+                     reinterpret_cast<uintptr_t>(c) % 2 == 0;
+    if (vec)
+        k_prolong<true><<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
+                                             mode == 1 ? maxupd : nullptr);
+    else
+        k_prolong<false><<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
+                                              mode == 1 ? maxupd : nullptr);
     count();
     return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ def _case(h, w, C, d, seed, nan=True):
     return f, fn, c
 
 
-SIZES = [(1, 1), (1, 9), (7, 1), (3, 5), (17, 33), (64, 64), (101, 67), (130, 257)]
+SIZES = [(1, 1), (1, 9), (7, 1), (3, 5), (17, 33), (64, 64), (101, 67), (130, 257), (66, 128), (2, 2)]
 
 
 @pytest.mark.parametrize("h,w", SIZES)
