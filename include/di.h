@@ -82,6 +82,14 @@ enum { DI_SCHED_REDUCED_FMG = 0, DI_SCHED_FULL_FMG = 1, DI_SCHED_MULTILEVEL = 2,
  * The single-block solve of the coarsest level always uses the block solver. */
 enum { DI_SMOOTH_ORAS = 0, DI_SMOOTH_CG = 1 };
 
+/* Launch of the finest-level V-cycles.  ON: each di_inpaint call captures one
+ * V-cycle as a CUDA graph (on a stream of the context, while the cascade
+ * runs) and replays it once per cycle, which removes the per-kernel launch
+ * gaps; used for the V-cycle schedules with pre + post even, otherwise (and
+ * if the capture fails) the kernels are launched one by one.  OFF: always
+ * one by one.  The results are identical. */
+enum { DI_GRAPH_ON = 0, DI_GRAPH_OFF = 1 };
+
 /* Solver configuration; a zero field takes the default in brackets. */
 typedef struct {
     int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
@@ -103,7 +111,7 @@ typedef struct {
                          the update of u are FP32 in every mode */
     int schedule;     /* DI_SCHED_* [DI_SCHED_REDUCED_FMG] */
     int smoother;     /* DI_SMOOTH_* [DI_SMOOTH_ORAS] */
-    int reserved[1];
+    int graph;        /* DI_GRAPH_*: replay of the finest-level V-cycle [DI_GRAPH_ON] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

@@ -21,6 +21,7 @@ STOP_ERROR_ESTIMATE, STOP_RELATIVE_RESIDUAL, STOP_FIXED_CYCLES = range(3)
 PREC_FP32, PREC_FP16, PREC_BF16 = range(3)
 SCHED_REDUCED_FMG, SCHED_FULL_FMG, SCHED_MULTILEVEL, SCHED_SINGLE = range(4)
 SMOOTH_ORAS, SMOOTH_CG = range(2)
+GRAPH_ON, GRAPH_OFF = range(2)
 
 
 class di_config(ctypes.Structure):
@@ -31,7 +32,7 @@ class di_config(ctypes.Structure):
                 ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("smoother", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class di_stats(ctypes.Structure):
@@ -390,7 +391,7 @@ def autotune(items, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=2, device=None,
     ms = ctypes.c_double()
     _check(load().di_autotune(ctypes.byref(base), int(device), arr, len(items), bl, len(blocks),
                               ov, len(overlaps), int(reps), ctypes.byref(best), ctypes.byref(ms)))
-    return {k: getattr(best, k) for k, _ in di_config._fields_ if k != "reserved"}, ms.value
+    return {k: getattr(best, k) for k, _ in di_config._fields_ }, ms.value
 
 
 class Server:

@@ -68,6 +68,17 @@ struct di_ctx {
     float* cg[4] = {nullptr, nullptr, nullptr, nullptr};
     double* cg_sc = nullptr;
     int cg_par = 0;
+    // CUDA graph of the finest-level V-cycle: captured on cap_stream once per
+    // di_inpaint call (while the cascade runs), updated into gexec and
+    // replayed once per cycle; its profiling events are gev (fixed handles)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool capturing = false;
+    static constexpr int kGPairs = 16;
+    cudaEvent_t gev[kGPairs][2] = {};
+    int g_pairs = 0;            // event pairs recorded by one replay
+    long long g_kernels = 0;    // kernels launched by one replay
+    long long g_oras = 0, g_pxch = 0, g_steps = 0;  // profile counters of one replay
 };
 
 namespace {
@@ -109,6 +120,7 @@ bool config_ok(const di_config& c) {
     if (c.precision < 0 || c.precision > 2) return false;
     if (c.schedule < 0 || c.schedule > 3) return false;
     if (c.smoother < 0 || c.smoother > 1) return false;
+    if (c.graph < 0 || c.graph > 1) return false;
     return true;
 }
 
@@ -124,8 +136,22 @@ void prof_flush(di_ctx* ctx) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess)
             ctx->prof.oras_l0_ms += ms;
+        else
+            cudaGetLastError();  // a missing time is not an error of the next call
     }
     ctx->ev_used = 0;
+}
+
+// Add the durations of the event pairs of the last graph replay (the stream
+// has been synchronised) and that replay's counters to the profile.
+void prof_flush_graph(di_ctx* ctx) {
+    for (int i = 0; i < ctx->g_pairs; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->gev[i][0], ctx->gev[i][1]) == cudaSuccess)
+            ctx->prof.oras_l0_ms += ms;
+        else
+            cudaGetLastError();
+    }
 }
 
 #define DI_CUDA(ctx, call)                                  \
@@ -269,13 +295,20 @@ struct Sched {
             if (!ctx->ev_made) {
                 for (int i = 0; i < di_ctx::kEvPairs; ++i)
                     for (int k = 0; k < 2; ++k) DI_CUDA(ctx, cudaEventCreate(&ctx->ev[i][k]));
+                for (int i = 0; i < di_ctx::kGPairs; ++i)
+                    for (int k = 0; k < 2; ++k) DI_CUDA(ctx, cudaEventCreate(&ctx->gev[i][k]));
                 ctx->ev_made = true;
             }
-            if (ctx->ev_used == di_ctx::kEvPairs) {
-                DI_CUDA(ctx, cudaStreamSynchronize(s));
-                prof_flush(ctx);
+            if (ctx->capturing) {
+                // a graph node: the pair is read after every replay
+                if (ctx->g_pairs < di_ctx::kGPairs) ev = ctx->gev[ctx->g_pairs++];
+            } else {
+                if (ctx->ev_used == di_ctx::kEvPairs) {
+                    DI_CUDA(ctx, cudaStreamSynchronize(s));
+                    prof_flush(ctx);
+                }
+                ev = ctx->ev[ctx->ev_used++];
             }
-            ev = ctx->ev[ctx->ev_used++];
             ctx->prof.oras_l0_launches += 1;
             ctx->prof.oras_l0_pixel_channels += (long long)v.n * C;
             ctx->prof.oras_l0_cg_steps += iters;
@@ -356,6 +389,66 @@ struct Sched {
     }
 };
 
+// Capture one finest-level V-cycle (with the reset of the update slots) as a
+// CUDA graph and make ctx->gexec replay it.  The cycle must leave the iterate
+// in lv[0].u[0] (pre + post even).  Nothing runs during the capture; on any
+// failure the caller falls back to launching the cycle kernel by kernel.
+bool capture_vcycle(di_ctx* ctx, Sched& S) {
+    if (!ctx->cap_stream &&
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const di_profile p0 = ctx->prof;
+    const long long k0 = launch_count();
+    cudaStream_t s = S.s;
+    ctx->g_pairs = 0;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    ctx->capturing = true;
+    S.s = ctx->cap_stream;
+    int which = -1;
+    di_status st = DI_OK;
+    if (cudaMemsetAsync(ctx->upd, 0, kMaxUpdSlots * sizeof(unsigned), ctx->cap_stream) !=
+        cudaSuccess)
+        st = DI_ERR_CUDA;
+    if (st == DI_OK) st = S.vcycle(0, false, &which, ctx->upd);
+    S.s = s;
+    ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->g_kernels = launch_count() - k0;
+    add_launches(-ctx->g_kernels);  // captured, not launched
+    ctx->g_oras = ctx->prof.oras_l0_launches - p0.oras_l0_launches;
+    ctx->g_pxch = ctx->prof.oras_l0_pixel_channels - p0.oras_l0_pixel_channels;
+    ctx->g_steps = ctx->prof.oras_l0_cg_steps - p0.oras_l0_cg_steps;
+    ctx->prof = p0;
+    if (st != DI_OK || e != cudaSuccess || g == nullptr || which != 0) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        ctx->err[0] = 0;
+        return false;
+    }
+    bool ok = true;
+    if (ctx->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ctx->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+    }
+    if (!ctx->gexec && cudaGraphInstantiate(&ctx->gexec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->gexec = nullptr;
+        ok = false;
+    }
+    cudaGraphDestroy(g);
+    return ok;
+}
+
 float bits_to_float(unsigned b) {
     float f;
     std::memcpy(&f, &b, sizeof f);
@@ -429,9 +522,14 @@ void di_destroy(di_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_workspace(ctx);
-    if (ctx->ev_made)
+    if (ctx->ev_made) {
         for (int i = 0; i < di_ctx::kEvPairs; ++i)
             for (int k = 0; k < 2; ++k) cudaEventDestroy(ctx->ev[i][k]);
+        for (int i = 0; i < di_ctx::kGPairs; ++i)
+            for (int k = 0; k < 2; ++k) cudaEventDestroy(ctx->gev[i][k]);
+    }
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->norm2) cudaFree(ctx->norm2);
     if (ctx->counts) cudaFree(ctx->counts);
     if (ctx->upd) cudaFree(ctx->upd);
@@ -577,6 +675,10 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     // schedules) or single smoothing steps (multilevel, single level)
     S.root = 0;
     const bool vcycles = cfg.schedule == DI_SCHED_REDUCED_FMG || cfg.schedule == DI_SCHED_FULL_FMG;
+    // replay the finest-level V-cycle as a CUDA graph, captured while the
+    // cascade (already queued) runs
+    const bool graph = vcycles && cfg.graph == DI_GRAPH_ON && (cfg.pre + cfg.post) % 2 == 0 &&
+                       cfg.max_cycles > 0 && capture_vcycle(ctx, S);
     // CG smoothing on the finest level continues one CG run across the steps
     // of the multilevel and single-level schedules (multilevel: from the
     // cascade's level-0 call, which solves the same system)
@@ -599,8 +701,23 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         for (int k = 0; k < C; ++k) bnorm2[k] = hnorm[k];
     }
     while (cycles < cfg.max_cycles) {
-        DI_CUDA(ctx, cudaMemsetAsync(ctx->upd, 0, kMaxUpdSlots * sizeof(unsigned), s));
         int which = 0;
+        if (graph) {
+            DI_CUDA(ctx, cudaGraphLaunch(ctx->gexec, s));
+            add_launches(ctx->g_kernels);
+            ctx->prof.oras_l0_launches += ctx->g_oras;
+            ctx->prof.oras_l0_pixel_channels += ctx->g_pxch;
+            ctx->prof.oras_l0_cg_steps += ctx->g_steps;
+            if (cfg.profile && cfg.stop_rule == DI_STOP_FIXED_CYCLES) {
+                // the replay's event pairs are re-recorded by the next one
+                DI_CUDA(ctx, cudaStreamSynchronize(s));
+                prof_flush_graph(ctx);
+            }
+            ++cycles;
+            if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) continue;
+            goto stop_test;
+        }
+        DI_CUDA(ctx, cudaMemsetAsync(ctx->upd, 0, kMaxUpdSlots * sizeof(unsigned), s));
         // the iterate lives in v0.u[0] between cycles (buffers swap by pointer)
         if (vcycles) {
             st = S.vcycle(0, false, &which, ctx->upd);
@@ -613,11 +730,13 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         if (which != 0) std::swap(v0.u[0], v0.u[1]);
         ++cycles;
         if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) continue;
+    stop_test:
         if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE) {
             DI_CUDA(ctx, cudaMemcpyAsync(hupd, ctx->upd, nslots * sizeof(unsigned),
                                          cudaMemcpyDeviceToHost, s));
             DI_CUDA(ctx, cudaStreamSynchronize(s));
             prof_flush(ctx);
+            if (graph) prof_flush_graph(ctx);
             float U = 0.f;
             for (int k = 0; k < nslots; ++k) U += bits_to_float(reinterpret_cast<unsigned*>(hupd)[k]);
             if (!std::isfinite(U)) { est = INFINITY; prevU = -1.f; prevQ = -1.f; }
@@ -642,6 +761,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
                                          cudaMemcpyDeviceToHost, s));
             DI_CUDA(ctx, cudaStreamSynchronize(s));
             prof_flush(ctx);
+            if (graph) prof_flush_graph(ctx);
             bool ok = true;
             for (int k = 0; k < C; ++k) {
                 const double rr = bnorm2[k] > 0 ? std::sqrt(hnorm[k] / bnorm2[k]) : 0.0;

@@ -18,6 +18,9 @@ inline int axis_blocks_decl(int n, int B, int o) {
 
 // Kernels enqueued by the launch wrappers below (process-wide counter).
 long long launch_count();
+// Adjust the launch counter (graph replays add their kernels, captures that
+// launched nothing take theirs back).
+void add_launches(long long k);
 constexpr int kMaxLevels = 24;
 constexpr int kMaxUpdSlots = 16;
 

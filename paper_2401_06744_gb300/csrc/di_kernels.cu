@@ -43,6 +43,7 @@ namespace di {
 
 static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 namespace {
 
@@ -1651,6 +1652,16 @@ k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restr
     u_out[ch * n + (size_t)y * w + x] = strips[at] + strips[at + side];
 }
 
+// Timing event on s; inside a stream capture it becomes an event record node
+// of the graph (recorded by every replay).
+void record_event(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
     return dim3((unsigned)((w + blk.x - 1) / blk.x), (unsigned)((h + blk.y - 1) / blk.y),
                 (unsigned)z);
@@ -1711,11 +1722,11 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     const int chan_inner = nblk >= slots ? 1 : 0;
     int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
     if (grid < 1) grid = 1;
-    if (ev) cudaEventRecord(ev[0], s);
+    if (ev) record_event(ev[0], s);
     kern<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, nbx, nby,
                                 alpha, iters, rtol2, u_out, planes, maxupd, chan_inner);
     count();
-    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);
@@ -1751,12 +1762,12 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     const int chan_inner = nblk >= slots ? 1 : 0;
     int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
     if (grid < 1) grid = 1;
-    if (ev) cudaEventRecord(ev[0], s);
+    if (ev) record_event(ev[0], s);
     k_oras_warp<B><<<grid, 32, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
                                           nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
                                           chan_inner);
     count();
-    if (ev) cudaEventRecord(ev[1], s);
+    if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);

@@ -148,3 +148,45 @@ def test_bad_schedule_and_smoother_rejected(di):
         di.Context(schedule=4)
     with pytest.raises(Exception):
         di.Context(smoother=2)
+
+
+@pytest.mark.parametrize("stop", ["estimate", "residual", "fixed"])
+def test_graph_replay_matches_direct_launches(di, case, stop):
+    # the finest-level V-cycle replayed as a CUDA graph gives the same bits,
+    # cycle count, launch count and profile counters as launching it kernel by
+    # kernel
+    f, c, _ = case
+    rule = {"estimate": di.STOP_ERROR_ESTIMATE, "residual": di.STOP_RELATIVE_RESIDUAL,
+            "fixed": di.STOP_FIXED_CYCLES}[stop]
+    tol = 1e-4 if stop == "residual" else TOL
+    res = {}
+    for mode in (di.GRAPH_ON, di.GRAPH_OFF):
+        with di.Context(graph=mode, stop_rule=rule, max_cycles=5, profile=1) as ctx:
+            ft, ct = torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV)
+            for _ in range(2):  # the second call updates the cached graph
+                ctx.reset_profile()
+                u, st = ctx.inpaint(ft, ct, tol=tol)
+                torch.cuda.synchronize()
+            res[mode] = (u.cpu().numpy(), st, ctx.stats(), ctx.profile())
+    (u0, s0, st0, p0), (u1, s1, st1, p1) = res[di.GRAPH_ON], res[di.GRAPH_OFF]
+    assert s0 == s1 and st0["cycles"] == st1["cycles"]
+    assert np.array_equal(u0, u1)
+    assert p0["launches"] == p1["launches"] and p0["launches"] > 0
+    assert p0["oras_l0_launches"] == p1["oras_l0_launches"]
+    assert p0["oras_l0_cg_steps"] == p1["oras_l0_cg_steps"]
+    assert p0["oras_l0_ms"] > 0 and p1["oras_l0_ms"] > 0
+
+
+def test_graph_follows_changing_inputs(di):
+    # one context, frames of different sizes and masks in turn: every result
+    # equals a fresh context's (the cached graph is updated or rebuilt)
+    cases = [synth.make_case(w, h, 3, d, k, 70 + i) for i, (w, h, d, k) in
+             enumerate([(160, 96, 0.05, "edge"), (160, 96, 0.02, "uniform"),
+                        (200, 120, 0.05, "edge"), (160, 96, 0.05, "edge")])]
+    with di.Context() as ctx:
+        for f, c in cases:
+            u, st = ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), tol=TOL)
+            torch.cuda.synchronize()
+            ref, st2, _ = _run(di, f, c, TOL, graph=di.GRAPH_OFF)
+            assert st == st2 == di.OK
+            assert np.array_equal(u.cpu().numpy(), ref)
