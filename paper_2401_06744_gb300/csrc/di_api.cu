@@ -315,7 +315,8 @@ struct Sched {
         }
         DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.mbits, v.w, v.h, C, ctx->cfg.block,
                                  ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
-                                 ctx->planes, maxupd, s, ev, ctx->cfg.precision));
+                                 ctx->planes, maxupd, s, ev, ctx->cfg.precision,
+                                 ctx->upd + kMaxUpdSlots));
         return DI_OK;
     }
 
@@ -449,6 +450,12 @@ bool capture_vcycle(di_ctx* ctx, Sched& S) {
     return ok;
 }
 
+di_status timeout(di_ctx* ctx) {
+    std::snprintf(ctx->err, sizeof ctx->err,
+                  "a bounded device-side wait of the block kernel ran out (tile copies missing)");
+    return DI_ERR_TIMEOUT;
+}
+
 float bits_to_float(unsigned b) {
     float f;
     std::memcpy(&f, &b, sizeof f);
@@ -506,7 +513,9 @@ di_status di_create(const di_config* cfg, int device, di_ctx** out) {
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->norm2, kMaxChannels * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counts, (kMaxLevels + 1) * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->upd, kMaxUpdSlots * sizeof(unsigned));
+    // update slots, then one word: the device-side error flag (timed-out waits)
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->upd, (kMaxUpdSlots + 1) * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->upd, 0, (kMaxUpdSlots + 1) * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->cg_sc, 4 * kMaxChannels * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host, 4096);
     if (e != cudaSuccess) {
@@ -597,6 +606,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     // 1. pyramids and unknown counts
     unsigned long long* cnt = ctx->counts;
     DI_CUDA(ctx, cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s));
+    DI_CUDA(ctx, cudaMemsetAsync(ctx->upd + kMaxUpdSlots, 0, sizeof(unsigned), s));
     // cnt[1 + l]: unknown pixels of level l
     DI_CUDA(ctx, launch_pack_mask(c, width, height, ctx->lv[0].mbits, cnt + 1, s));
     for (int l = 1; l < L; ++l) {
@@ -732,11 +742,12 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         if (cfg.stop_rule == DI_STOP_FIXED_CYCLES) continue;
     stop_test:
         if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE) {
-            DI_CUDA(ctx, cudaMemcpyAsync(hupd, ctx->upd, nslots * sizeof(unsigned),
+            DI_CUDA(ctx, cudaMemcpyAsync(hupd, ctx->upd, (kMaxUpdSlots + 1) * sizeof(unsigned),
                                          cudaMemcpyDeviceToHost, s));
             DI_CUDA(ctx, cudaStreamSynchronize(s));
             prof_flush(ctx);
             if (graph) prof_flush_graph(ctx);
+            if (reinterpret_cast<unsigned*>(hupd)[kMaxUpdSlots]) return timeout(ctx);
             float U = 0.f;
             for (int k = 0; k < nslots; ++k) U += bits_to_float(reinterpret_cast<unsigned*>(hupd)[k]);
             if (!std::isfinite(U)) { est = INFINITY; prevU = -1.f; prevQ = -1.f; }
@@ -778,8 +789,13 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     if (v0.u[0] != caller_u)
         DI_CUDA(ctx, cudaMemcpyAsync(caller_u, v0.u[0], v0.n * C * sizeof(float),
                                      cudaMemcpyDeviceToDevice, s));
-    if (cfg.stop_rule == DI_STOP_FIXED_CYCLES || v0.u[0] != caller_u)
+    if (cfg.stop_rule != DI_STOP_ERROR_ESTIMATE || v0.u[0] != caller_u) {
+        unsigned* hflag = static_cast<unsigned*>(ctx->host) + 1000;
+        DI_CUDA(ctx, cudaMemcpyAsync(hflag, ctx->upd + kMaxUpdSlots, sizeof(unsigned),
+                                     cudaMemcpyDeviceToHost, s));
         DI_CUDA(ctx, cudaStreamSynchronize(s));
+        if (*hflag) return timeout(ctx);
+    }
     prof_flush(ctx);
     ctx->stats.cycles = cycles;
     ctx->stats.converged = converged ? 1 : 0;
@@ -877,7 +893,8 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, nullptr, s));
     DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels,
                              ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
-                             u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision));
+                             u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision,
+                             ctx->upd + kMaxUpdSlots));
     return DI_OK;
 }
 

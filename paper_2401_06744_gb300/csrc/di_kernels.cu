@@ -31,11 +31,13 @@
 #include "di_internal.h"
 
 #include <cfloat>
+#include <cstring>
 #include <cmath>
 
 #include <atomic>
 #include <mutex>
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the runtime)
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -994,17 +996,71 @@ struct Tile2W {
     static constexpr int FIXED = 2 * TILE + B;
 };
 
+// Shared-memory layout of the FP32 kernel (floats, from a 128-byte aligned
+// base): two u tiles of TH rows with pitch PU (a 40-wide TMA box, or the
+// 34-wide cp.async copy at column 0), the row weights, then two right-hand
+// side tiles of B rows with pitch PB (36-wide TMA box).  Tile strides are
+// multiples of 128 bytes, the alignment of a TMA destination.
+struct Smem2W {
+    static constexpr int B = 32, TH = 34, PU = 40, PB = 36;
+    static constexpr int USTRIDE = 1376;            // >= TH * PU, 128-byte multiple
+    static constexpr int BSTRIDE = B * PB;          // 1152 floats = 4608 bytes
+    static constexpr int WY = 2 * USTRIDE;          // row weights (32 floats)
+    static constexpr int RHS = WY + 32;             // 128-byte aligned
+    static constexpr int TMA_U_BYTES = TH * PU * 4; // 5440
+    static constexpr int TMA_B_BYTES = B * PB * 4;  // 4608
+    static size_t bytes(bool rhs) { return 128 + 4 * (size_t)(RHS + (rhs ? 2 * BSTRIDE : 0)); }
+};
+
+// Bounded wait for phase `parity` of the mbarrier at shared address `bar`;
+// false if it did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    for (int n = 0; n < (1 << 20); ++n) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y,
+                                            int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];"
+        :
+        : "r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+          "r"(bar)
+        : "memory");
+}
+
+// use_tma: the tiles come by TMA (tm_u over u_in, tm_b over rhs, both FP32
+// [C][h][w] with w a multiple of 4); otherwise by 4-byte cp.async.  errflag:
+// set to 1 if a TMA wait ran out (the CTA then stops).
 __global__ void __launch_bounds__(64, 8)
 k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
           int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
           int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
-          float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner) {
-    constexpr int B = 32, NP = 8, TH = Tile2W::TH, P = Tile2W::P, TILE = Tile2W::TILE;
-    extern __shared__ float smem[];
-    float* const s_u = smem;                     // [2][TH][P]
-    float* const s_wy = smem + 2 * TILE;         // [B]
-    float* const s_b = smem + Tile2W::FIXED;     // [2][B][B] if rhs_zero == 0
+          float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
+          const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
+          int use_tma, unsigned* __restrict__ errflag) {
+    constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
+    constexpr int TILE = Smem2W::USTRIDE;
+    extern __shared__ float smem_raw[];
+    float* const smem = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    float* const s_u = smem;                     // [2][USTRIDE]
+    float* const s_wy = smem + Smem2W::WY;       // [B]
+    float* const s_b = smem + Smem2W::RHS;       // [2][BSTRIDE] if rhs_zero == 0
     __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
+    __shared__ __align__(8) unsigned long long s_bar[2];
 
     const int t = threadIdx.x;
     const int lane = t & 31, wi = t >> 5;
@@ -1033,7 +1089,26 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
     auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
-        if (!zero_in) {
+        if (use_tma) {
+            if (t == 0) {
+                const unsigned bar =
+                    (unsigned)__cvta_generic_to_shared(&s_bar[bs]);
+                const unsigned bytes = (zero_in ? 0u : (unsigned)Smem2W::TMA_U_BYTES) +
+                                       (rhs_zero ? 0u : (unsigned)Smem2W::TMA_B_BYTES);
+                // the buffer's previous contents were read before the loop-top barrier
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(bar), "r"(bytes) : "memory");
+                // x must be a multiple of 4 elements (16 bytes): round the
+                // halo column down; the tile is indexed from the remainder
+                if (!zero_in)
+                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_u + bs * TILE), &tm_u,
+                                (px0 - 1) & ~3, py0 - 1, ch, bar);
+                if (!rhs_zero)
+                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_b + bs * Smem2W::BSTRIDE),
+                                &tm_b, px0 & ~3, py0, ch, bar);
+            }
+        } else if (!zero_in) {
             // thread t copies tile column lane of the rows ty = wi, wi + 2, ...
             // (and column 32 + lane for lane < 2)
             const float* src = u_in + ch * n;
@@ -1051,18 +1126,18 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                     cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
             }
         }
-        if (!rhs_zero) {
+        if (!use_tma && !rhs_zero) {
             const float* src = rhs + ch * n;
-            float* dst = s_b + bs * B * B;
+            float* dst = s_b + bs * Smem2W::BSTRIDE;
             const int gx = px0 + lane;
 #pragma unroll 4
             for (int ly = wi; ly < B; ly += 2) {
                 const int gy = py0 + ly;
                 const bool ok = gx < w && gy < h;
-                cp_async4(dst + ly * B + lane, ok ? src + (size_t)gy * w + gx : src, ok);
+                cp_async4(dst + ly * PB + lane, ok ? src + (size_t)gy * w + gx : src, ok);
             }
         }
-        cp_async_commit();
+        if (!use_tma) cp_async_commit();
         if (blk != have_blk && lane < 16) {
             const int gy = py0 + row0 + lane;
             if (gy < h) {
@@ -1077,6 +1152,13 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 
     int blk, ch;
     if (!task_of(0, blk, ch)) return;  // block-uniform
+    if (use_tma && t == 0) {
+        for (int b = 0; b < 2; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
+                         :: "r"((unsigned)__cvta_generic_to_shared(&s_bar[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned phase = 0;  // bit b: parity of the next completion of s_bar[b]
     prefetch(blk, ch, 0, -1);
     int buf = 0, cur_blk = -1;
     f2 ndg[NP], keep[NP];
@@ -1086,8 +1168,20 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     float vmax = 0.f;
 
     for (int i = 0;; ++i) {
-        cp_async_wait_all();
-        __syncthreads();
+        if (use_tma) {
+            const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[buf]);
+            bool ok = mbar_wait(bar, (phase >> buf) & 1u);
+            phase ^= 1u << buf;
+            if (__syncthreads_or(!ok)) {
+                // give the copy one more bounded wait before the CTA leaves
+                if (!ok) mbar_wait(bar, ((phase >> buf) & 1u) ^ 1u);
+                if (t == 0 && errflag) atomicExch(errflag, 1u);
+                return;
+            }
+        } else {
+            cp_async_wait_all();
+            __syncthreads();
+        }
         const uint32_t mlo = nlo, mhi = nhi;
         int nb2, nc2;
         const bool more = task_of(i + 1, nb2, nc2);
@@ -1132,8 +1226,11 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             // s_wy is read only after the barriers of the CG below
         }
 
-        const float* tu = s_u + buf * TILE;
-        const float* tb = s_b + buf * B * B;
+        // TMA tiles start at the 4-aligned column below the halo column
+        const int du = use_tma ? ((x0 - 1) & 3) : 0;
+        const int db = use_tma ? (x0 & 3) : 0;
+        const float* tu = s_u + buf * TILE + du;
+        const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
 
         f2 x[NP], r[NP], p[NP], q[NP];
         f2 acc0 = 0ull, acc1 = 0ull;
@@ -1143,7 +1240,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int ly = row0 + k + 8 * e, gy = y0 + ly;
-                float v = rhs_zero ? 0.f : tb[ly * B + col];
+                float v = rhs_zero ? 0.f : tb[ly * PB + col];
                 if (!zero_in) {
                     const float* c0 = tu + (ly + 1) * P + col + 1;
                     const float dv = (float)((gy > 0) + (gy < h - 1));
@@ -1670,61 +1767,120 @@ inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
 cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
                            int B, int o, int nbx, int nby, float* u_out, cudaStream_t s);
 
-typedef void (*Oras2wKernel)(const float*, int, const float*, int, const uint32_t*, int, int, int,
-                             int, int, int, int, float, int, float, float*, float*, unsigned*,
-                             int);
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// precision: 0 FP32, 1 FP16, 2 BF16 local iterates
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of an FP32 [C][h][w] image with a (bw x bh x 1) box; false if
+// the image does not meet TMA's rules (w a multiple of 4, 16-byte base).
+bool make_map(CUtensorMap* m, const float* base, int w, int h, int C, int bw, int bh) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || !base || w % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)C};
+    const cuuint64_t strides[2] = {(cuuint64_t)w * 4, (cuuint64_t)w * h * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// occupancy per (kernel, shared-memory size), cached
+int cached_occupancy(const void* kern, int threads, size_t smem, size_t smem_max, int* nsm_out) {
+    static std::mutex occ_mu;
+    static int nsm = 0;
+    static const void* occ_fn[16] = {};
+    static size_t occ_key[16] = {};
+    static int occ_val[16] = {};
+    std::lock_guard<std::mutex> occ_lock(occ_mu);
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    *nsm_out = nsm;
+    for (int i = 0; i < 16; ++i)
+        if (occ_fn[i] == kern && occ_key[i] == smem) return occ_val[i];
+    int oc = 0;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, kern, threads, smem);
+    if (oc < 1) oc = 1;
+    for (int i = 0; i < 16; ++i)
+        if (occ_fn[i] == nullptr) {
+            occ_fn[i] = kern;
+            occ_key[i] = smem;
+            occ_val[i] = oc;
+            break;
+        }
+    return oc;
+}
+
+// precision: 0 FP32 (tiles by TMA where the image allows it), 1 FP16, 2 BF16
+// local iterates
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                           cudaStream_t s, cudaEvent_t* ev, int precision) {
+                           cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag) {
     constexpr int B = 32;
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
-    const size_t smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) *
-                        sizeof(float);
-    const Oras2wKernel kern = precision == 1 ? k_oras_2w_h<HalfT>
-                              : precision == 2 ? k_oras_2w_h<Bf16T>
-                                               : k_oras_2w;
-    // occupancy per (kernel, shared-memory size), cached
-    static std::mutex occ_mu;
-    static int nsm = 0;
-    static const void* occ_fn[12] = {};
-    static size_t occ_key[12] = {};
-    static int occ_val[12] = {};
-    int oc = 0;
-    {
-        std::lock_guard<std::mutex> occ_lock(occ_mu);
-        if (nsm == 0) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        }
-        for (int i = 0; i < 12; ++i)
-            if (occ_fn[i] == (const void*)kern && occ_key[i] == smem) oc = occ_val[i];
-        if (oc == 0) {
-            const size_t mx = ((size_t)Tile2W::FIXED + (size_t)2 * B * B) * sizeof(float);
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, kern, 64, smem);
-            if (oc < 1) oc = 1;
-            for (int i = 0; i < 12; ++i)
-                if (occ_fn[i] == nullptr) {
-                    occ_fn[i] = (const void*)kern;
-                    occ_key[i] = smem;
-                    occ_val[i] = oc;
-                    break;
-                }
-        }
+    const int nblk = nbx * nby;
+    int nsm = 0, oc = 0;
+    size_t smem = 0;
+    const void* kern = nullptr;
+    CUtensorMap tm_u, tm_b;
+    std::memset(&tm_u, 0, sizeof tm_u);
+    std::memset(&tm_b, 0, sizeof tm_b);
+    int use_tma = 0;
+    if (precision == 0) {
+        use_tma = (!zero_in || !rhs_zero) &&
+                  (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
+                  (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
+        smem = Smem2W::bytes(!rhs_zero);
+        kern = (const void*)k_oras_2w;
+        oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true), &nsm);
+    } else {
+        smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) * sizeof(float);
+        kern = precision == 1 ? (const void*)k_oras_2w_h<HalfT> : (const void*)k_oras_2w_h<Bf16T>;
+        oc = cached_occupancy(kern, 64, smem, ((size_t)Tile2W::FIXED + (size_t)2 * B * B) *
+                                                  sizeof(float), &nsm);
     }
     const int slots = nsm * oc;
-    const int nblk = nbx * nby;
     const int chan_inner = nblk >= slots ? 1 : 0;
     int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
     if (grid < 1) grid = 1;
     if (ev) record_event(ev[0], s);
-    kern<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, nbx, nby,
-                                alpha, iters, rtol2, u_out, planes, maxupd, chan_inner);
+    if (precision == 0)
+        k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
+                                         nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
+                                         chan_inner, tm_u, tm_b, use_tma, errflag);
+    else if (precision == 1)
+        k_oras_2w_h<HalfT><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
+                                                  C, o, nbx, nby, alpha, iters, rtol2, u_out,
+                                                  planes, maxupd, chan_inner);
+    else
+        k_oras_2w_h<Bf16T><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
+                                                  C, o, nbx, nby, alpha, iters, rtol2, u_out,
+                                                  planes, maxupd, chan_inner);
     count();
     if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -1987,12 +2143,12 @@ cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s, cudaEvent_t* ev, int precision) {
+                        cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag) {
     const int wpr = mask_words_per_row(w);
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                  iters, rtol2, u_out, planes, maxupd, s, ev, precision);
+                                  iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev);

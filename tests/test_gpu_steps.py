@@ -186,3 +186,30 @@ def test_oras_rejects_aliasing(di):
         ut = T(f)
         with pytest.raises(di.DiError):
             ctx.oras_iteration(ut, T(fn), T(c), 4, rhs_zero=True, out=ut)
+
+
+def _unaligned(a):
+    # the same values in a tensor whose data starts 4 bytes past a 16-byte
+    # boundary: the block kernel then copies its tiles with cp.async, not TMA
+    flat = torch.empty(a.size + 1, dtype=torch.float32, device=DEV)
+    v = flat[1:].view(a.shape)
+    v.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    assert v.data_ptr() % 16 == 4
+    return v
+
+
+@pytest.mark.parametrize("o,rhs_zero", [(2, True), (6, True), (2, False), (6, False)])
+def test_oras_tma_and_cp_async_tiles_agree(di, o, rhs_zero):
+    # widths that are multiples of 4 with 16-byte aligned images take the TMA
+    # path; the same data 4 bytes off that alignment takes cp.async: identical
+    # tiles, identical bits
+    h, w = 70, 96
+    f, fn, c = _case(h, w, 3, 0.06, 4242 + o)
+    g = np.random.default_rng(9)
+    u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+    b = fn if rhs_zero else g.uniform(-5, 5, f.shape).astype(np.float32)
+    with di.Context(block=32, overlap=o) as ctx:
+        a = N(ctx.oras_iteration(T(u), T(b), T(c), 8, rhs_zero=rhs_zero))
+        bq = N(ctx.oras_iteration(_unaligned(u), _unaligned(b), T(c), 8, rhs_zero=rhs_zero))
+    assert np.array_equal(a, bq)
+    assert np.isfinite(a).all()
