@@ -65,6 +65,22 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 ORAS_TRAFFIC_BYTES = 149.2e6
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest of the ranks' values of x (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(frames_per_rank: int, world_size: int, elapsed_ms: float) -> float:
+    """Whole-job frames/s: every rank decodes frames_per_rank frames (replicas,
+    no shared work) and the job takes the slowest rank's time."""
+    return frames_per_rank * world_size / (elapsed_ms / 1e3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -281,13 +297,8 @@ def run_ours(args):
     elapsed_ms = t_start.elapsed_time(t_end)
     lat = sorted(a.elapsed_time(b) for a, b in ev)
     if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    frames_total = args.steps * ws
-    value = frames_total / (elapsed_ms / 1e3)
+        elapsed_ms = max_over_ranks(elapsed_ms, dev)
+    value = job_rate(args.steps, ws, elapsed_ms)
 
     # --- end to end: host buffers, copies inside the timed region -----------
     e2e_steps = max(3 * S, min(args.steps, 12 * S))
@@ -315,11 +326,7 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
     if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dev)
     h2d = f_host[0].numel() * 4 + c_host[0].numel()
     d2h = u_host[0].numel() * 4
 
@@ -456,7 +463,7 @@ def run_ours(args):
                           "frames": solo_n},
         "cycles_mean": round(mean_cycles, 3),
         "hbm_model_gbs": round(hbm_model_gbs, 1),
-        "e2e": {"value": round(e2e_steps * ws / (e2e_ms / 1e3), 3), "unit": UNIT,
+        "e2e": {"value": round(job_rate(e2e_steps, ws, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roofline,
