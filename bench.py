@@ -595,10 +595,15 @@ def run_compare(args):
     if args.compare == "methods":
         rows = [(W4K, H4K, d) for d in COMPARE_DENSITIES]
         methods = METHODS
+    elif args.compare == "video":
+        rows, methods = [], ()
     else:
         rows = [(w, h, 0.05) for (w, h) in RESOLUTIONS]
         methods = ("multigrid_oras", "multilevel_oras", "multigrid_cg", "multilevel_cg")
     s = torch.cuda.current_stream(dev)
+    if args.compare == "video":
+        _compare_video(args, di, dev, s)
+        return
     for i, (w, h, d) in enumerate(rows):
         f, c = synth.make_case(w, h, C4K, d, "edge", _case_seed(40 + i))
         ft = torch.from_numpy(f).to(dev)
@@ -641,6 +646,58 @@ def run_compare(args):
                 "rms_err": round(float(err.pow(2).mean().sqrt()), 5)}), flush=True)
 
 
+def _compare_video(args, di, dev, s):
+    """A 4K RGB video with a fixed 4 % edge-clustered mask (synth.make_video:
+    static background, one moving disk): every frame decoded from the cascade
+    (cold) and from the previous frame's result (warm, DI_START_GIVEN), with
+    the bench's solver setting and stop rule; one JSON line per mode with the
+    median ms per frame, the mean cycles and the largest error against 12
+    fixed V-cycles per frame."""
+    import statistics
+
+    import torch
+
+    import synth
+
+    n = 12
+    seq, c = synth.make_video(W4K, H4K, C4K, 0.04, "edge", _case_seed(60), frames=n,
+                              speed=4.0)
+    ct = torch.from_numpy(c).to(dev)
+    ft = [torch.from_numpy(f).to(dev) for f in seq]
+    refs = []
+    cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters)
+    with di.Context(device=0, stop_rule=di.STOP_FIXED_CYCLES, max_cycles=12, min_cycles=12,
+                    **cfg) as ctx:
+        for f in ft:
+            r, _ = ctx.inpaint(f, ct, tol=TOL)
+            refs.append(r)
+    for mode in ("cold", "warm"):
+        start = di.START_GIVEN if mode == "warm" else di.START_CASCADE
+        with di.Context(device=0, start=start, max_cycles=64, **cfg) as ctx, \
+                di.Context(device=0, max_cycles=64, **cfg) as first:
+            for _rep in range(2):  # the first pass warms up
+                u = torch.empty_like(ft[0])
+                first.inpaint(ft[0], ct, tol=TOL, out=u)  # frame 0 from the cascade
+                times, cyc, err = [], [], 0.0
+                for t in range(1, n):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    e0.record(s)
+                    _, st = ctx.inpaint(ft[t], ct, tol=TOL, out=u)
+                    e1.record(s)
+                    torch.cuda.synchronize(dev)
+                    times.append(e0.elapsed_time(e1))
+                    cyc.append(ctx.stats()["cycles"])
+                    err = max(err, float((u - refs[t]).abs().max()))
+        print(json.dumps({"mode": "video", "start": mode, "width": W4K, "height": H4K,
+                          "channels": C4K, "density": 0.04, "mask": "edge (fixed)",
+                          "frames": n - 1, "ms": round(statistics.median(times), 3),
+                          "fps": round(1000.0 / statistics.median(times), 2),
+                          "cycles_mean": round(sum(cyc) / len(cyc), 3),
+                          "max_err_vs_12_cycles": round(err, 4)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -660,7 +717,7 @@ def main():
                     help="CG steps of each local block solve")
     ap.add_argument("--streams", type=int, default=2,
                     help="frames in flight: decoders, each with its own context and stream")
-    ap.add_argument("--compare", choices=["methods", "resolution"],
+    ap.add_argument("--compare", choices=["methods", "resolution", "video"],
                     help="print the comparison table of the schedules and smoothers "
                          "(one JSON line per row) and exit")
     args = ap.parse_args()

@@ -90,6 +90,15 @@ enum { DI_SMOOTH_ORAS = 0, DI_SMOOTH_CG = 1 };
  * one by one.  The results are identical. */
 enum { DI_GRAPH_ON = 0, DI_GRAPH_OFF = 1 };
 
+/* Initial iterate.  CASCADE: the coarse-to-fine cascade of the schedule (or,
+ * single level, u = f on the mask and 0 elsewhere).  GIVEN: the values in u
+ * on entry (finite everywhere) are the initial iterate off the mask, u = f on
+ * the mask; the cascade is skipped and the cycles start at once.  A decoder
+ * of video frames with a fixed mask passes the previous frame's result: the
+ * temporal coherence that Section 1 names as a way to make the method faster
+ * on videos. */
+enum { DI_START_CASCADE = 0, DI_START_GIVEN = 1 };
+
 /* Solver configuration; a zero field takes the default in brackets. */
 typedef struct {
     int block;        /* B, square ORAS block side: 8, 16 or 32 [32] (Section 3.1) */
@@ -112,6 +121,7 @@ typedef struct {
     int schedule;     /* DI_SCHED_* [DI_SCHED_REDUCED_FMG] */
     int smoother;     /* DI_SMOOTH_* [DI_SMOOTH_ORAS] */
     int graph;        /* DI_GRAPH_*: replay of the finest-level V-cycle [DI_GRAPH_ON] */
+    int start;        /* DI_START_*: initial iterate [DI_START_CASCADE] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

@@ -13,7 +13,7 @@ in hand-written CUDA kernels for sm_103a behind the C ABI of include/di.h.
 from ._lib import (  # noqa: F401
     CUDA_ERROR, EMPTY_MASK, INVALID_ARG, NOT_CONVERGED, OK, OOM, PREC_BF16, PREC_FP16, PREC_FP32,
     STOP_ERROR_ESTIMATE, SCHED_REDUCED_FMG, SCHED_FULL_FMG, SCHED_MULTILEVEL, SCHED_SINGLE,
-    SMOOTH_ORAS, SMOOTH_CG, GRAPH_ON, GRAPH_OFF,
+    SMOOTH_ORAS, SMOOTH_CG, GRAPH_ON, GRAPH_OFF, START_CASCADE, START_GIVEN,
     STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
     exported_symbols, load, mask_downsample, plan, prolong, residual_norm_noalloc,
     restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server)

@@ -22,6 +22,7 @@ PREC_FP32, PREC_FP16, PREC_BF16 = range(3)
 SCHED_REDUCED_FMG, SCHED_FULL_FMG, SCHED_MULTILEVEL, SCHED_SINGLE = range(4)
 SMOOTH_ORAS, SMOOTH_CG = range(2)
 GRAPH_ON, GRAPH_OFF = range(2)
+START_CASCADE, START_GIVEN = range(2)
 
 
 class di_config(ctypes.Structure):
@@ -32,7 +33,8 @@ class di_config(ctypes.Structure):
                 ("alpha", ctypes.c_float), ("downsample", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("graph", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("graph", ctypes.c_int),
+                ("start", ctypes.c_int)]
 
 
 class di_stats(ctypes.Structure):

@@ -121,6 +121,7 @@ bool config_ok(const di_config& c) {
     if (c.schedule < 0 || c.schedule > 3) return false;
     if (c.smoother < 0 || c.smoother > 1) return false;
     if (c.graph < 0 || c.graph > 1) return false;
+    if (c.start < 0 || c.start > 1) return false;
     return true;
 }
 
@@ -613,8 +614,10 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
         Level& f_ = ctx->lv[l - 1];
         Level& cv = ctx->lv[l];
         DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), s));
-        DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
-                                        const_cast<float*>(cv.b), cfg.downsample == 0 ? 1 : 0, s));
+        if (cfg.start != DI_START_GIVEN)  // the coarse values feed the cascade only
+            DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
+                                            const_cast<float*>(cv.b),
+                                            cfg.downsample == 0 ? 1 : 0, s));
         DI_CUDA(ctx, launch_pack_mask(cv.c, cv.w, cv.h, cv.mbits, cnt + 1 + l, s));
     }
     unsigned long long* hcnt = static_cast<unsigned long long*>(ctx->host);
@@ -643,7 +646,11 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     Sched S{ctx, C, Leff, s};
     Level& v0 = ctx->lv[0];
     float* const caller_u = v0.u[0];
-    if (cfg.schedule == DI_SCHED_SINGLE) {
+    if (cfg.start == DI_START_GIVEN) {
+        // the caller's u is the initial iterate (e.g. the previous video
+        // frame's result): u = f on the mask, the given values elsewhere
+        DI_CUDA(ctx, launch_select(f, c, width, height, C, v0.u[0], s, 1));
+    } else if (cfg.schedule == DI_SCHED_SINGLE) {
         // no hierarchy: u = f on the mask, 0 elsewhere, then smoothing on level 0
         DI_CUDA(ctx, launch_select(f, c, width, height, C, v0.u[0], s));
     } else {

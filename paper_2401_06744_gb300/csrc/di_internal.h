@@ -58,9 +58,9 @@ cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const 
 cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, int w, int h,
                            int C, float* u, int mode, unsigned* maxupd, cudaStream_t s);
 
-// u = c ? b : 0.
+// u = c ? b : 0 (keep = 0) or u = c ? b : u (keep = 1).
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
-                          cudaStream_t s);
+                          cudaStream_t s, int keep = 0);
 
 // Bit-packed mask (see mask_words_per_row) of c; *unknown (nullable, zeroed
 // by the caller) gains the number of unknown pixels.

@@ -12,7 +12,7 @@
 //   k_reduce         fixed-order sum of the partials (one global scalar product)
 //   k_restrict       Algorithm 3 steps 2-3 fused: residual + 2x2 averaging (x4)
 //   k_prolong        Section 4.4 bilinear prolongation, cascadic or correction mode
-//   k_select         u = c ? b : 0
+//   k_select         u = c ? b : 0 (or c ? b : u for a given start)
 //   k_pack_mask      bit-packed copy of a level's mask for the block solver
 //   k_oras_warp      Algorithm 2 step 2 and the D_i-weighted part of step 3:
 //                    one warp per (block, channel); the block and a one-pixel
@@ -535,12 +535,15 @@ k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict_
     }
 }
 
+// keep == 0: u = c ? b : 0;  keep == 1: u = c ? b : u (a given iterate).
 __global__ void k_select(const float* __restrict__ b, const uint8_t* __restrict__ c, size_t n,
-                         float* __restrict__ u) {
+                         float* __restrict__ u, int keep) {
     const int ch = blockIdx.y;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        u[ch * n + i] = c[i] ? b[ch * n + i] : 0.f;
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (c[i]) u[ch * n + i] = b[ch * n + i];
+        else if (!keep) u[ch * n + i] = 0.f;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -2067,12 +2070,12 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
 }
 
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
-                          cudaStream_t s) {
+                          cudaStream_t s, int keep) {
     const size_t n = (size_t)w * h;
     size_t blocks = (n + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
-    k_select<<<dim3((unsigned)blocks, (unsigned)C), 256, 0, s>>>(b, c, n, u);
+    k_select<<<dim3((unsigned)blocks, (unsigned)C), 256, 0, s>>>(b, c, n, u, keep);
     count();
     return cudaGetLastError();
 }

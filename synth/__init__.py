@@ -14,12 +14,17 @@ value painted over it, then an affine map onto [0, 255].  Masks are binary
 round(d * N) pixels drawn without replacement with probability proportional to
 |LoG_sigma=2(f)| summed over channels plus a small floor (edge-clustered).
 Every mask holds at least one pixel.
+
+Video (a stand-in for image sequences, which the paper does not test): a
+static background frame with one disk of constant value per channel moving
+along a straight line, and one mask for the whole sequence, drawn on the first
+frame (a fixed sampling pattern).
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["image", "mask_uniform", "mask_edge", "make_case"]
+__all__ = ["image", "mask_uniform", "mask_edge", "make_case", "make_video"]
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -113,3 +118,35 @@ def make_case(width: int, height: int, channels: int, density: float, kind: str,
     else:
         raise ValueError(f"unknown mask kind {kind!r}")
     return f, c
+
+
+def make_video(width: int, height: int, channels: int, density: float, kind: str, seed: int,
+               frames: int, speed: float = 2.0):
+    """([f_0, ..., f_{frames-1}], c): the background of make_case(seed) with a
+    disk of radius min(w, h)/10 crossing it at `speed` pixels per frame; c is
+    drawn on frame 0 and shared by all frames."""
+    base = image(width, height, channels, seed)
+    g = _rng(seed + 7919)
+    m = max(1, min(width, height))
+    rad = m / 10.0
+    y0, x0 = g.uniform(0.3, 0.7) * height, g.uniform(0.2, 0.4) * width
+    ang = g.uniform(-0.5, 0.5)
+    vals = g.uniform(0.0, 255.0, size=channels)
+    ys = np.arange(height, dtype=np.float64)[:, None]
+    xs = np.arange(width, dtype=np.float64)[None, :]
+    seq = []
+    for t in range(frames):
+        cx = x0 + t * speed * np.cos(ang)
+        cy = y0 + t * speed * np.sin(ang)
+        inside = (xs - cx) ** 2 + (ys - cy) ** 2 <= rad * rad
+        f = base.copy()
+        for k in range(channels):
+            f[k][inside] = vals[k]
+        seq.append(f)
+    if kind == "uniform":
+        c = mask_uniform(width, height, density, seed)
+    elif kind == "edge":
+        c = mask_edge(seq[0], density, seed)
+    else:
+        raise ValueError(f"unknown mask kind {kind!r}")
+    return seq, c
