@@ -595,7 +595,7 @@ def run_compare(args):
     if args.compare == "methods":
         rows = [(W4K, H4K, d) for d in COMPARE_DENSITIES]
         methods = METHODS
-    elif args.compare == "video":
+    elif args.compare in ("video", "configs"):
         rows, methods = [], ()
     else:
         rows = [(w, h, 0.05) for (w, h) in RESOLUTIONS]
@@ -603,6 +603,9 @@ def run_compare(args):
     s = torch.cuda.current_stream(dev)
     if args.compare == "video":
         _compare_video(args, di, dev, s)
+        return
+    if args.compare == "configs":
+        _compare_configs(args, di, dev, s)
         return
     for i, (w, h, d) in enumerate(rows):
         f, c = synth.make_case(w, h, C4K, d, "edge", _case_seed(40 + i))
@@ -698,6 +701,155 @@ def _compare_video(args, di, dev, s):
                           "max_err_vs_12_cycles": round(err, 4)}), flush=True)
 
 
+def _median_ms(fn, s, reps):
+    import statistics
+
+    import torch
+
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _compare_configs(args, di, dev, s):
+    """The parity-test configurations measured (one JSON line each): 1, a
+    256x256 single-channel frame; 3, a batch of 32 images of uneven sizes with
+    an autotuned (block, overlap); 4, a 0.5 % 4K RGB frame with FP32, FP16 and
+    BF16 local iterates; 5, Poisson request streams at 60, 120 and 240 per
+    second through the serving loop.  Errors are against the FP64 oracle where
+    it is run."""
+    import time
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+
+    cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters)
+
+    def err_of(u, ref):
+        e = np.abs(u.astype(np.float64) - ref)
+        return round(float(e.max()), 5), round(float(np.sqrt((e ** 2).mean())), 6)
+
+    # --- config 1 ---------------------------------------------------------------
+    f, c = synth.make_case(256, 256, 1, 0.04, "uniform", BASE_SEED)
+    t0 = time.perf_counter()
+    ref = oracle.cg_inpaint(f, c)
+    t_or = time.perf_counter() - t0
+    ft, ct = torch.from_numpy(f).to(dev), torch.from_numpy(c).to(dev)
+    with di.Context(device=0, **cfg) as ctx:
+        u = torch.empty_like(ft)
+        for _ in range(3):
+            ctx.inpaint(ft, ct, tol=TOL, out=u)
+        ms = _median_ms(lambda: ctx.inpaint(ft, ct, tol=TOL, out=u), s, 50)
+        mx, rms = err_of(u.cpu().numpy(), ref)
+    print(json.dumps({"config": 1, "workload": "256x256x1, uniform 4 %", "ms": round(ms, 4),
+                      "fps": round(1000 / ms, 1), "max_abs": mx, "rms": rms,
+                      "oracle_s": round(t_or, 3), "cores": os.cpu_count()}), flush=True)
+
+    # --- config 3 ---------------------------------------------------------------
+    g = np.random.default_rng(BASE_SEED)
+    sizes = [(512, 512), (1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+    specs = []
+    for i in range(32):
+        w, h = sizes[int(g.integers(0, len(sizes)))]
+        specs.append((w, h, int(g.integers(1, 4)), float(g.uniform(0.01, 0.10)),
+                      "uniform" if g.random() < 0.5 else "edge", 5000 + i))
+    cases = [synth.make_case(*sp) for sp in specs]
+    items = [(torch.from_numpy(f).to(dev), torch.from_numpy(c).to(dev), TOL) for f, c in cases]
+    small = [it for it, sp in zip(items, specs) if sp[0] == 512][:2] or items[:1]
+    best, tune_ms = di.autotune(small, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=1)
+    pxch = sum(sp[0] * sp[1] * sp[2] for sp in specs)
+    with di.Pool(concurrency=4, block=best["block"], overlap=best["overlap"]) as pool:
+        outs, sts, cyc = pool.inpaint(items)  # warm-up: workspaces, graphs
+        ms = _median_ms(lambda: pool.inpaint(items), s, 3)
+        outs, sts, cyc = pool.inpaint(items)
+    torch.cuda.synchronize()
+    errs = []
+    for (f, c), u, sp in zip(cases, outs, specs):
+        if sp[0] == 512:
+            errs.append(err_of(u.cpu().numpy(), oracle.cg_inpaint(f, c)))
+    print(json.dumps({"config": 3, "workload": "32 images, sizes 512^2..4K, 1-3 channels, 1-10 %",
+                      "autotuned": {"block": best["block"], "overlap": best["overlap"],
+                                    "ms_per_sample_pass": round(tune_ms, 3)},
+                      "ms_per_batch": round(ms, 3), "images_per_s": round(32e3 / ms, 1),
+                      "gpix_ch_per_s": round(pxch / ms / 1e6, 3),
+                      "statuses_ok": all(x == di.OK for x in sts),
+                      "cycles_mean": round(float(np.mean(cyc)), 3),
+                      "max_abs_512": max(e[0] for e in errs) if errs else None,
+                      "rms_512": max(e[1] for e in errs) if errs else None}), flush=True)
+    del items, outs
+
+    # --- config 4 ---------------------------------------------------------------
+    f, c = synth.make_case(W4K, H4K, C4K, 0.005, "edge", BASE_SEED + 4)
+    t0 = time.perf_counter()
+    ref = oracle.cg_inpaint(f, c)
+    t_or = time.perf_counter() - t0
+    ft, ct = torch.from_numpy(f).to(dev), torch.from_numpy(c).to(dev)
+    for name, prec in (("fp32", di.PREC_FP32), ("fp16", di.PREC_FP16), ("bf16", di.PREC_BF16)):
+        with di.Context(device=0, precision=prec, **cfg) as ctx:
+            u = torch.empty_like(ft)
+            for _ in range(2):
+                _, st = ctx.inpaint(ft, ct, tol=TOL, out=u)
+            ms = _median_ms(lambda: ctx.inpaint(ft, ct, tol=TOL, out=u), s, 10)
+            ctx.inpaint(ft, ct, tol=TOL, out=u)
+            cycles = ctx.stats()["cycles"]
+            un = u.cpu().numpy().astype(np.float64)
+        per_ch = [round(float(np.abs(un[k] - ref[k]).max()), 5) for k in range(C4K)]
+        print(json.dumps({"config": 4, "workload": "3840x2160x3, edge-clustered 0.5 %",
+                          "precision": name, "ms": round(ms, 3), "fps": round(1000 / ms, 1),
+                          "cycles": cycles, "max_abs_per_channel": per_ch,
+                          "oracle_s": round(t_or, 1)}), flush=True)
+
+    # --- config 5 ---------------------------------------------------------------
+    gs = np.random.default_rng(BASE_SEED + 5)
+    pool_imgs = []
+    for i, (w, h) in enumerate([(1280, 720), (1920, 1080), (3840, 2160)] * 4):
+        d = float(gs.uniform(0.005, 0.10))
+        kind = "uniform" if i % 2 == 0 else "edge"
+        pool_imgs.append(synth.make_case(w, h, 3, d, kind, 7000 + i))
+    for lam in (60.0, 120.0, 240.0):
+        n = int(2 * lam)  # about two seconds of offered load
+        gaps = gs.exponential(1.0 / lam, size=n)
+        pick = gs.integers(0, len(pool_imgs), size=n)
+        with di.Server(slots=4, **cfg) as srv:
+            # warm-up: four 4K requests at once, one per slot (workspaces at 4K)
+            warm = [srv.submit(*pool_imgs[2], TOL) for _ in range(4)]
+            for t_ in warm:
+                srv.wait(t_)
+            tickets = []
+            t_first = time.perf_counter()
+            due = t_first
+            for gap, k in zip(gaps, pick):
+                due += gap
+                now = time.perf_counter()
+                if due > now:
+                    time.sleep(due - now)
+                f, c = pool_imgs[int(k)]
+                tickets.append(srv.submit(f, c, TOL))
+            res = [srv.wait(t)[1] for t in tickets]
+            t_last = time.perf_counter()
+        lat = sorted(r["latency_ms"] for r in res)
+        print(json.dumps({"config": 5, "workload": "Poisson stream, 720p/1080p/4K RGB, 0.5-10 %",
+                          "offered_per_s": lam, "requests": n,
+                          "served_per_s": round(n / (t_last - t_first), 1),
+                          "p50_ms": round(lat[len(lat) // 2], 3),
+                          "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                          "all_ok": all(r["status"] == di.OK for r in res),
+                          "failed": {di.status_string(k): sum(1 for r in res if r["status"] == k)
+                                     for k in {r["status"] for r in res} if k != di.OK}}),
+              flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,7 +869,7 @@ def main():
                     help="CG steps of each local block solve")
     ap.add_argument("--streams", type=int, default=2,
                     help="frames in flight: decoders, each with its own context and stream")
-    ap.add_argument("--compare", choices=["methods", "resolution", "video"],
+    ap.add_argument("--compare", choices=["methods", "resolution", "video", "configs"],
                     help="print the comparison table of the schedules and smoothers "
                          "(one JSON line per row) and exit")
     args = ap.parse_args()

@@ -227,6 +227,16 @@ typedef struct {
 di_status di_inpaint_batch(const di_config *cfg, int device, di_image *imgs, int n,
                            int concurrency, void *stream);
 
+/* A persistent pool of `concurrency` decoder slots (0 = 4), each with its own
+ * context, stream and host thread, reused by every di_pool_inpaint call, so
+ * the slots' workspaces and graphs stay resident between batches.
+ * di_inpaint_batch is create + one call + destroy.  One batch at a time per
+ * pool (concurrent calls on one pool serialise). */
+typedef struct di_pool di_pool;
+di_status di_pool_create(const di_config *cfg, int device, int concurrency, di_pool **out);
+di_status di_pool_inpaint(di_pool *pool, di_image *imgs, int n, void *stream);
+void di_pool_destroy(di_pool *pool);
+
 /* Time every (block, overlap) pair of the given lists on the sample images
  * (`reps` timed passes after one warm-up pass, CUDA events) and return the
  * fastest configuration whose decodes all converge, with its mean time per

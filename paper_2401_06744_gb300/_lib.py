@@ -92,6 +92,9 @@ _SIGS = {
     "di_reset_profile": (_I, [_P]),
     "di_inpaint_batch": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I, _I,
                               _P]),
+    "di_pool_create": (_I, [ctypes.POINTER(di_config), _I, _I, ctypes.POINTER(_P)]),
+    "di_pool_inpaint": (_I, [_P, ctypes.POINTER(di_image), _I, _P]),
+    "di_pool_destroy": (None, [_P]),
     "di_autotune": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I,
                          ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I,
                          ctypes.POINTER(di_config), ctypes.POINTER(ctypes.c_double)]),
@@ -378,6 +381,44 @@ def inpaint_batch(items, device=None, concurrency=0, stream=None, **config):
     load().di_inpaint_batch(ctypes.byref(cfg), int(device), arr, n, int(concurrency),
                             _stream(stream))
     return outs, [arr[i].status for i in range(n)], [arr[i].cycles for i in range(n)]
+
+
+class Pool:
+    """Persistent decoder slots for repeated batches (di_pool_*)."""
+
+    def __init__(self, concurrency=4, device=None, **config):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.config = make_config(**config)
+        h = _P()
+        self._h = None
+        _check(load().di_pool_create(ctypes.byref(self.config), int(device), int(concurrency),
+                                     ctypes.byref(h)))
+        self._h = h
+
+    def inpaint(self, items, stream=None):
+        """Decode a list of (f, c, tol); returns (outputs, statuses, cycles)."""
+        arr, outs = _images(items)
+        n = len(outs)
+        load().di_pool_inpaint(self._h, arr, n, _stream(stream))
+        return outs, [arr[i].status for i in range(n)], [arr[i].cycles for i in range(n)]
+
+    def close(self):
+        if self._h:
+            load().di_pool_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def autotune(items, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=2, device=None, **config):

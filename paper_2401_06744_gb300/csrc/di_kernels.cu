@@ -1155,11 +1155,16 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 
     int blk, ch;
     if (!task_of(0, blk, ch)) return;  // block-uniform
-    if (use_tma && t == 0) {
-        for (int b = 0; b < 2; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
-                         :: "r"((unsigned)__cvta_generic_to_shared(&s_bar[b])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (use_tma) {
+        if (t == 0) {
+            for (int b = 0; b < 2; ++b)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
+                             :: "r"((unsigned)__cvta_generic_to_shared(&s_bar[b])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        // no thread may probe a barrier before it is initialised (the shared
+        // memory still holds whatever an earlier CTA left there)
+        __syncthreads();
     }
     unsigned phase = 0;  // bit b: parity of the next completion of s_bar[b]
     prefetch(blk, ch, 0, -1);

@@ -56,9 +56,46 @@ void free_slot(Slot* s) {
 // Batched decoding
 // ---------------------------------------------------------------------------
 
-extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image* imgs, int n,
-                                      int concurrency, void* stream) {
-    if (!imgs || n < 0 || concurrency < 0) return DI_ERR_INVALID_ARG;
+struct di_pool {
+    int device = 0;
+    std::vector<Slot> slots;
+    cudaEvent_t start = nullptr;
+    std::mutex busy;  // one batch at a time per pool
+};
+
+extern "C" di_status di_pool_create(const di_config* cfg, int device, int concurrency,
+                                    di_pool** out) {
+    if (!out || concurrency < 0) return DI_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int P = concurrency > 0 ? concurrency : 4;
+    if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    di_pool* pool = new (std::nothrow) di_pool();
+    if (!pool) return DI_ERR_OOM;
+    pool->device = device;
+    pool->slots.resize(P);
+    di_status st = DI_OK;
+    for (int k = 0; k < P && st == DI_OK; ++k) st = make_slot(cfg, device, &pool->slots[k]);
+    if (st == DI_OK &&
+        cudaEventCreateWithFlags(&pool->start, cudaEventDisableTiming) != cudaSuccess)
+        st = DI_ERR_CUDA;
+    if (st != DI_OK) {
+        di_pool_destroy(pool);
+        return st;
+    }
+    *out = pool;
+    return DI_OK;
+}
+
+void di_pool_destroy(di_pool* pool) {
+    if (!pool) return;
+    cudaSetDevice(pool->device);
+    for (auto& s : pool->slots) free_slot(&s);
+    if (pool->start) cudaEventDestroy(pool->start);
+    delete pool;
+}
+
+extern "C" di_status di_pool_inpaint(di_pool* pool, di_image* imgs, int n, void* stream) {
+    if (!pool || !imgs || n < 0) return DI_ERR_INVALID_ARG;
     if (n == 0) return DI_OK;
     for (int i = 0; i < n; ++i) {
         const di_image& im = imgs[i];
@@ -66,23 +103,13 @@ extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image
             im.channels > di::kMaxChannels || !(im.tol > 0.f))
             return DI_ERR_INVALID_ARG;
     }
-    int P = concurrency > 0 ? concurrency : 4;
-    if (P > n) P = n;
+    std::lock_guard<std::mutex> lock(pool->busy);
+    const int device = pool->device;
     if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    const int P = std::min<int>((int)pool->slots.size(), n);
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     // work starts after everything already queued on the caller's stream
-    cudaEvent_t start;
-    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return DI_ERR_CUDA;
-    cudaEventRecord(start, caller);
-
-    std::vector<Slot> slots(P);
-    di_status st = DI_OK;
-    for (int k = 0; k < P && st == DI_OK; ++k) st = make_slot(cfg, device, &slots[k]);
-    if (st != DI_OK) {
-        for (auto& s : slots) free_slot(&s);
-        cudaEventDestroy(start);
-        return st;
-    }
+    if (cudaEventRecord(pool->start, caller) != cudaSuccess) return DI_ERR_CUDA;
     // largest images first: better packing of the slots
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
@@ -92,9 +119,9 @@ extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image
     });
     std::atomic<int> next{0};
     auto worker = [&](int k) {
-        Slot& s = slots[k];
+        Slot& s = pool->slots[k];
         cudaSetDevice(device);
-        cudaStreamWaitEvent(s.stream, start, 0);
+        cudaStreamWaitEvent(s.stream, pool->start, 0);
         for (;;) {
             const int j = next.fetch_add(1);
             if (j >= n) break;
@@ -111,14 +138,26 @@ extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image
     for (int k = 1; k < P; ++k) th.emplace_back(worker, k);
     worker(0);
     for (auto& t : th) t.join();
-    for (auto& s : slots) cudaStreamWaitEvent(caller, s.done, 0);
+    for (int k = 0; k < P; ++k) cudaStreamWaitEvent(caller, pool->slots[k].done, 0);
     cudaStreamSynchronize(caller);
-    for (auto& s : slots) free_slot(&s);
-    cudaEventDestroy(start);
     di_status worst = DI_OK;
     for (int i = 0; i < n; ++i)
         if (imgs[i].status != DI_OK && worst == DI_OK) worst = (di_status)imgs[i].status;
     return worst;
+}
+
+extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image* imgs, int n,
+                                      int concurrency, void* stream) {
+    if (!imgs || n < 0 || concurrency < 0) return DI_ERR_INVALID_ARG;
+    if (n == 0) return DI_OK;
+    int P = concurrency > 0 ? concurrency : 4;
+    if (P > n) P = n;
+    di_pool* pool = nullptr;
+    di_status st = di_pool_create(cfg, device, P, &pool);
+    if (st != DI_OK) return st;
+    st = di_pool_inpaint(pool, imgs, n, stream);
+    di_pool_destroy(pool);
+    return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,11 +330,12 @@ void serve_loop(di_server* srv, int k) {
             cudaMemcpyAsync(sl.c_dev, r->c, px, cudaMemcpyHostToDevice, sl.s.stream);
             st = di_inpaint(sl.s.ctx, sl.f_dev, sl.c_dev, r->w, r->h, r->ch, r->tol, sl.u_dev,
                             sl.s.stream);
-            if (st == DI_OK || st == DI_ERR_NOT_CONVERGED) {
+            if (st == DI_OK || st == DI_ERR_NOT_CONVERGED)
                 cudaMemcpyAsync(r->u, sl.u_dev, pxch * sizeof(float), cudaMemcpyDeviceToHost,
                                 sl.s.stream);
-                if (cudaStreamSynchronize(sl.s.stream) != cudaSuccess) st = DI_ERR_CUDA;
-            }
+            // whatever the status, nothing of this request stays queued
+            if (cudaStreamSynchronize(sl.s.stream) != cudaSuccess && st == DI_OK)
+                st = DI_ERR_CUDA;
         }
         di_stats ss;
         di_get_stats(sl.s.ctx, &ss);

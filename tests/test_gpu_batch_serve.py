@@ -154,3 +154,27 @@ def test_server_admission_budget_serialises_large_requests(di):
     assert max(r[1]["queue_ms"] for r in res) > 0.0
     for u, _ in res[1:]:
         assert np.array_equal(u, res[0][0])
+
+
+def test_pool_reuse_matches_solo(di):
+    # a persistent pool decodes two batches in turn (slots, workspaces and
+    # graphs reused); every image equals its solo decode bit for bit
+    g = np.random.default_rng(12)
+    sizes = [(160, 90), (257, 129), (96, 64), (320, 180)]
+    batches = []
+    for b in range(2):
+        cases = []
+        for i in range(5):
+            w, h = sizes[(i + b) % len(sizes)]
+            cases.append(_case(w, h, int(g.integers(1, 4)), float(g.uniform(0.02, 0.08)),
+                               "edge" if i % 2 else "uniform", 300 + 10 * b + i))
+        batches.append(cases)
+    with di.Pool(concurrency=3) as pool:
+        for cases in batches:
+            items = [(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), TOL)
+                     for f, c in cases]
+            outs, sts, cyc = pool.inpaint(items)
+            torch.cuda.synchronize()
+            assert all(s == di.OK for s in sts), sts
+            for (f, c), u in zip(cases, outs):
+                assert np.array_equal(u.cpu().numpy(), _solo(di, f, c))
