@@ -414,6 +414,7 @@ k_reduce_slot(const double* __restrict__ partials, int nparts, double* __restric
 // unknown children (max pooling), so their residuals need no mask loads: the
 // 4x4 patch of u around the children is read at once (zero outside the image)
 // and the in-image neighbour count gives the reflecting boundary.
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zero,
            int w, int h, const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH,
@@ -431,24 +432,41 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
     for (int j = 0; j < 4; ++j) {
         const int y = y0 + j;
         const bool yok = y >= 0 && y < h;
+        if (VEC) {
+            // the two children's columns as one 8-byte word, the outer
+            // columns (rows 1 and 2 only) as single words
+            float2 mid = make_float2(0.f, 0.f);
+            if (yok) mid = *reinterpret_cast<const float2*>(uc + (size_t)y * w + x0 + 1);
+            t[j][1] = mid.x;
+            t[j][2] = mid.y;
+            const bool inner = j == 1 || j == 2;
+            t[j][0] = (inner && yok && x0 >= 0) ? uc[(size_t)y * w + x0] : 0.f;
+            t[j][3] = (inner && yok && x0 + 3 < w) ? uc[(size_t)y * w + x0 + 3] : 0.f;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int x = x0 + i;
-            const bool corner = (i == 0 || i == 3) && (j == 0 || j == 3);
-            t[j][i] = (!corner && yok && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
+            for (int i = 0; i < 4; ++i) {
+                const int x = x0 + i;
+                const bool corner = (i == 0 || i == 3) && (j == 0 || j == 3);
+                t[j][i] = (!corner && yok && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
+            }
         }
     }
     float sum = 0.f;
     int cnt = 0;
 #pragma unroll
     for (int j = 1; j <= 2; ++j) {
+        float2 rb = make_float2(0.f, 0.f);
+        if (VEC && !rhs_zero && y0 + j < h)
+            rb = *reinterpret_cast<const float2*>(b + ch * n + (size_t)(y0 + j) * w + x0 + 1);
 #pragma unroll
         for (int i = 1; i <= 2; ++i) {
             const int x = x0 + i, y = y0 + j;
             if (x >= w || y >= h) continue;
             const int deg = (x > 0) + (x < w - 1) + (y > 0) + (y < h - 1);
             const float lu = (float)deg * t[j][i] - (t[j][i - 1] + t[j][i + 1] + t[j - 1][i] + t[j + 1][i]);
-            const float rhs = rhs_zero ? 0.f : b[ch * n + (size_t)y * w + x];
+            const float rhs = rhs_zero ? 0.f
+                              : VEC ? (i == 1 ? rb.x : rb.y)
+                                    : b[ch * n + (size_t)y * w + x];
             sum += rhs - lu;
             ++cnt;
         }
@@ -459,62 +477,70 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
 // Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
 // coarse cell, 3/16 of each of the two edge neighbours of the parent on the
 // child's side and 1/16 of the diagonal one (coarse indices clamped at the
-// border).  One thread per pair of fine pixels (2X, 2X+1) of one fine row y:
-// both have parent column X; the row blend takes coarse row Y = y/2 three
-// times and its neighbour on the child's side once, the column blend the
-// same with X-1 (left child) or X+1 (right child).
+// border).  One thread per coarse cell (X, Y) and its up to 2x2 children:
+// for the child row y = 2Y + dy the row blend takes coarse row Y three times
+// and its neighbour on the child's side (Y - 1 for dy = 0, Y + 1 for dy = 1)
+// once, the column blend the same with X - 1 (left child) or X + 1.
 // mode 0: u = c ? b : P uH;  mode 1: u += c ? 0 : P uH (largest |P uH| over
-// the updated pixels into *maxupd).  VEC: the pair is one 8-byte word of u
-// and b and one 2-byte word of c (w even, aligned base pointers).
+// the updated pixels into *maxupd).  VEC: each child pair is one 8-byte word
+// of u and b and one 2-byte word of c (w even, aligned base pointers).
 template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
           const uint8_t* __restrict__ c, int w, int h, float* __restrict__ u, int mode,
           unsigned* __restrict__ maxupd) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     float amax = 0.f;
-    if (X < wH && y < h) {
+    if (X < wH && Y < hH) {
         const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
-        const int Y = y >> 1;
-        const int Yn = (y & 1) ? min(Y + 1, hH - 1) : max(Y - 1, 0);
-        const float* rc = uH + ch * nH + (size_t)Y * wH;
-        const float* rn = uH + ch * nH + (size_t)Yn * wH;
+        const float* e = uH + ch * nH;
         const int Xl = max(X - 1, 0), Xr = min(X + 1, wH - 1);
-        const float v_l = 3.f * rc[Xl] + rn[Xl];
-        const float v_c = 3.f * rc[X] + rn[X];
-        const float v_r = 3.f * rc[Xr] + rn[Xr];
-        const float a0 = (3.f * v_c + v_l) * (1.f / 16.f);
-        const float a1 = (3.f * v_c + v_r) * (1.f / 16.f);
+        const float* rc = e + (size_t)Y * wH;
+        const float* ru = e + (size_t)max(Y - 1, 0) * wH;
+        const float* rd = e + (size_t)min(Y + 1, hH - 1) * wH;
+        const float cl = rc[Xl], cc = rc[X], cr = rc[Xr];
+        const float ul = ru[Xl], uc = ru[X], ur = ru[Xr];
+        const float dl = rd[Xl], dc = rd[X], dr = rd[Xr];
         const int x = 2 * X;
-        const size_t p = (size_t)y * w + x;
-        float* uc = u + ch * n;
-        if (VEC) {
-            const uchar2 cm = *reinterpret_cast<const uchar2*>(c + p);
-            float2* up = reinterpret_cast<float2*>(uc + p);
-            if (mode == 0) {
-                float2 bv = make_float2(0.f, 0.f);
-                if (cm.x | cm.y) bv = *reinterpret_cast<const float2*>(b + ch * n + p);
-                *up = make_float2(cm.x ? bv.x : a0, cm.y ? bv.y : a1);
-            } else {
-                float2 uv = *up;
-                if (!cm.x) { uv.x += a0; amax = fabsf(a0); }
-                if (!cm.y) { uv.y += a1; amax = fmaxf(amax, fabsf(a1)); }
-                *up = uv;
-            }
-        } else {
+        float* ucn = u + ch * n;
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                if (x + dx >= w) break;
-                const float v = dx ? a1 : a0;
-                if (c[p + dx]) {
-                    if (mode == 0) uc[p + dx] = b[ch * n + p + dx];
-                } else if (mode == 0) {
-                    uc[p + dx] = v;
+        for (int dy = 0; dy < 2; ++dy) {
+            const int y = 2 * Y + dy;
+            if (y >= h) break;
+            const float v_l = 3.f * cl + (dy ? dl : ul);
+            const float v_c = 3.f * cc + (dy ? dc : uc);
+            const float v_r = 3.f * cr + (dy ? dr : ur);
+            const float a0 = (3.f * v_c + v_l) * (1.f / 16.f);
+            const float a1 = (3.f * v_c + v_r) * (1.f / 16.f);
+            const size_t p = (size_t)y * w + x;
+            if (VEC) {
+                const uchar2 cm = *reinterpret_cast<const uchar2*>(c + p);
+                float2* up = reinterpret_cast<float2*>(ucn + p);
+                if (mode == 0) {
+                    float2 bv = make_float2(0.f, 0.f);
+                    if (cm.x | cm.y) bv = *reinterpret_cast<const float2*>(b + ch * n + p);
+                    *up = make_float2(cm.x ? bv.x : a0, cm.y ? bv.y : a1);
                 } else {
-                    uc[p + dx] += v;
-                    amax = fmaxf(amax, fabsf(v));
+                    float2 uv = *up;
+                    if (!cm.x) { uv.x += a0; amax = fmaxf(amax, fabsf(a0)); }
+                    if (!cm.y) { uv.y += a1; amax = fmaxf(amax, fabsf(a1)); }
+                    *up = uv;
+                }
+            } else {
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    if (x + dx >= w) break;
+                    const float v = dx ? a1 : a0;
+                    if (c[p + dx]) {
+                        if (mode == 0) ucn[p + dx] = b[ch * n + p + dx];
+                    } else if (mode == 0) {
+                        ucn[p + dx] = v;
+                    } else {
+                        ucn[p + dx] += v;
+                        amax = fmaxf(amax, fabsf(v));
+                    }
                 }
             }
         }
@@ -2050,7 +2076,15 @@ cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const 
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    k_restrict<<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
+    const bool vec = (w % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) |
+                                       reinterpret_cast<uintptr_t>(rhs_zero ? nullptr : b)) %
+                                      8 == 0);
+    if (vec)
+        k_restrict<true><<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH,
+                                                               hH);
+    else
+        k_restrict<false><<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH,
+                                                                wH, hH);
     count();
     return cudaGetLastError();
 }
@@ -2060,7 +2094,7 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    const dim3 grid = grid2(wH, h, blk, C);  // one thread per fine pixel pair
+    const dim3 grid = grid2(wH, hH, blk, C);  // one thread per coarse cell
     const bool vec = (w % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) |
                                        reinterpret_cast<uintptr_t>(b)) % 8 == 0) &&
                      reinterpret_cast<uintptr_t>(c) % 2 == 0;

@@ -213,3 +213,27 @@ def test_oras_tma_and_cp_async_tiles_agree(di, o, rhs_zero):
         bq = N(ctx.oras_iteration(_unaligned(u), _unaligned(b), T(c), 8, rhs_zero=rhs_zero))
     assert np.array_equal(a, bq)
     assert np.isfinite(a).all()
+
+
+@pytest.mark.parametrize("h,w", [(64, 96), (31, 130)])
+def test_transfers_vector_and_scalar_paths_agree(di, h, w):
+    # even widths with 8-byte aligned images take the 8-byte-word paths of the
+    # restriction and prolongation, the same data 4 bytes off alignment the
+    # scalar paths: identical bits
+    f, fn, c = _case(h, w, 2, 0.05, 77 + w)
+    g = np.random.default_rng(3)
+    u = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+    b = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+    cH = T(M.mask_downsample(c))
+    ra = N(di.restrict_residual(T(u), T(b), T(c), cH, rhs_zero=False))
+    rb = N(di.restrict_residual(_unaligned(u), _unaligned(b), T(c), cH, rhs_zero=False))
+    assert np.array_equal(ra, rb)
+    H, W = M.coarse_shape(h, w)
+    e = g.uniform(-3, 3, (2, H, W)).astype(np.float32)
+    ua, ub = T(u), _unaligned(u)
+    di.prolong(T(e), T(c), 1, u=ua)
+    di.prolong(T(e), T(c), 1, u=ub)
+    assert np.array_equal(N(ua), N(ub))
+    pa = N(di.prolong(T(e), T(c), 0, b=T(fn)))
+    pb = N(di.prolong(T(e), T(c), 0, b=_unaligned(fn)))
+    assert np.array_equal(pa, pb)
