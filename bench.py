@@ -65,6 +65,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 ORAS_TRAFFIC_BYTES = 149.2e6
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def max_over_ranks(x: float, device) -> float:
     """The largest of the ranks' values of x (the slowest rank's time)."""
     import torch
@@ -413,6 +422,7 @@ def run_ours(args):
     mean_cycles = sum(cycles) / len(cycles)
     model_bytes = W4K * H4K * C4K * (46 + 83 * mean_cycles)
     hbm_model_gbs = model_bytes * value / ws / 1e9
+    hbm_peak, hbm_src = _hbm_peak()
 
     # --- CPU baseline: the oracle on a bounded sample (and a parity check) ----
     cpu = None
@@ -463,6 +473,10 @@ def run_ours(args):
                           "frames": solo_n},
         "cycles_mean": round(mean_cycles, 3),
         "hbm_model_gbs": round(hbm_model_gbs, 1),
+        "hbm_model": {"gbs": round(hbm_model_gbs, 1), "peak_gbs": hbm_peak,
+                      "frac": round(hbm_model_gbs / hbm_peak, 4), "peak_source": hbm_src,
+                      "bytes_per_frame": int(model_bytes),
+                      "model": "N C (46 + 83 k) bytes per frame, k V-cycles"},
         "e2e": {"value": round(job_rate(e2e_steps, ws, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
