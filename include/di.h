@@ -44,14 +44,16 @@ typedef enum {
     DI_ERR_OOM = 3,           /* device workspace could not be allocated */
     DI_ERR_NOT_CONVERGED = 4, /* max_cycles reached first; u holds the last iterate */
     DI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
-    DI_ERR_TIMEOUT = 6        /* reserved for bounded device-side waits */
+    DI_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out: a tile copy of the
+                                 32x32 block kernel did not arrive; u is not valid */
 } di_status;
 
 /* Stop rules of di_inpaint.  DI_STOP_ERROR_ESTIMATE: after every V-cycle the
  * error is estimated from the size of the cycle's updates and their decay
  * (est = U_k q/(1-q), q the larger of the last two ratios U_k/U_{k-1}, U_k the
  * sum of the largest pre-smoothing, coarse-correction and post-smoothing
- * updates on the finest grid); the solve stops when est <= tol/2.  DI_STOP_RELATIVE_RESIDUAL: the paper's criterion
+ * updates on the finest grid); the solve stops when est <= tol/2.
+ * DI_STOP_RELATIVE_RESIDUAL: the paper's criterion
  * (Section 5.2), ||b - A u||_2 / ||b||_2 <= tol, per channel.
  * DI_STOP_FIXED_CYCLES: exactly max_cycles V-cycles. */
 enum { DI_STOP_ERROR_ESTIMATE = 0, DI_STOP_RELATIVE_RESIDUAL = 1, DI_STOP_FIXED_CYCLES = 2 };
