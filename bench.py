@@ -6,10 +6,10 @@ Workload: six seeded synthetic 4K RGB frames (sinusoids + disks, Section 5
 sizes; masks of 10 %, 4 % and 1 % density, edge-clustered and uniform),
 resident in HBM and decoded in rotation, one frame per step, with the error
 estimate stop rule at tol = 0.05 gray (32x32 blocks, overlap 2, 10 local CG
-steps; the paper's overlap 6 / 8 steps is timed beside it).  Two frames are in
+steps; the paper's overlap 6 / 8 steps is timed beside it).  Four frames are in
 flight (--streams): each decoder has its own context, stream and host thread,
-so one decoder's kernels fill the GPU while the other waits on its stop test
-or runs its small coarse-level launches.  The six frames
+so the others' kernels fill the GPU while one waits on its stop test or runs
+its small coarse-level launches.  The six frames
 (650 MB of inputs) exceed the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -881,7 +881,7 @@ def main():
     ap.add_argument("--overlap", type=int, default=OVERLAP, help="ORAS block overlap")
     ap.add_argument("--local-iters", type=int, default=LOCAL_ITERS,
                     help="CG steps of each local block solve")
-    ap.add_argument("--streams", type=int, default=2,
+    ap.add_argument("--streams", type=int, default=4,
                     help="frames in flight: decoders, each with its own context and stream")
     ap.add_argument("--compare", choices=["methods", "resolution", "video", "configs"],
                     help="print the comparison table of the schedules and smoothers "

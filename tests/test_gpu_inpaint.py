@@ -182,3 +182,40 @@ def test_non_default_stream(di):
     s.synchronize()
     assert st == di.OK
     _check(u.cpu().numpy(), f, c, ref)
+
+
+def test_full_size_bench_frames_in_bench_configuration(di):
+    # the 4 % and 1 % edge-clustered 3840x2160 RGB bench frames, decoded as the
+    # bench times them (its block, overlap and local steps; two decoders with
+    # their own contexts and streams at once), against the FP64 oracle
+    import os
+    import sys
+    import threading
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    frames = [synth.make_case(bench.W4K, bench.H4K, bench.C4K, *bench.CASES[k],
+                              bench._case_seed(k)) for k in (1, 2)]
+    cfg = dict(block=bench.BLOCK, overlap=bench.OVERLAP, local_iters=bench.LOCAL_ITERS)
+    outs, sts = [None, None], [None, None]
+
+    def work(t):
+        f, c = frames[t]
+        s = torch.cuda.Stream(DEV)
+        with di.Context(**cfg) as ctx, torch.cuda.stream(s):
+            u, st = ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV),
+                                tol=TOL, stream=s)
+            s.synchronize()
+            outs[t], sts[t] = u.cpu().numpy(), st
+
+    th = [threading.Thread(target=work, args=(t,)) for t in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    for (f, c), u, st in zip(frames, outs, sts):
+        assert st == di.OK
+        _check(u, f, c, oracle.cg_inpaint(f, c))
+        solo, st2, _ = _run(di, f, c, **cfg)
+        assert st2 == di.OK and np.array_equal(u, solo)
