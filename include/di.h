@@ -124,6 +124,8 @@ typedef struct {
     int smoother;     /* DI_SMOOTH_* [DI_SMOOTH_ORAS] */
     int graph;        /* DI_GRAPH_*: replay of the finest-level V-cycle [DI_GRAPH_ON] */
     int start;        /* DI_START_*: initial iterate [DI_START_CASCADE] */
+    int local_iters_coarse; /* CG steps of the local solves on the levels below the finest
+                               (smoothing of the error equations and the cascade) [local_iters] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

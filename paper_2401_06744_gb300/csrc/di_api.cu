@@ -122,6 +122,7 @@ bool config_ok(const di_config& c) {
     if (c.smoother < 0 || c.smoother > 1) return false;
     if (c.graph < 0 || c.graph > 1) return false;
     if (c.start < 0 || c.start > 1) return false;
+    if (c.local_iters_coarse < 0) return false;
     return true;
 }
 
@@ -328,7 +329,10 @@ struct Sched {
                      bool restart = true) {
         const di_config& cfg = ctx->cfg;
         if (cfg.smoother == DI_SMOOTH_ORAS)
-            return run_oras(l, in, zero_in, out, cfg.local_iters, maxupd);
+            return run_oras(l, in, zero_in, out,
+                            l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
+                                                                : cfg.local_iters,
+                            maxupd);
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);

@@ -197,7 +197,8 @@ def test_full_size_bench_frames_in_bench_configuration(di):
 
     frames = [synth.make_case(bench.W4K, bench.H4K, bench.C4K, *bench.CASES[k],
                               bench._case_seed(k)) for k in (1, 2)]
-    cfg = dict(block=bench.BLOCK, overlap=bench.OVERLAP, local_iters=bench.LOCAL_ITERS)
+    cfg = dict(block=bench.BLOCK, overlap=bench.OVERLAP, local_iters=bench.LOCAL_ITERS,
+               local_iters_coarse=bench.LOCAL_ITERS_COARSE)
     outs, sts = [None, None], [None, None]
 
     def work(t):

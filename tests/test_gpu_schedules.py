@@ -190,3 +190,15 @@ def test_graph_follows_changing_inputs(di):
             ref, st2, _ = _run(di, f, c, TOL, graph=di.GRAPH_OFF)
             assert st == st2 == di.OK
             assert np.array_equal(u.cpu().numpy(), ref)
+
+
+def test_coarse_level_local_steps(di, case):
+    # fewer local steps on the coarse levels changes the iterates but not the
+    # fixed point; the default (0) is the finest level's count
+    f, c, ref = case
+    u0, st0, _ = _run(di, f, c, TOL)
+    u1, st1, _ = _run(di, f, c, TOL, local_iters_coarse=8)  # local_iters 8: same as default
+    assert st0 == st1 == di.OK and np.array_equal(u0, u1)
+    u2, st2, _ = _run(di, f, c, TOL, local_iters=10, local_iters_coarse=4, max_cycles=64)
+    assert st2 == di.OK
+    _check(u2, f, c, ref, TOL)
