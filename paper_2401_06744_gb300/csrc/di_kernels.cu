@@ -1367,6 +1367,25 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         float* plane = planes + ((size_t)par * C + ch) * n;
         float* uo = u_out + ch * n;
         const bool colok = x0 + col < w;
+        if (nsh == 0) {
+            // 0/1 weights (overlap 2): each pixel is written by the one block
+            // whose weight is 1 there, with u_in added
+            if (colok && wx > 0.f) {
+                float* uol = uo + (size_t)(y0 + row0) * w + x0 + col;
+                const float* tol = tu + (row0 + 1) * P + col + 1;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int j = k + 8 * e;
+                        if (row0 + j >= bh || !(s_wy[row0 + j] > 0.f)) continue;
+                        const float v = e ? hi2(x[k]) : lo2(x[k]);
+                        uol[j * w] = (zero_in ? 0.f : tol[j * P]) + v;
+                        vmax = fmaxf(vmax, fabsf(v));
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
 #pragma unroll
@@ -1394,6 +1413,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 }
                 if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
             }
+        }
         }
         if (!more) break;
         blk = nb2;

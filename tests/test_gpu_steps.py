@@ -134,6 +134,7 @@ ORAS_CASES = [  # (h, w, block, overlap, iters)
     (32, 32, 32, 6, 8), (70, 95, 32, 6, 8), (77, 61, 16, 4, 6), (61, 77, 16, 2, 5),
     (45, 38, 8, 2, 4), (45, 38, 8, 4, 3), (40, 41, 8, 1, 4), (50, 33, 16, 1, 2),
     (130, 100, 32, 6, 0), (130, 100, 32, 6, 1), (9, 120, 32, 6, 8), (120, 9, 16, 4, 8),
+    (70, 96, 32, 2, 8), (130, 100, 32, 2, 10), (33, 35, 32, 2, 4), (70, 95, 32, 3, 8),
 ]
 
 
