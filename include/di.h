@@ -372,6 +372,15 @@ di_status di_oras_iteration(di_ctx *ctx, const float *u_in, const float *b, int 
                             const uint8_t *c, int width, int height, int channels,
                             int local_iters, float *u_out, void *stream);
 
+/* Fault-path self test (no counterpart in the paper): launches one CTA that
+ * waits, with the same bounded mbarrier wait as the 32x32 block kernel
+ * (`limit` polls), on a barrier that nothing completes, and reports what the
+ * decoder would: DI_ERR_TIMEOUT when the wait ran out (the expected result),
+ * DI_OK if it completed, DI_ERR_CUDA on a runtime error.  Nothing faults and
+ * nothing stays in flight; the device stays usable.  Exists so that tests can
+ * exercise the timeout path on a GPU. */
+di_status di_selftest_bounded_wait(int device, int limit, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

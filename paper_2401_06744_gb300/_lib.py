@@ -112,6 +112,7 @@ _SIGS = {
     "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
     "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
+    "di_selftest_bounded_wait": (_I, [_I, _I, _P]),
 }
 
 
@@ -381,6 +382,14 @@ def inpaint_batch(items, device=None, concurrency=0, stream=None, **config):
     load().di_inpaint_batch(ctypes.byref(cfg), int(device), arr, n, int(concurrency),
                             _stream(stream))
     return outs, [arr[i].status for i in range(n)], [arr[i].cycles for i in range(n)]
+
+
+def selftest_bounded_wait(limit=4096, device=None, stream=None) -> int:
+    """Run the bounded-wait self test (di_selftest_bounded_wait); returns the
+    status, TIMEOUT when the wait ran out as designed."""
+    if device is None:
+        device = torch.cuda.current_device()
+    return load().di_selftest_bounded_wait(int(device), int(limit), _stream(stream))
 
 
 class Pool:

@@ -909,4 +909,22 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     return DI_OK;
 }
 
+di_status di_selftest_bounded_wait(int device, int limit, void* stream) {
+    if (limit < 1) return DI_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned* flag = nullptr;
+    unsigned h = 0;
+    di_status st = DI_OK;
+    if (cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess) return DI_ERR_OOM;
+    if (cudaMemsetAsync(flag, 0, sizeof(unsigned), s) != cudaSuccess ||
+        launch_wait_selftest(flag, limit, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        st = DI_ERR_CUDA;
+    cudaFree(flag);
+    if (st != DI_OK) return st;
+    return h == 1 ? DI_ERR_TIMEOUT : h == 2 ? DI_OK : DI_ERR_CUDA;
+}
+
 }  // extern "C"

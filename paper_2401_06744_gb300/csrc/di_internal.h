@@ -62,6 +62,10 @@ cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, in
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
                           cudaStream_t s, int keep = 0);
 
+// One CTA waits, with the block kernel's bounded mbarrier wait (`limit`
+// polls), on a barrier nothing completes; *flag = 1 when the wait ran out.
+cudaError_t launch_wait_selftest(unsigned* flag, int limit, cudaStream_t s);
+
 // Bit-packed mask (see mask_words_per_row) of c; *unknown (nullable, zeroed
 // by the caller) gains the number of unknown pixels.
 cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,

@@ -1043,8 +1043,8 @@ struct Smem2W {
 
 // Bounded wait for phase `parity` of the mbarrier at shared address `bar`;
 // false if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (int n = 0; n < (1 << 20); ++n) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit = 1 << 20) {
+    for (int n = 0; n < limit; ++n) {
         unsigned ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -1056,6 +1056,23 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
         if (ok) return true;
     }
     return false;
+}
+
+// Self test of the bounded wait: one CTA waits on an mbarrier that no thread
+// and no copy ever completes.  *flag = 1 when the wait runs out (the expected
+// outcome; the CTA then leaves normally, nothing is in flight), 2 if it
+// completed.
+__global__ void k_bounded_wait_selftest(unsigned* __restrict__ flag, int limit) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(a, 0u, limit);
+    const int any_out = __syncthreads_or(!ok);
+    if (threadIdx.x == 0) *flag = any_out ? 1u : 2u;
 }
 
 // 3-D tiled TMA load of one box into shared memory, completing on `bar`.
@@ -2185,6 +2202,12 @@ cudaError_t launch_cg_smooth(const float* in, int zero_in, const float* b, int r
         *step_par = par ^ 1;
     }
     k_cg_finish<<<dim3((unsigned)nb, (unsigned)C), 256, 0, s>>>(in, zero_in, x, out, n, maxupd);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(unsigned* flag, int limit, cudaStream_t s) {
+    k_bounded_wait_selftest<<<1, 64, 0, s>>>(flag, limit);
     count();
     return cudaGetLastError();
 }
