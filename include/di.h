@@ -126,6 +126,11 @@ typedef struct {
     int start;        /* DI_START_*: initial iterate [DI_START_CASCADE] */
     int local_iters_coarse; /* CG steps of the local solves on the levels below the finest
                                (smoothing of the error equations and the cascade) [local_iters] */
+    float local_stop; /* with DI_STOP_ERROR_ESTIMATE: a block's local CG stops early once the
+                         2-norm of its residual (per channel, over the block's pixels) is at
+                         most local_stop * tol gray -- a local correction that small is
+                         below what the stop rule resolves (Section 3.1 stops the local
+                         solves on their residual too); < 0 disables [0.2] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

@@ -34,7 +34,8 @@ class di_config(ctypes.Structure):
                 ("stop_rule", ctypes.c_int), ("profile", ctypes.c_int),
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("graph", ctypes.c_int),
-                ("start", ctypes.c_int), ("local_iters_coarse", ctypes.c_int)]
+                ("start", ctypes.c_int), ("local_iters_coarse", ctypes.c_int),
+                ("local_stop", ctypes.c_float)]
 
 
 class di_stats(ctypes.Structure):

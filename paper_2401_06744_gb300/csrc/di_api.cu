@@ -104,6 +104,7 @@ di_config resolve(const di_config* in) {
     if (c.max_cycles == 0) c.max_cycles = 16;
     if (c.min_cycles == 0) c.min_cycles = 1;
     if (c.alpha == 0.f) c.alpha = 0.5f;
+    if (c.local_stop == 0.f) c.local_stop = 0.2f;
     return c;
 }
 
@@ -123,6 +124,7 @@ bool config_ok(const di_config& c) {
     if (c.graph < 0 || c.graph > 1) return false;
     if (c.start < 0 || c.start > 1) return false;
     if (c.local_iters_coarse < 0) return false;
+    if (!std::isfinite(c.local_stop)) return false;
     return true;
 }
 
@@ -276,6 +278,7 @@ struct Sched {
     int Leff;   // levels that carry unknown pixels (recursion depth)
     cudaStream_t s;
     int root = 0;  // level whose own problem is being solved (the others solve A e = r)
+    float abs2 = 0.f;  // absolute local stop r.r <= abs2 of the smoothing ORAS calls (0: none)
 
     // Right-hand side of level l: the root level solves A u = b_l (level 0:
     // b = C f; coarse levels: the downsampled mask values), whose right-hand
@@ -332,7 +335,7 @@ struct Sched {
             return run_oras(l, in, zero_in, out,
                             l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
                                                                 : cfg.local_iters,
-                            maxupd);
+                            maxupd, abs2 > 0.f ? -abs2 : 0.f);
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);
@@ -648,6 +651,8 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     }
 
     Sched S{ctx, C, Leff, s};
+    if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE && cfg.local_stop > 0.f)
+        S.abs2 = (cfg.local_stop * tol) * (cfg.local_stop * tol);
     Level& v0 = ctx->lv[0];
     float* const caller_u = v0.u[0];
     if (cfg.start == DI_START_GIVEN) {

@@ -81,7 +81,9 @@ inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
 
 // One ORAS iteration u_in -> u_out (planes: oras_scratch_floats of workspace;
 // mbits: the packed mask of this level).  Each local CG runs `iters` steps or
-// until r.r <= max(rtol2, 1e-14) * (r.r)_0.  max |v_i| over pixels with
+// until r.r <= max(rtol2, 1e-14) * (r.r)_0 (rtol2 >= 0), or until
+// r.r <= max(1e-14 (r.r)_0, -rtol2) (rtol2 < 0: an absolute level, per block
+// and channel, summed over the block's pixels).  max |v_i| over pixels with
 // nonzero weight is folded into *maxupd (nullable).
 // ev (nullable): two events recorded on `s` right before and right after the
 // block kernel (the combine kernels follow the second one).  precision: 0

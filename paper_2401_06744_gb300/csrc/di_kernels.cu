@@ -903,7 +903,10 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
         }
         acc0 = add2(acc0, acc1);
         float rr = warp_sum(lo2(acc0) + hi2(acc0));
-        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+        // rtol2 >= 0: relative stop (r.r <= max(rtol2, 1e-14) (r.r)_0); rtol2 < 0:
+        // also stop once r.r <= -rtol2 (an absolute level, or the FP32 floor)
+        const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
+                                           : fmaxf(1e-14f * rr, -rtol2);
 
         for (int it = 0; it < iters; ++it) {
             if (!(rr > rr_stop)) break;  // rr is warp-uniform
@@ -1313,7 +1316,10 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         __syncthreads();
         float rr = s_red2[0] + s_red2[1];
         float pb = s_seam[wi ^ 1][lane];  // partner's seam row of p
-        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+        // rtol2 >= 0: relative stop (r.r <= max(rtol2, 1e-14) (r.r)_0); rtol2 < 0:
+        // also stop once r.r <= -rtol2 (an absolute level, or the FP32 floor)
+        const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
+                                           : fmaxf(1e-14f * rr, -rtol2);
 
         for (int it = 0; it < iters; ++it) {
             if (!(rr > rr_stop)) break;  // rr is identical in both warps
@@ -1655,7 +1661,10 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
         __syncthreads();
         float rr = s_red2[0] + s_red2[1];
         float pb = s_seam[wi ^ 1][lane];
-        const float rr_stop = fmaxf(rtol2, 1e-14f) * rr;
+        // rtol2 >= 0: relative stop (r.r <= max(rtol2, 1e-14) (r.r)_0); rtol2 < 0:
+        // also stop once r.r <= -rtol2 (an absolute level, or the FP32 floor)
+        const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
+                                           : fmaxf(1e-14f * rr, -rtol2);
         bool bad = !(rr < INFINITY);
 
         for (int it = 0; it < iters; ++it) {
