@@ -63,7 +63,7 @@ FLOP_PER_LAUNCH = 11
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the finest-level ORAS block kernel (ncu, 4K RGB,
 # the same launch as in the bench; see profiles/); None once the kernel changes.
-ORAS_TRAFFIC_BYTES = 149.2e6
+ORAS_TRAFFIC_BYTES = None
 
 
 def _hbm_peak():
@@ -406,7 +406,9 @@ def run_ours(args):
     n_l = max(1, prof["oras_l0_launches"])
     avg_ms = prof["oras_l0_ms"] / n_l
     pxch = prof["oras_l0_pixel_channels"] / n_l
-    steps_per = prof["oras_l0_cg_steps"] / n_l
+    # local CG steps the local problems completed (blocks stop early at the
+    # local_stop level), per local problem
+    steps_per = prof["oras_l0_cg_steps"] / max(1, prof["oras_l0_tasks"])
     flop = (FLOP_PER_STEP * steps_per + FLOP_PER_LAUNCH) * pxch
     achieved = flop / (avg_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_oras_2w (32x32 ORAS blocks, finest level)",
@@ -414,6 +416,7 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "traffic": ORAS_TRAFFIC_BYTES, "avg_launch_us": round(avg_ms * 1e3, 1),
                 "launches": prof["oras_l0_launches"],
+                "cg_steps_per_block": round(steps_per, 3),
                 "measured": f"CUDA events around every finest-level launch, one decoder alone "
                             f"on the same frames ({solo_n} frames) right after the timed region",
                 "peak_note": "FP32 FMA issue rate from unit counts x max clock (no measured "

@@ -189,15 +189,19 @@ di_status di_get_stats(const di_ctx *ctx, di_stats *out);
  * (all contexts of the process, since the library has one launch counter).
  * The oras_* fields are filled only when cfg.profile = 1: number of
  * finest-level ORAS block-kernel launches, their summed duration (from CUDA
- * events on the launching stream, so they include nothing but that kernel)
- * and the pixel-channels they processed. */
+ * events on the launching stream, so they include nothing but that kernel),
+ * the image pixel-channels they processed, their local problems (blocks x
+ * channels) and the local CG steps those problems completed (a block stops
+ * before the step limit at its residual floor or the cfg.local_stop level).
+ * Read after the decoding stream's work has completed. */
 typedef struct {
     long long launches;
     long long oras_l0_launches;
     double oras_l0_ms;
     long long oras_l0_pixel_channels;
-    long long oras_l0_cg_steps;  /* local CG step limit of those launches, summed */
-    long long reserved[4];
+    long long oras_l0_cg_steps;  /* local CG steps completed, summed over the local problems */
+    long long oras_l0_tasks;     /* local problems (blocks x channels) of those launches */
+    long long reserved[3];
 } di_profile;
 
 di_status di_get_profile(const di_ctx *ctx, di_profile *out);

@@ -55,7 +55,8 @@ class di_plan_info(ctypes.Structure):
 class di_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("oras_l0_launches", ctypes.c_longlong),
                 ("oras_l0_ms", ctypes.c_double), ("oras_l0_pixel_channels", ctypes.c_longlong),
-                ("oras_l0_cg_steps", ctypes.c_longlong), ("reserved", ctypes.c_longlong * 4)]
+                ("oras_l0_cg_steps", ctypes.c_longlong), ("oras_l0_tasks", ctypes.c_longlong),
+                ("reserved", ctypes.c_longlong * 3)]
 
 
 class di_image(ctypes.Structure):
@@ -263,7 +264,7 @@ class Context:
         _check(load().di_get_profile(self._h, ctypes.byref(pr)), self)
         return {"launches": pr.launches, "oras_l0_launches": pr.oras_l0_launches,
                 "oras_l0_ms": pr.oras_l0_ms, "oras_l0_pixel_channels": pr.oras_l0_pixel_channels,
-                "oras_l0_cg_steps": pr.oras_l0_cg_steps}
+                "oras_l0_cg_steps": pr.oras_l0_cg_steps, "oras_l0_tasks": pr.oras_l0_tasks}
 
     def reset_profile(self):
         _check(load().di_reset_profile(self._h), self)

@@ -78,7 +78,8 @@ struct di_ctx {
     cudaEvent_t gev[kGPairs][2] = {};
     int g_pairs = 0;            // event pairs recorded by one replay
     long long g_kernels = 0;    // kernels launched by one replay
-    long long g_oras = 0, g_pxch = 0, g_steps = 0;  // profile counters of one replay
+    long long g_oras = 0, g_pxch = 0, g_tasks = 0;  // profile counters of one replay
+    unsigned long long* dsteps = nullptr;  // device: completed finest-level local CG steps
 };
 
 namespace {
@@ -129,7 +130,7 @@ bool config_ok(const di_config& c) {
 }
 
 di_status cuda_fail(di_ctx* ctx, cudaError_t e, const char* what) {
-    if (ctx) std::snprintf(ctx->err, sizeof ctx->err, "%s: %s", what, cudaGetErrorString(e));
+    if (ctx) std::snprintf(ctx->err, sizeof ctx->err, "%.160s: %.80s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? DI_ERR_OOM : DI_ERR_CUDA;
 }
 
@@ -316,12 +317,14 @@ struct Sched {
             }
             ctx->prof.oras_l0_launches += 1;
             ctx->prof.oras_l0_pixel_channels += (long long)v.n * C;
-            ctx->prof.oras_l0_cg_steps += iters;
+            ctx->prof.oras_l0_tasks += (long long)axis_blocks(v.w, ctx->cfg.block, ctx->cfg.overlap) *
+                                       axis_blocks(v.h, ctx->cfg.block, ctx->cfg.overlap) * C;
         }
         DI_CUDA(ctx, launch_oras(in, zero_in, rhs, rhs_zero, v.mbits, v.w, v.h, C, ctx->cfg.block,
                                  ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
                                  ctx->planes, maxupd, s, ev, ctx->cfg.precision,
-                                 ctx->upd + kMaxUpdSlots));
+                                 ctx->upd + kMaxUpdSlots,
+                                 l == 0 && ctx->cfg.profile ? ctx->dsteps : nullptr));
         return DI_OK;
     }
 
@@ -432,7 +435,7 @@ bool capture_vcycle(di_ctx* ctx, Sched& S) {
     add_launches(-ctx->g_kernels);  // captured, not launched
     ctx->g_oras = ctx->prof.oras_l0_launches - p0.oras_l0_launches;
     ctx->g_pxch = ctx->prof.oras_l0_pixel_channels - p0.oras_l0_pixel_channels;
-    ctx->g_steps = ctx->prof.oras_l0_cg_steps - p0.oras_l0_cg_steps;
+    ctx->g_tasks = ctx->prof.oras_l0_tasks - p0.oras_l0_tasks;
     ctx->prof = p0;
     if (st != DI_OK || e != cudaSuccess || g == nullptr || which != 0) {
         if (g) cudaGraphDestroy(g);
@@ -525,6 +528,8 @@ di_status di_create(const di_config* cfg, int device, di_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->upd, (kMaxUpdSlots + 1) * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(ctx->upd, 0, (kMaxUpdSlots + 1) * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->cg_sc, 4 * kMaxChannels * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dsteps, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dsteps, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host, 4096);
     if (e != cudaSuccess) {
         di_status st = cuda_fail(ctx, e, "di_create");
@@ -551,6 +556,7 @@ void di_destroy(di_ctx* ctx) {
     if (ctx->counts) cudaFree(ctx->counts);
     if (ctx->upd) cudaFree(ctx->upd);
     if (ctx->cg_sc) cudaFree(ctx->cg_sc);
+    if (ctx->dsteps) cudaFree(ctx->dsteps);
     if (ctx->host) cudaFreeHost(ctx->host);
     delete ctx;
 }
@@ -574,6 +580,11 @@ di_status di_get_profile(const di_ctx* ctx, di_profile* out) {
     if (!ctx || !out) return DI_ERR_INVALID_ARG;
     *out = ctx->prof;
     out->launches = launch_count() - ctx->launch_base;
+    unsigned long long steps = 0;
+    if (cudaSetDevice(ctx->device) != cudaSuccess ||
+        cudaMemcpy(&steps, ctx->dsteps, sizeof steps, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DI_ERR_CUDA;
+    out->oras_l0_cg_steps = (long long)steps;
     return DI_OK;
 }
 
@@ -581,6 +592,9 @@ di_status di_reset_profile(di_ctx* ctx) {
     if (!ctx) return DI_ERR_INVALID_ARG;
     std::memset(&ctx->prof, 0, sizeof ctx->prof);
     ctx->launch_base = launch_count();
+    if (cudaSetDevice(ctx->device) != cudaSuccess ||
+        cudaMemset(ctx->dsteps, 0, sizeof(unsigned long long)) != cudaSuccess)
+        return DI_ERR_CUDA;
     return DI_OK;
 }
 
@@ -733,7 +747,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
             add_launches(ctx->g_kernels);
             ctx->prof.oras_l0_launches += ctx->g_oras;
             ctx->prof.oras_l0_pixel_channels += ctx->g_pxch;
-            ctx->prof.oras_l0_cg_steps += ctx->g_steps;
+            ctx->prof.oras_l0_tasks += ctx->g_tasks;
             if (cfg.profile && cfg.stop_rule == DI_STOP_FIXED_CYCLES) {
                 // the replay's event pairs are re-recorded by the next one
                 DI_CUDA(ctx, cudaStreamSynchronize(s));

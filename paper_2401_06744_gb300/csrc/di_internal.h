@@ -89,12 +89,13 @@ inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
 // block kernel (the combine kernels follow the second one).  precision: 0
 // FP32, 1 FP16, 2 BF16 local CG iterates (32x32 blocks; other sizes use FP32).
 // errflag (nullable): set to 1 when a bounded device-side wait of the FP32
-// 32x32 kernel ran out (its tile copies did not arrive).
+// 32x32 kernel ran out (its tile copies did not arrive).  step_count
+// (nullable): gains the local CG steps completed, summed over the tasks.
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev = nullptr, int precision = 0,
-                        unsigned* errflag = nullptr);
+                        unsigned* errflag = nullptr, unsigned long long* step_count = nullptr);
 
 // Global CG smoother: `steps` CG steps on the level's reduced system from the
 // iterate `in`, out = in + correction; restart = 0 continues the previous

@@ -729,7 +729,7 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
             int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C,
             int o, int nbx, int nby, float alpha, int iters, float rtol2,
             float* __restrict__ u_out, float* __restrict__ planes, unsigned* __restrict__ maxupd,
-            int chan_inner) {
+            int chan_inner, unsigned long long* __restrict__ step_count) {
     using WT = WarpTile<B>;
     constexpr int G = WT::G, R = WT::R, NP = WT::NP, TH = WT::TH, P = WT::P, TILE = WT::TILE;
     static_assert(G * B == 32 && R * G == B && NP * 2 == R, "warp shape");
@@ -822,6 +822,7 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
     float vmax = 0.f;
+    unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
     for (int i = 0;; ++i) {
         cp_async_wait_all();
@@ -953,6 +954,7 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
             const f2 b2 = pk(beta, beta);
 #pragma unroll
             for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
+            ++nsteps;
         }
 
         // u_out = u_in + sum_i R_i^T D_i v_i: weight-1 pixels directly, shared
@@ -1008,6 +1010,7 @@ k_oras_warp(const float* __restrict__ u_in, int zero_in, const float* __restrict
         ch = nch;
         buf ^= 1;
     }
+    if (step_count && lane == 0) atomicAdd(step_count, (unsigned long long)nsteps);
     if (maxupd) {
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
@@ -1099,7 +1102,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
           int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
           float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
           const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
-          int use_tma, unsigned* __restrict__ errflag) {
+          int use_tma, unsigned* __restrict__ errflag,
+          unsigned long long* __restrict__ step_count) {
     constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
     constexpr int TILE = Smem2W::USTRIDE;
     extern __shared__ float smem_raw[];
@@ -1220,6 +1224,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
     float vmax = 0.f;
+    unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
     for (int i = 0;; ++i) {
         if (use_tma) {
@@ -1370,6 +1375,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 #pragma unroll
             for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
             pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
+            ++nsteps;
         }
 
         // x-only shared pixels go to the compact seam strips that follow the
@@ -1443,6 +1449,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         ch = nc2;
         buf ^= 1;
     }
+    if (step_count && t == 0) atomicAdd(step_count, (unsigned long long)nsteps);
     if (maxupd) {
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
@@ -1487,7 +1494,8 @@ __global__ void __launch_bounds__(64, 10)
 k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
             int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
             int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
-            float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner) {
+            float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
+            unsigned long long* __restrict__ step_count) {
     typedef typename H::T2 T2;
     constexpr int B = 32, NP = 8, TH = Tile2W::TH, P = Tile2W::P, TILE = Tile2W::TILE;
     extern __shared__ float smem[];
@@ -1567,6 +1575,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
     float vmax = 0.f;
+    unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
     for (int i = 0;; ++i) {
         cp_async_wait_all();
@@ -1721,6 +1730,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
 #pragma unroll
             for (int k = 0; k < NP; ++k) p[k] = __hfma2(b2, p[k], r[k]);
             pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
+            ++nsteps;
         }
 
         const int par = (kx & 1) | ((ky & 1) << 1);
@@ -1770,6 +1780,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
         ch = nc2;
         buf ^= 1;
     }
+    if (step_count && t == 0) atomicAdd(step_count, (unsigned long long)nsteps);
     if (maxupd) {
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
@@ -1919,7 +1930,8 @@ int cached_occupancy(const void* kern, int threads, size_t smem, size_t smem_max
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                           cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag) {
+                           cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
+                           unsigned long long* step_count) {
     constexpr int B = 32;
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
@@ -1952,15 +1964,15 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     if (precision == 0)
         k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
                                          nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
-                                         chan_inner, tm_u, tm_b, use_tma, errflag);
+                                         chan_inner, tm_u, tm_b, use_tma, errflag, step_count);
     else if (precision == 1)
         k_oras_2w_h<HalfT><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
                                                   C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                  planes, maxupd, chan_inner);
+                                                  planes, maxupd, chan_inner, step_count);
     else
         k_oras_2w_h<Bf16T><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
                                                   C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                  planes, maxupd, chan_inner);
+                                                  planes, maxupd, chan_inner, step_count);
     count();
     if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -1972,7 +1984,8 @@ template <int B>
 cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                           const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                           int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                          cudaStream_t s, cudaEvent_t* ev) {
+                          cudaStream_t s, cudaEvent_t* ev,
+                          unsigned long long* step_count) {
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
     constexpr int FIXED = WarpTile<B>::FIXED;
@@ -2001,7 +2014,7 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     if (ev) record_event(ev[0], s);
     k_oras_warp<B><<<grid, 32, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
                                           nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
-                                          chan_inner);
+                                          chan_inner, step_count);
     count();
     if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
@@ -2237,18 +2250,20 @@ cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
-                        cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag) {
+                        cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
+                        unsigned long long* step_count) {
     const int wpr = mask_words_per_row(w);
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                  iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag);
+                                  iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag,
+                                  step_count);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                     iters, rtol2, u_out, planes, maxupd, s, ev);
+                                     iters, rtol2, u_out, planes, maxupd, s, ev, step_count);
         case 8:
             return launch_oras_t<8>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
-                                    iters, rtol2, u_out, planes, maxupd, s, ev);
+                                    iters, rtol2, u_out, planes, maxupd, s, ev, step_count);
         default:
             return cudaErrorInvalidValue;
     }

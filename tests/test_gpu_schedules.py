@@ -202,3 +202,19 @@ def test_coarse_level_local_steps(di, case):
     u2, st2, _ = _run(di, f, c, TOL, local_iters=10, local_iters_coarse=4, max_cycles=64)
     assert st2 == di.OK
     _check(u2, f, c, ref, TOL)
+
+
+def test_profile_counts_completed_local_steps(di, case):
+    # the profile counts the local CG steps the finest-level local problems
+    # completed: at most the step limit each, fewer with the local stop
+    f, c, _ = case
+    per_task = {}
+    for ls in (-1.0, 0.2):
+        with di.Context(profile=1, local_stop=ls) as ctx:
+            ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), tol=TOL)
+            torch.cuda.synchronize()
+            pr = ctx.profile()
+        assert pr["oras_l0_tasks"] > 0
+        assert 0 < pr["oras_l0_cg_steps"] <= 8 * pr["oras_l0_tasks"]  # default local_iters 8
+        per_task[ls] = pr["oras_l0_cg_steps"] / pr["oras_l0_tasks"]
+    assert per_task[0.2] <= per_task[-1.0]
