@@ -63,7 +63,7 @@ FLOP_PER_LAUNCH = 11
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the finest-level ORAS block kernel (ncu, 4K RGB,
 # the same launch as in the bench; see profiles/); None once the kernel changes.
-ORAS_TRAFFIC_BYTES = None
+ORAS_TRAFFIC_BYTES = 148.9e6
 
 
 def _hbm_peak():
