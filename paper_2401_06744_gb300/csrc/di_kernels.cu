@@ -1671,9 +1671,10 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
         float rr = s_red2[0] + s_red2[1];
         float pb = s_seam[wi ^ 1][lane];
         // rtol2 >= 0: relative stop (r.r <= max(rtol2, 1e-14) (r.r)_0); rtol2 < 0:
-        // also stop once r.r <= -rtol2 (an absolute level, or the FP32 floor)
+        // also stop once r.r <= -rtol2 (an absolute level, or the FP32 floor). rr is
+        // the normalised residual's, so the absolute level is scaled by isc^2 too.
         const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
-                                           : fmaxf(1e-14f * rr, -rtol2);
+                                           : fmaxf(1e-14f * rr, -rtol2 * isc * isc);
         bool bad = !(rr < INFINITY);
 
         for (int it = 0; it < iters; ++it) {
