@@ -36,6 +36,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 
 #include <cuda.h>  // CUtensorMap and its enums (the encoder comes from the runtime)
 #include <cuda_bf16.h>
@@ -1128,12 +1129,13 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     // bits and operator serve all its channels); otherwise (fewer blocks than
     // CTA slots) tasks blockIdx.x, +gridDim.x, ... of the (block, channel) list.
     const int nblk = nbx * nby;
-    auto task_of = [&](int i, int& blk, int& ch) {
+    // the task after (blk, ch) in this CTA's sequence (no division on the
+    // channel-inner path, which the large levels take)
+    auto next_task = [&](int& blk, int& ch) {
         if (chan_inner) {
-            blk = (int)blockIdx.x + (i / C) * (int)gridDim.x;
-            ch = i % C;
+            if (++ch == C) { ch = 0; blk += (int)gridDim.x; }
         } else {
-            const int tt = (int)blockIdx.x + i * (int)gridDim.x;
+            const int tt = blk * C + ch + (int)gridDim.x;
             blk = tt / C;
             ch = tt - blk * C;
         }
@@ -1203,8 +1205,9 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         }
     };
 
-    int blk, ch;
-    if (!task_of(0, blk, ch)) return;  // block-uniform
+    int blk = chan_inner ? (int)blockIdx.x : (int)blockIdx.x / C;
+    int ch = chan_inner ? 0 : (int)blockIdx.x - blk * C;
+    if (blk >= nblk) return;  // block-uniform
     if (use_tma) {
         if (t == 0) {
             for (int b = 0; b < 2; ++b)
@@ -1223,10 +1226,11 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     f2 ml2 = 0ull, mr2 = 0ull;
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
+    uint32_t rows_w = 0;  // bit ly: row ly of the block is in the image with weight > 0
     float vmax = 0.f;
     unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
-    for (int i = 0;; ++i) {
+    for (;;) {
         if (use_tma) {
             const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[buf]);
             bool ok = mbar_wait(bar, (phase >> buf) & 1u);
@@ -1242,8 +1246,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             __syncthreads();
         }
         const uint32_t mlo = nlo, mhi = nhi;
-        int nb2, nc2;
-        const bool more = task_of(i + 1, nb2, nc2);
+        int nb2 = blk, nc2 = ch;
+        const bool more = next_task(nb2, nc2);
         if (more) prefetch(nb2, nc2, buf ^ 1, blk);
 
         if (blk != cur_blk) {
@@ -1281,8 +1285,10 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
             }
             wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
-            if (t < B) s_wy[t] = ramp_weight(t, ky, nby, s, o, inv_o1);
+            const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);  // row lane
+            if (t < B) s_wy[t] = wyl;
             // s_wy is read only after the barriers of the CG below
+            rows_w = __ballot_sync(kFull, wyl > 0.f && lane < bh);
         }
 
         // TMA tiles start at the 4-aligned column below the halo column
@@ -1293,25 +1299,37 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 
         f2 x[NP], r[NP], p[NP], q[NP];
         f2 acc0 = 0ull, acc1 = 0ull;
+        // r = b - A u on the block (0 on the mask).  The variants: rows off the
+        // image's top and bottom rows (vertical degree 2), and b = 0 off the mask.
+        auto residual = [&](auto interior, auto rhs0) {
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            float rv[2];
+            for (int k = 0; k < NP; ++k) {
+                float rv[2];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int ly = row0 + k + 8 * e, gy = y0 + ly;
-                float v = rhs_zero ? 0.f : tb[ly * PB + col];
-                if (!zero_in) {
-                    const float* c0 = tu + (ly + 1) * P + col + 1;
-                    const float dv = (float)((gy > 0) + (gy < h - 1));
-                    v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                    float v = decltype(rhs0)::value ? 0.f : tb[ly * PB + col];
+                    if (!zero_in) {
+                        const float* c0 = tu + (ly + 1) * P + col + 1;
+                        const float dv = decltype(interior)::value
+                                             ? 2.f : (float)((gy > 0) + (gy < h - 1));
+                        v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                    }
+                    rv[e] = v;
                 }
-                rv[e] = v;
+                r[k] = mul2(pk(rv[0], rv[1]), keep[k]);
+                p[k] = r[k];
+                x[k] = 0ull;
+                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+                else acc0 = fma2(r[k], r[k], acc0);
             }
-            r[k] = mul2(pk(rv[0], rv[1]), keep[k]);
-            p[k] = r[k];
-            x[k] = 0ull;
-            if (k & 1) acc1 = fma2(r[k], r[k], acc1);
-            else acc0 = fma2(r[k], r[k], acc0);
+        };
+        if (y0 > 0 && y0 + B < h) {
+            if (rhs_zero) residual(std::true_type{}, std::true_type{});
+            else residual(std::true_type{}, std::false_type{});
+        } else {
+            if (rhs_zero) residual(std::false_type{}, std::true_type{});
+            else residual(std::false_type{}, std::false_type{});
         }
         acc0 = add2(acc0, acc1);
         // seam rows: warp 0 publishes its row 15 (hi of pair 7), warp 1 its row 16 (lo of pair 0)
@@ -1378,22 +1396,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             ++nsteps;
         }
 
-        // x-only shared pixels go to the compact seam strips that follow the
-        // four parity planes: strip[side][ch][seam - 1][y][j], side 0 = left block
-        const int nsh = shared_per_seam(o), first = shared_first(o);
-        int sx_seam = -1, sx_side = 0, sx_j = 0;
-        if (kx > 0 && col >= first && col < first + nsh) {
-            sx_seam = kx; sx_side = 1; sx_j = col - first;
-        } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
-            sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
-        }
-        float* strip = sx_seam > 0
-                           ? planes + 4 * (size_t)C * n +
-                                 (((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h) *
-                                     nsh + sx_j
-                           : planes;
-        const int par = (kx & 1) | ((ky & 1) << 1);
-        float* plane = planes + ((size_t)par * C + ch) * n;
+        const int nsh = shared_per_seam(o);
         float* uo = u_out + ch * n;
         const bool colok = x0 + col < w;
         if (nsh == 0) {
@@ -1403,11 +1406,11 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 float* uol = uo + (size_t)(y0 + row0) * w + x0 + col;
                 const float* tol = tu + (row0 + 1) * P + col + 1;
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
+                for (int e = 0; e < 2; ++e) {
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
+                    for (int k = 0; k < NP; ++k) {
                         const int j = k + 8 * e;
-                        if (row0 + j >= bh || !(s_wy[row0 + j] > 0.f)) continue;
+                        if (!((rows_w >> (row0 + j)) & 1u)) continue;
                         const float v = e ? hi2(x[k]) : lo2(x[k]);
                         uol[j * w] = (zero_in ? 0.f : tol[j * P]) + v;
                         vmax = fmaxf(vmax, fabsf(v));
@@ -1415,34 +1418,49 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 }
             }
         } else {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int ly = row0 + k + 8 * e;
-                if (ly >= bh || !colok) continue;
-                const float v = e ? hi2(x[k]) : lo2(x[k]);
-                const float d = wx * s_wy[ly];
-                const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
-                // the first contributor of a shared pixel (smallest block
-                // index along each shared axis) also carries u_in, so the
-                // combine passes only add parked values
-                const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
-                if (d == 1.f) {
-                    uo[gp] = uold + v;
-                } else if (d > 0.f) {
-                    const float wyr = s_wy[ly];
-                    const bool xfirst = sx_seam < 0 || sx_side == 0;  // no left partner on x
-                    if (wyr < 1.f) {
-                        const bool yfirst = ly >= s;  // upper block of its row overlap
-                        plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
-                    } else {
-                        strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
-                    }
-                }
-                if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+            // x-only shared pixels go to the compact seam strips that follow the
+            // four parity planes: strip[side][ch][seam - 1][y][j], side 0 = left block
+            const int first = shared_first(o);
+            int sx_seam = -1, sx_side = 0, sx_j = 0;
+            if (kx > 0 && col >= first && col < first + nsh) {
+                sx_seam = kx; sx_side = 1; sx_j = col - first;
+            } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
+                sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
             }
-        }
+            const size_t strip_row0 =
+                ((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h;
+            float* strip = sx_seam > 0 ? planes + 4 * (size_t)C * n + strip_row0 * nsh + sx_j
+                                       : planes;
+            const int par = (kx & 1) | ((ky & 1) << 1);
+            float* plane = planes + ((size_t)par * C + ch) * n;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = row0 + k + 8 * e;
+                    if (ly >= bh || !colok) continue;
+                    const float v = e ? hi2(x[k]) : lo2(x[k]);
+                    const float d = wx * s_wy[ly];
+                    const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
+                    // the first contributor of a shared pixel (smallest block
+                    // index along each shared axis) also carries u_in, so the
+                    // combine passes only add parked values
+                    const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
+                    if (d == 1.f) {
+                        uo[gp] = uold + v;
+                    } else if (d > 0.f) {
+                        const float wyr = s_wy[ly];
+                        const bool xfirst = sx_seam < 0 || sx_side == 0;  // no left partner on x
+                        if (wyr < 1.f) {
+                            const bool yfirst = ly >= s;  // upper block of its row overlap
+                            plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
+                        } else {
+                            strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
+                        }
+                    }
+                    if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
+                }
+            }
         }
         if (!more) break;
         blk = nb2;
