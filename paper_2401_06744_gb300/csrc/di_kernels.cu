@@ -1272,18 +1272,31 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             const float ml = col > 0 ? 1.f : 0.f, mr = col < B - 1 ? 1.f : 0.f;
             ml2 = pk(ml, ml);
             mr2 = pk(mr, mr);
+            if (bh == B) {
+                // full height: vertical coupling count 2 except in rows 0 and 31
+                const float d2 = -(hc + 2.f);
+                const float vt = (y0 > 0 ? alpha : 0.f) + 1.f;
+                const float vb = 1.f + (y0 + B < h ? alpha : 0.f);
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                float vc[2];
+                for (int k = 0; k < NP; ++k) ndg[k] = pk(d2, d2);
+                if (wi == 0) ndg[0] = pk(-(hc + vt), d2);
+                else ndg[NP - 1] = pk(d2, -(hc + vb));
+            } else {
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int ly = row0 + k + 8 * e, gy = y0 + ly;
-                    vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
-                            (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                for (int k = 0; k < NP; ++k) {
+                    float vc[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                        vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
+                                (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                    }
+                    ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
                 }
-                ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
-                keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
             }
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
             wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
             const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);  // row lane
             if (t < B) s_wy[t] = wyl;
