@@ -45,7 +45,8 @@ typedef enum {
     DI_ERR_NOT_CONVERGED = 4, /* max_cycles reached first; u holds the last iterate */
     DI_ERR_CUDA = 5,          /* a CUDA runtime call failed */
     DI_ERR_TIMEOUT = 6        /* a bounded device-side wait ran out: a tile copy of the
-                                 32x32 block kernel did not arrive; u is not valid */
+                                 32x32 block kernel did not arrive; every output of the
+                                 call (u included) is undefined */
 } di_status;
 
 /* Stop rules of di_inpaint.  DI_STOP_ERROR_ESTIMATE: after every V-cycle the
@@ -336,9 +337,13 @@ di_status di_residual_norm(di_ctx *ctx, const float *u, const float *b, int rhs_
  *  Limit: ceil(width/32) * ceil(height/8) * channels <= DI_NOALLOC_PARTIALS
  *    (3840x2160 with up to 4 channels fits); a larger call returns
  *    DI_ERR_INVALID_ARG before touching the GPU.
- *  Set-up: the first call on a device looks up the array's device address
- *    (with that device current), so make that first call before any stream
- *    capture on the device.
+ *  Device and set-up: the kernels run on the calling thread's current
+ *    device, so `stream` must belong to that device (a stream of another
+ *    device makes the launch fail with DI_ERR_CUDA).  The first call on a
+ *    device (and the first after its context was destroyed and created
+ *    again, e.g. by a device reset) looks up the array's device address with
+ *    that device current, so make that first call before any stream capture
+ *    on the device.
  *  Sharing: every call uses the same array and leaves its partial sums
  *    there; nothing in it needs to start at zero.  Calls whose kernels
  *    overlap on the GPU (different streams or host threads without ordering)
@@ -369,8 +374,8 @@ di_status di_prolong(const float *uH, const float *b, const uint8_t *c, int widt
                      int channels, float *u, int mode, void *stream);
 
 /* One ORAS iteration (Algorithm 2) with the context's block size, overlap
- * and alpha: r = b - A u_in; on every block i, `local_iters` Jacobi-PCG steps
- * (from 0) on A_i v_i = R_i r, A_i = A restricted to the block with Robin rows
+ * and alpha: r = b - A u_in; on every block i, `local_iters` steps of plain
+ * (unpreconditioned) conjugate gradients (from 0, Section 3.1) on A_i v_i = R_i r, A_i = A restricted to the block with Robin rows
  * on inner block edges (Section 3); u_out = u_in + sum_i R_i^T D_i v_i with
  * the separable linear partition-of-unity weights of Section 3.1.
  *  u_in: [ch][h][w]; must equal b at mask pixels (then r = 0 there).

@@ -2125,14 +2125,46 @@ cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_
 // Fixed reduction scratch for callers that cannot allocate (see
 // di_residual_norm_noalloc in di.h).  Host code must not pass the symbol
 // itself to a kernel: on the host it names a stand-in, not device memory.
-// Its device address is looked up once per device, with that device current.
+// Its device address is looked up once per device and context, with that
+// device current: a context that is destroyed and created again (a device
+// reset) loads the module anew, so the address is keyed on the context's
+// process-unique id, not on the device ordinal alone.
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Process-unique id of the calling thread's current context (0 if none).
+unsigned long long current_context_id() {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx ||
+        get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 cudaError_t launch_residual_noalloc(const float* u, const float* b, int rhs_zero,
                                     const uint8_t* c, int w, int h, int C, float* r,
                                     double* norm2, cudaStream_t s) {
     static std::mutex mu;
     static double* addr[128] = {};
+    static unsigned long long addr_ctx[128] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -2140,11 +2172,16 @@ cudaError_t launch_residual_noalloc(const float* u, const float* b, int rhs_zero
     double* scratch;
     {
         std::lock_guard<std::mutex> lock(mu);
-        if (!addr[dev]) {
+        unsigned long long id = current_context_id();
+        if (!addr[dev] || id == 0 || id != addr_ctx[dev]) {
+            // first call on this device, or its context changed: (re)load
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_partials);
             if (e != cudaSuccess) return e;
             addr[dev] = static_cast<double*>(p);
+            // the lookup makes the primary context current if none was
+            if (id == 0) id = current_context_id();
+            addr_ctx[dev] = id;
         }
         scratch = addr[dev];
     }

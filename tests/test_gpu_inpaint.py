@@ -185,9 +185,10 @@ def test_non_default_stream(di):
 
 
 def test_full_size_bench_frames_in_bench_configuration(di):
-    # the 4 % and 1 % edge-clustered 3840x2160 RGB bench frames, decoded as the
-    # bench times them (its block, overlap and local steps; two decoders with
-    # their own contexts and streams at once), against the FP64 oracle
+    # all six 3840x2160 RGB bench frames ({10, 4, 1} % x {edge-clustered,
+    # uniform}, the bench's seeds), decoded as the bench times them (its block,
+    # overlap and local steps; two decoders with their own contexts and streams
+    # at once), each against the FP64 oracle at the 0.05 / 0.01 bar
     import os
     import sys
     import threading
@@ -195,28 +196,31 @@ def test_full_size_bench_frames_in_bench_configuration(di):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
 
+    ks = list(range(len(bench.CASES)))
     frames = [synth.make_case(bench.W4K, bench.H4K, bench.C4K, *bench.CASES[k],
-                              bench._case_seed(k)) for k in (1, 2)]
+                              bench._case_seed(k)) for k in ks]
     cfg = dict(block=bench.BLOCK, overlap=bench.OVERLAP, local_iters=bench.LOCAL_ITERS,
                local_iters_coarse=bench.LOCAL_ITERS_COARSE)
-    outs, sts = [None, None], [None, None]
+    outs, sts = [None] * len(ks), [None] * len(ks)
 
     def work(t):
-        f, c = frames[t]
         s = torch.cuda.Stream(DEV)
         with di.Context(**cfg) as ctx, torch.cuda.stream(s):
-            u, st = ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV),
-                                tol=TOL, stream=s)
-            s.synchronize()
-            outs[t], sts[t] = u.cpu().numpy(), st
+            for j in range(t, len(ks), 2):
+                f, c = frames[j]
+                u, st = ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV),
+                                    tol=TOL, stream=s)
+                s.synchronize()
+                outs[j], sts[j] = u.cpu().numpy(), st
 
     th = [threading.Thread(target=work, args=(t,)) for t in range(2)]
     for x in th:
         x.start()
     for x in th:
         x.join()
-    for (f, c), u, st in zip(frames, outs, sts):
-        assert st == di.OK
+    for j, ((f, c), u, st) in enumerate(zip(frames, outs, sts)):
+        assert st == di.OK, bench.CASES[j]
         _check(u, f, c, oracle.cg_inpaint(f, c))
-        solo, st2, _ = _run(di, f, c, **cfg)
-        assert st2 == di.OK and np.array_equal(u, solo)
+        if j in (1, 2):  # the same result when decoded alone
+            solo, st2, _ = _run(di, f, c, **cfg)
+            assert st2 == di.OK and np.array_equal(u, solo)

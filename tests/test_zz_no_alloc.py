@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import method as M
+
 DEV = torch.device("cuda:0")
 
 
@@ -40,7 +42,10 @@ def _case(h, w, C, d, seed):
 @pytest.mark.gpu
 def test_noalloc_matches_context_entry_point_twice(di):
     # two calls in a row on different shapes: the shared scratch keeps the
-    # first call's partial sums, which the second must not pick up
+    # first call's partial sums, which the second must not pick up.  Each
+    # result is compared with the context entry point and with the oracle's
+    # FP64 residual r = b - A u (Algorithm 2 step 1, eq. 2.6) and its squared
+    # 2-norm per channel.
     cases = [((333, 171, 3), True, 1), ((1080, 1920, 1), False, 2)]
     with di.Context() as ctx:
         for (h, w, C), rhs_zero, seed in cases:
@@ -52,6 +57,12 @@ def test_noalloc_matches_context_entry_point_twice(di):
             assert torch.isfinite(r_na).all()
             assert (r_na - r_ref).abs().max().item() <= 2e-4
             assert np.allclose(n_na.cpu().numpy(), n_ref.cpu().numpy(), rtol=1e-5, atol=1e-6)
+            # b is read only on the mask when rhs_zero is set (b = C f there)
+            rhs = M.rhs(b, c) if rhs_zero else b
+            r_or = M.residual(u, rhs, c)
+            assert np.abs(r_na.cpu().numpy() - r_or).max() <= 2e-4
+            assert np.allclose(n_na.cpu().numpy(), (r_or ** 2).sum(axis=(1, 2)), rtol=1e-5,
+                               atol=1e-6)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch_before_touching_the_gpu(di):
