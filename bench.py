@@ -696,6 +696,43 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_decode_once(args):
+    """The six bench frames decoded once each by one decoder with the bench's
+    solver setting (graphs as in the bench), after one warm-up decode of
+    every frame: the launches a whole-decode ncu capture (`-s` the warm-up
+    launches) measures.  Prints the cycles per frame."""
+    import torch
+
+    from paper_2401_06744_gb300 import build as _build
+
+    _build.build()
+    import paper_2401_06744_gb300 as di
+
+    dev = torch.device("cuda", 0)
+    cases = _make_cases()
+    fd = [torch.from_numpy(f).to(dev) for f, _ in cases]
+    cd = [torch.from_numpy(c).to(dev) for _, c in cases]
+    out = torch.empty_like(fd[0])
+    cyc = []
+    with di.Context(device=0, block=args.block, overlap=args.overlap,
+                    local_iters=args.local_iters,
+                    local_iters_coarse=args.local_iters_coarse) as ctx:
+        for k in range(len(cases)):
+            ctx.inpaint(fd[k], cd[k], tol=TOL, out=out)
+        torch.cuda.synchronize(dev)
+        warm = ctx.profile()["launches"]
+        ctx.reset_profile()
+        for k in range(len(cases)):
+            _, st = ctx.inpaint(fd[k], cd[k], tol=TOL, out=out)
+            cyc.append(ctx.stats()["cycles"])
+        torch.cuda.synchronize(dev)
+        launches = ctx.profile()["launches"]
+    print(json.dumps({"frames": len(cases), "cycles": cyc, "launches": launches,
+                      "warmup_launches": warm,
+                      "block": args.block, "overlap": args.overlap,
+                      "local_iters": args.local_iters}), flush=True)
+
+
 def run_kernel(args):
     """One launch of one step of the path on the first bench frame (for ncu
     captures of a single kernel); prints a short JSON line."""
@@ -1048,6 +1085,9 @@ def main():
                     help="CG steps of the local block solves on the coarser levels")
     ap.add_argument("--streams", type=int, default=4,
                     help="frames in flight: decoders, each with its own context and stream")
+    ap.add_argument("--decode-once", action="store_true",
+                    help="decode the six bench frames once each after a warm-up pass "
+                         "(for whole-decode ncu captures) and exit")
     ap.add_argument("--compare", choices=["methods", "resolution", "video", "configs"],
                     help="print the comparison table of the schedules and smoothers "
                          "(one JSON line per row) and exit")
@@ -1057,6 +1097,9 @@ def main():
         return
     if args.kernel:
         run_kernel(args)
+        return
+    if args.decode_once:
+        run_decode_once(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -85,12 +85,13 @@ enum { DI_SCHED_REDUCED_FMG = 0, DI_SCHED_FULL_FMG = 1, DI_SCHED_MULTILEVEL = 2,
  * The single-block solve of the coarsest level always uses the block solver. */
 enum { DI_SMOOTH_ORAS = 0, DI_SMOOTH_CG = 1 };
 
-/* Launch of the finest-level V-cycles.  ON: each di_inpaint call captures one
- * V-cycle as a CUDA graph (on a stream of the context, while the cascade
- * runs) and replays it once per cycle, which removes the per-kernel launch
- * gaps; used for the V-cycle schedules with pre + post even, otherwise (and
- * if the capture fails) the kernels are launched one by one.  OFF: always
- * one by one.  The results are identical. */
+/* Launch of the decode.  ON: CUDA graphs -- the whole decode as one
+ * device-driven graph (see di_inpaint) where the configuration allows it;
+ * otherwise (profiling on, the full-FMG schedule) one finest-level V-cycle
+ * captured per call and replayed once per cycle with the stop rule on the
+ * host; the multilevel and single-level schedules launch kernel by kernel.
+ * If a capture fails the kernels are launched one by one.  OFF: always one
+ * by one, stop rule on the host.  The results are identical. */
 enum { DI_GRAPH_ON = 0, DI_GRAPH_OFF = 1 };
 
 /* Initial iterate.  CASCADE: the coarse-to-fine cascade of the schedule (or,
@@ -143,6 +144,7 @@ typedef struct {
     float est_error;       /* last error estimate (gray levels), DI_STOP_ERROR_ESTIMATE */
     float rel_residual[4]; /* final ||b - A u||_2 / ||b||_2 per channel (if computed) */
     long long unknowns;    /* unknown pixels on the finest level */
+    int status;            /* di_status of the call */
 } di_stats;
 
 /* Static plan of a solve, computed on the host without touching a GPU. */
@@ -177,12 +179,36 @@ void di_destroy(di_ctx *ctx);
  *     exactly).
  *  tol: target of the stop rule (gray levels for the error estimate, a ratio
  *     for the relative residual), > 0.
- * The call enqueues its kernels on `stream` and waits for the stream once per
- * V-cycle to evaluate the stop rule, so it returns with the work finished. */
+ * How it runs.  Device-driven (the default: cfg.graph = DI_GRAPH_ON with the
+ * reduced-FMG schedule, no profiling, pre + post even and an image larger
+ * than one block): the whole decode is one CUDA graph launch on `stream` --
+ * pyramid, cascade and the V-cycle loop, with the stop rule evaluated on the
+ * device after every cycle (a WHILE node) and the levels in use and the
+ * cascade's start chosen on the device from the mask (IF / SWITCH nodes), so
+ * no host round trip happens during the decode.  The graph is captured on
+ * the first call with a given (f, c, u, size, tol) and replayed by later
+ * calls with the same buffers (a context keeps the last 8); the buffers'
+ * contents may change between calls.  di_inpaint then waits for the stream
+ * once, at the end.  Host-driven (every other configuration): the host
+ * evaluates the stop rule, waiting for the stream after the pyramid and once
+ * per V-cycle.  Both give bit-identical results.  The call returns with the
+ * work finished. */
 di_status di_inpaint(di_ctx *ctx, const float *f, const uint8_t *c, int width, int height,
                      int channels, float tol, float *u, void *stream);
 
-/* Statistics of the last di_inpaint call. */
+/* di_inpaint without the final wait: on the device-driven path the call
+ * enqueues the decode on `stream` and returns DI_OK at once (argument errors
+ * are still reported synchronously); the decode's status (DI_OK,
+ * DI_ERR_NOT_CONVERGED, DI_ERR_EMPTY_MASK, DI_ERR_TIMEOUT) is in
+ * di_stats.status, which di_get_stats waits for.  On the host-driven path it
+ * behaves like di_inpaint.  The context's workspace serves one decode at a
+ * time: enqueue the calls of one context on one stream (or order them), and
+ * keep f, c and u valid until the work is done. */
+di_status di_inpaint_async(di_ctx *ctx, const float *f, const uint8_t *c, int width,
+                           int height, int channels, float tol, float *u, void *stream);
+
+/* Statistics of the last di_inpaint / di_inpaint_async call (after an
+ * asynchronous call, this waits for its work first). */
 di_status di_get_stats(const di_ctx *ctx, di_stats *out);
 
 /* Kernel counters of a context, accumulated over di_inpaint calls since the
@@ -202,7 +228,8 @@ typedef struct {
     long long oras_l0_pixel_channels;
     long long oras_l0_cg_steps;  /* local CG steps completed, summed over the local problems */
     long long oras_l0_tasks;     /* local problems (blocks x channels) of those launches */
-    long long reserved[3];
+    long long device_decodes;    /* decodes run as one device-driven graph (see di_inpaint) */
+    long long reserved[2];
 } di_profile;
 
 di_status di_get_profile(const di_ctx *ctx, di_profile *out);

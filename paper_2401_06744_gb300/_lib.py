@@ -42,7 +42,7 @@ class di_stats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("levels_used", ctypes.c_int),
                 ("cycles", ctypes.c_int), ("converged", ctypes.c_int),
                 ("est_error", ctypes.c_float), ("rel_residual", ctypes.c_float * 4),
-                ("unknowns", ctypes.c_longlong)]
+                ("unknowns", ctypes.c_longlong), ("status", ctypes.c_int)]
 
 
 class di_plan_info(ctypes.Structure):
@@ -56,7 +56,7 @@ class di_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("oras_l0_launches", ctypes.c_longlong),
                 ("oras_l0_ms", ctypes.c_double), ("oras_l0_pixel_channels", ctypes.c_longlong),
                 ("oras_l0_cg_steps", ctypes.c_longlong), ("oras_l0_tasks", ctypes.c_longlong),
-                ("reserved", ctypes.c_longlong * 3)]
+                ("device_decodes", ctypes.c_longlong), ("reserved", ctypes.c_longlong * 2)]
 
 
 class di_image(ctypes.Structure):
@@ -89,6 +89,7 @@ _SIGS = {
     "di_create": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(_P)]),
     "di_destroy": (None, [_P]),
     "di_inpaint": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P]),
+    "di_inpaint_async": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, _P]),
     "di_get_stats": (_I, [_P, ctypes.POINTER(di_stats)]),
     "di_get_profile": (_I, [_P, ctypes.POINTER(di_profile)]),
     "di_reset_profile": (_I, [_P]),
@@ -252,19 +253,36 @@ class Context:
         res = u if f.dim() == 3 else u[0]
         return res, st
 
+    def inpaint_async(self, f: torch.Tensor, c: torch.Tensor, tol: float = 0.05,
+                      out: torch.Tensor | None = None, stream=None):
+        """Enqueue the decode on `stream` and return u at once (di_inpaint_async);
+        stats() waits for the work and gives its status."""
+        f3 = _img(f, "f")
+        c = _mask(c)
+        C, H, W = f3.shape
+        if c.shape != (H, W):
+            raise ValueError("mask shape does not match f")
+        u = torch.empty_like(f3) if out is None else _img(out, "out")
+        st = load().di_inpaint_async(self._h, f3.data_ptr(), c.data_ptr(), W, H, C, float(tol),
+                                     u.data_ptr(), _stream(stream))
+        _check(st, self)
+        return u if f.dim() == 3 else u[0]
+
     def stats(self) -> dict:
         s = di_stats()
         _check(load().di_get_stats(self._h, ctypes.byref(s)), self)
         return {"levels": s.levels, "levels_used": s.levels_used, "cycles": s.cycles,
                 "converged": bool(s.converged), "est_error": s.est_error,
-                "rel_residual": list(s.rel_residual), "unknowns": s.unknowns}
+                "rel_residual": list(s.rel_residual), "unknowns": s.unknowns,
+                "status": s.status}
 
     def profile(self) -> dict:
         pr = di_profile()
         _check(load().di_get_profile(self._h, ctypes.byref(pr)), self)
         return {"launches": pr.launches, "oras_l0_launches": pr.oras_l0_launches,
                 "oras_l0_ms": pr.oras_l0_ms, "oras_l0_pixel_channels": pr.oras_l0_pixel_channels,
-                "oras_l0_cg_steps": pr.oras_l0_cg_steps, "oras_l0_tasks": pr.oras_l0_tasks}
+                "oras_l0_cg_steps": pr.oras_l0_cg_steps, "oras_l0_tasks": pr.oras_l0_tasks,
+                "device_decodes": pr.device_decodes}
 
     def reset_profile(self):
         _check(load().di_reset_profile(self._h), self)

@@ -14,6 +14,7 @@
 // A level whose mask covers every pixel has an identically zero correction,
 // so recursion stops above the first such level and the cascade starts from
 // it (u = b there); this changes no arithmetic result.
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -36,6 +37,27 @@ struct Level {
     float* r = nullptr;          // restricted residual (right-hand side of the error equation)
     uint32_t* mbits = nullptr;   // bit-packed mask for the block solver
     long long unknowns = 0;
+};
+
+// One whole decode as a CUDA graph (pyramid, plan, cascade, V-cycle loop with
+// the stop test), valid for the buffers and sizes it was captured for.  The
+// level structure that depends on the mask (levels in use, the cascade's
+// start) is steered on the device by conditional nodes, so the graph needs no
+// host round trip.  Kernel counts per body feed the launch counter.
+struct DecodeGraph {
+    bool valid = false;
+    const float* f = nullptr;
+    const uint8_t* c = nullptr;
+    float* u = nullptr;
+    int w = 0, h = 0, C = 0;
+    float tol = 0.f;
+    unsigned long long ws_gen = 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long k_pre = 0, k_body = 0;
+    long long k_casc[kMaxLevels][kCascBodies] = {};
+    long long k_down[kMaxLevels] = {}, k_up[kMaxLevels] = {};
+    unsigned long long used = 0;
 };
 
 }  // namespace
@@ -80,6 +102,19 @@ struct di_ctx {
     long long g_kernels = 0;    // kernels launched by one replay
     long long g_oras = 0, g_pxch = 0, g_tasks = 0;  // profile counters of one replay
     unsigned long long* dsteps = nullptr;  // device: completed finest-level local CG steps
+    // device-driven decode (see DecodeGraph): stop-test state on the device,
+    // its pinned host copy, the capture streams of the graph and its bodies,
+    // and a cache of whole-decode graphs keyed by the call's buffers
+    StopState* dstate = nullptr;
+    StopState* hstate = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+    static constexpr int kGraphs = 8;
+    DecodeGraph graphs[kGraphs];
+    unsigned long long graph_clock = 0;
+    unsigned long long ws_gen = 0;     // workspace generation (graphs bake its addresses)
+    DecodeGraph* pending = nullptr;    // device-driven decode whose stats are not read yet
+    bool device_path_broken = false;   // a capture failed: use the host-driven loop
 };
 
 namespace {
@@ -165,7 +200,17 @@ void prof_flush_graph(di_ctx* ctx) {
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
+void drop_graph(DecodeGraph& dg) {
+    if (dg.exec) cudaGraphExecDestroy(dg.exec);
+    if (dg.g) cudaGraphDestroy(dg.g);
+    dg = DecodeGraph();
+}
+
 void free_workspace(di_ctx* ctx) {
+    // the cached decode graphs bake the workspace's addresses
+    for (auto& dg : ctx->graphs) drop_graph(dg);
+    ctx->pending = nullptr;
+    ++ctx->ws_gen;
     for (int k = 0; k < 4; ++k) {
         if (ctx->cg[k]) cudaFree(ctx->cg[k]);
         ctx->cg[k] = nullptr;
@@ -473,6 +518,372 @@ float bits_to_float(unsigned b) {
     return f;
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven decode
+//
+// The whole decode of one image is captured once (per buffers, size and
+// tolerance) into a CUDA graph and replayed: the pyramid with the unknown
+// counts, the plan kernel, the cascade and a WHILE node around the V-cycle
+// whose last kernel is the stop test.  What depends on the mask is decided on
+// the device: the plan kernel sets one IF node per coarse level (the level
+// takes part in the cycles iff it has unknown pixels, as the host-driven
+// recursion stops above the first fully known level) and one SWITCH node per
+// level of the cascade (its start on the coarsest or the first fully known
+// level, then prolongation and smoothing).  The V-cycle is written flat: the
+// down-sweep bodies (restriction into level l, then its pre-smoothing or the
+// coarsest solve) and the up-sweep bodies (post-smoothing of level l, then
+// prolongation of its correction) run under level l's IF node; because a
+// fully known level has only fully known levels below it, this is the
+// recursion of Sched::vcycle.  Results equal the host-driven loop bit for bit.
+// ---------------------------------------------------------------------------
+
+// Add a conditional node after everything captured so far on `s` (which must
+// be capturing) and return its body graphs.
+bool add_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
+                     cudaGraphConditionalNodeType type, unsigned size, cudaGraph_t** bodies) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+        return false;
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &p) != cudaSuccess) return false;
+    if (cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+        return false;
+    *bodies = p.conditional.phGraph_out;
+    return true;
+}
+
+// Capture into `body` on stream s whatever fn enqueues on it; the kernels it
+// launched (counted, then taken back from the launch counter) go to *kern.
+template <class Fn>
+bool capture_body(cudaStream_t s, cudaGraph_t body, long long* kern, Fn&& fn) {
+    if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return false;
+    const long long k0 = launch_count();
+    const bool ok = fn();
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &out);
+    const long long k = launch_count() - k0;
+    add_launches(-k);
+    if (kern) *kern += k;
+    return ok && e == cudaSuccess;
+}
+
+// Device address of a norm array of the stop state.
+enum { kBnorm2, kNorm2 };
+double* state_field(di_ctx* ctx, int which) {
+    char* base = reinterpret_cast<char*>(ctx->dstate);
+    return reinterpret_cast<double*>(
+        base + (which == kBnorm2 ? offsetof(StopState, bnorm2) : offsetof(StopState, norm2)));
+}
+
+// Value of the cascade SWITCH of level l (mirror of the plan kernel).
+int cascade_case(int l, int L, int Leff) {
+    if (Leff == 0) return l == 0 ? kCascSelect : kCascSkip;
+    const int top = Leff == L ? L - 1 : Leff;
+    if (l == top) return Leff == L ? kCascCoarsest : kCascSelect;
+    return l < top ? kCascProlong : kCascSkip;
+}
+
+bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, float* u, int w,
+                    int h, int C, float tol, DecodeGraph& dg) {
+    const di_config& cfg = ctx->cfg;
+    const int L = ctx->L;
+    for (int k = 0; k < 3; ++k)
+        if (!ctx->cs[k] && cudaStreamCreateWithFlags(&ctx->cs[k], cudaStreamNonBlocking) != cudaSuccess)
+            return false;
+    cudaStream_t s0 = ctx->cs[0], s1 = ctx->cs[1], s2 = ctx->cs[2];
+    cudaStream_t caller = S.s;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    PlanParams pp;
+    std::memset(&pp, 0, sizeof pp);
+    pp.L = L;
+    pp.cascade = cfg.start != DI_START_GIVEN;
+    pp.max_cycles = cfg.max_cycles;
+    pp.n0 = (unsigned long long)w * h;
+    bool ok = cudaGraphConditionalHandleCreate(&pp.h_loop, g, 0, cudaGraphCondAssignDefault) ==
+              cudaSuccess;
+    for (int l = 1; l < L && ok; ++l)
+        ok = cudaGraphConditionalHandleCreate(&pp.h_act[l], g, 0, cudaGraphCondAssignDefault) ==
+             cudaSuccess;
+    for (int l = 0; l < L && ok && pp.cascade; ++l)
+        ok = cudaGraphConditionalHandleCreate(&pp.h_casc[l], g, kCascSkip,
+                                              cudaGraphCondAssignDefault) == cudaSuccess;
+    if (!ok) {
+        cudaGraphDestroy(g);
+        return false;
+    }
+    dg = DecodeGraph();
+    const long long k0 = launch_count();
+    StopParams sp;
+    sp.rule = cfg.stop_rule;
+    sp.nslots = cfg.pre + 1 + cfg.post;
+    sp.min_cycles = cfg.min_cycles;
+    sp.max_cycles = cfg.max_cycles;
+    sp.C = C;
+    sp.tol = tol;
+    Level* lv = ctx->lv;
+    int nparts = 0;
+    const int pre = cfg.pre, post = cfg.post;
+    const int cur0 = pre & 1;  // buffer of a level's iterate after its pre-smoothing
+    unsigned long long* cnt = ctx->counts;
+
+    ok = cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
+         cudaSuccess;
+    if (ok) {
+        S.s = s0;
+        auto run = [&]() -> bool {
+            // 1. pyramids with the unknown counts, then the plan
+            if (cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s0) ||
+                cudaMemsetAsync(ctx->upd, 0, (kMaxUpdSlots + 1) * sizeof(unsigned), s0))
+                return false;
+            if (launch_pack_mask(c, w, h, lv[0].mbits, cnt + 1, s0)) return false;
+            for (int l = 1; l < L; ++l) {
+                Level& fl = lv[l - 1];
+                Level& cl = lv[l];
+                if (launch_mask_down(fl.c, fl.w, fl.h, const_cast<uint8_t*>(cl.c), s0)) return false;
+                if (pp.cascade &&
+                    launch_values_down(fl.c, fl.b, fl.w, fl.h, C, cl.c, const_cast<float*>(cl.b),
+                                       cfg.downsample == 0 ? 1 : 0, s0))
+                    return false;
+                if (launch_pack_mask(cl.c, cl.w, cl.h, cl.mbits, cnt + 1 + l, s0)) return false;
+            }
+            if (launch_plan(cnt, ctx->dstate, pp, s0)) return false;
+            // 2. the cascade (or the given start)
+            if (!pp.cascade) {
+                if (launch_select(f, c, w, h, C, u, s0, 1)) return false;
+            } else {
+                for (int l = L - 1; l >= 0; --l) {
+                    cudaGraph_t* b = nullptr;
+                    if (!add_conditional(s0, pp.h_casc[l], cudaGraphCondTypeSwitch, kCascBodies, &b))
+                        return false;
+                    Level& v = lv[l];
+                    S.root = l;
+                    S.s = s1;
+                    bool bok = capture_body(s1, b[kCascSelect], &dg.k_casc[l][kCascSelect], [&] {
+                        return launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s1) == cudaSuccess;
+                    });
+                    if (bok && l == L - 1)
+                        bok = capture_body(s1, b[kCascCoarsest], &dg.k_casc[l][kCascCoarsest], [&] {
+                            return launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s1) == cudaSuccess &&
+                                   S.run_oras(l, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr,
+                                              kCoarseRtol2) == DI_OK;
+                        });
+                    if (bok && l < L - 1)
+                        bok = capture_body(s1, b[kCascProlong], &dg.k_casc[l][kCascProlong], [&] {
+                            Level& cv = lv[l + 1];
+                            return launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr,
+                                                  s1) == cudaSuccess &&
+                                   S.smooth(l, v.u[1], 0, v.u[0], nullptr) == DI_OK;
+                        });
+                    S.s = s0;
+                    if (!bok) return false;
+                }
+            }
+            S.root = 0;
+            // 3. reference norm of the relative-residual rule
+            if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL) {
+                if (launch_residual(nullptr, 1, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
+                                    s0) ||
+                    launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kBnorm2), s0))
+                    return false;
+            }
+            // 4. the V-cycle loop
+            cudaGraph_t* wb = nullptr;
+            if (!add_conditional(s0, pp.h_loop, cudaGraphCondTypeWhile, 1, &wb)) return false;
+            S.s = s1;
+            const bool lok = capture_body(s1, wb[0], &dg.k_body, [&] {
+                Level& v0 = lv[0];
+                unsigned* upd = ctx->upd;
+                int cur = 0, slot = 0;
+                for (int k = 0; k < pre; ++k, ++slot, cur ^= 1)
+                    if (S.smooth(0, v0.u[cur], 0, v0.u[cur ^ 1], upd + slot)) return false;
+                const int slot_cc = slot++;
+                // down-sweep: restriction into level l, then its smoothing
+                for (int l = 1; l < L; ++l) {
+                    cudaGraph_t* b = nullptr;
+                    if (!add_conditional(s1, pp.h_act[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    S.s = s2;
+                    const bool bok = capture_body(s2, b[0], &dg.k_down[l], [&] {
+                        Level& fl = lv[l - 1];
+                        Level& v = lv[l];
+                        int rz;
+                        const float* rhs = S.rhs_of(l - 1, &rz);
+                        if (launch_restrict(fl.u[cur0], rhs, rz, fl.c, fl.w, fl.h, C, v.c, v.r, s2))
+                            return false;
+                        if (l == L - 1)  // one block: the exact coarse solve, from zero
+                            return S.run_oras(l, v.u[0], 1, v.u[1], cfg.coarse_iters, nullptr,
+                                              kCoarseRtol2) == DI_OK;
+                        int cc = 0;
+                        bool zero = true;
+                        for (int k = 0; k < pre; ++k, cc ^= 1, zero = false)
+                            if (S.smooth(l, v.u[cc], zero ? 1 : 0, v.u[cc ^ 1], nullptr)) return false;
+                        if (zero && cudaMemsetAsync(v.u[cc], 0, v.n * C * sizeof(float), s2))
+                            return false;
+                        return true;
+                    });
+                    S.s = s1;
+                    if (!bok) return false;
+                }
+                // up-sweep: post-smoothing of level l, then its correction
+                // prolongated into level l - 1
+                for (int l = L - 1; l >= 1; --l) {
+                    cudaGraph_t* b = nullptr;
+                    if (!add_conditional(s1, pp.h_act[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    S.s = s2;
+                    const bool bok = capture_body(s2, b[0], &dg.k_up[l], [&] {
+                        Level& v = lv[l];
+                        Level& fl = lv[l - 1];
+                        int which = 1;  // the coarsest solve ends in u[1]
+                        if (l < L - 1) {
+                            int cc = cur0;
+                            for (int k = 0; k < post; ++k, cc ^= 1)
+                                if (S.smooth(l, v.u[cc], 0, v.u[cc ^ 1], nullptr)) return false;
+                            which = cc;
+                        }
+                        return launch_prolong(v.u[which], nullptr, fl.c, fl.w, fl.h, C, fl.u[cur0],
+                                              1, l == 1 ? upd + slot_cc : nullptr, s2) ==
+                               cudaSuccess;
+                    });
+                    S.s = s1;
+                    if (!bok) return false;
+                }
+                for (int k = 0; k < post; ++k, ++slot, cur ^= 1)
+                    if (S.smooth(0, v0.u[cur], 0, v0.u[cur ^ 1], upd + slot)) return false;
+                if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
+                    (launch_residual(v0.u[0], 0, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
+                                     s1) ||
+                     launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kNorm2), s1)))
+                    return false;
+                return launch_stop(upd, ctx->dstate, sp, pp.h_loop, s1) == cudaSuccess;
+            });
+            S.s = s0;
+            return lok;
+        };
+        ok = run();
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s0, &out);
+        ok = ok && e == cudaSuccess;
+    }
+    S.s = caller;
+    S.root = 0;
+    // everything left after the bodies took theirs is the fixed part
+    dg.k_pre = launch_count() - k0;
+    add_launches(-dg.k_pre);
+    if (ok) ok = cudaGraphInstantiate(&dg.exec, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        if (dg.exec) cudaGraphExecDestroy(dg.exec);
+        cudaGraphDestroy(g);
+        dg = DecodeGraph();
+        ctx->err[0] = 0;
+        return false;
+    }
+    dg.g = g;
+    dg.valid = true;
+    dg.f = f;
+    dg.c = c;
+    dg.u = u;
+    dg.w = w;
+    dg.h = h;
+    dg.C = C;
+    dg.tol = tol;
+    dg.ws_gen = ctx->ws_gen;
+    return true;
+}
+
+// Fill the statistics from the read-back stop state of a device-driven
+// decode (its stream has completed) and count its kernels.
+di_status finish_device(di_ctx* ctx) {
+    DecodeGraph* dg = ctx->pending;
+    ctx->pending = nullptr;
+    const StopState& hs = *ctx->hstate;
+    const int L = ctx->L;
+    const int Leff = hs.levels_used;
+    std::memset(&ctx->stats, 0, sizeof ctx->stats);
+    ctx->stats.levels = L;
+    ctx->stats.levels_used = Leff;
+    ctx->stats.cycles = hs.cycles;
+    ctx->stats.converged = hs.converged;
+    ctx->stats.est_error = ctx->cfg.stop_rule == DI_STOP_ERROR_ESTIMATE ? hs.est : 0.f;
+    for (int k = 0; k < 4; ++k) ctx->stats.rel_residual[k] = hs.rel[k];
+    ctx->stats.unknowns = (long long)hs.unknowns;
+    if (dg && dg->valid) {
+        long long k = dg->k_pre;  // the empty-mask case runs nothing else
+        if (ctx->cfg.start != DI_START_GIVEN && hs.status != DI_ERR_EMPTY_MASK)
+            for (int l = 0; l < L; ++l) {
+                const int cs = cascade_case(l, L, Leff);
+                if (cs < kCascBodies) k += dg->k_casc[l][cs];
+            }
+        long long per_cycle = dg->k_body;
+        for (int l = 1; l < Leff && l < L; ++l) per_cycle += dg->k_down[l] + dg->k_up[l];
+        add_launches(k + per_cycle * hs.cycles);
+    }
+    if (hs.status == DI_ERR_TIMEOUT) return timeout(ctx);
+    if (hs.status == DI_ERR_EMPTY_MASK) return DI_ERR_EMPTY_MASK;
+    return hs.status == DI_OK ? DI_OK : DI_ERR_NOT_CONVERGED;
+}
+
+// Run a decode through its cached (or newly captured) graph.  Returns false
+// if the graph could not be built (the caller then runs the host-driven
+// loop); otherwise *st is the status (DI_OK while the work is still running
+// when wait is false).
+bool device_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, float* u, int w,
+                   int h, int C, float tol, bool wait, di_status* st) {
+    DecodeGraph* hit = nullptr;
+    DecodeGraph* victim = &ctx->graphs[0];
+    for (auto& dg : ctx->graphs) {
+        if (dg.valid && dg.f == f && dg.c == c && dg.u == u && dg.w == w && dg.h == h &&
+            dg.C == C && dg.tol == tol && dg.ws_gen == ctx->ws_gen) {
+            hit = &dg;
+            break;
+        }
+        if (!dg.valid || dg.used < victim->used) victim = &dg;
+    }
+    if (!hit) {
+        drop_graph(*victim);
+        if (!capture_decode(ctx, S, f, c, u, w, h, C, tol, *victim)) {
+            ctx->device_path_broken = true;
+            return false;
+        }
+        hit = victim;
+    }
+    hit->used = ++ctx->graph_clock;
+    cudaStream_t s = S.s;
+    cudaError_t e = cudaGraphLaunch(hit->exec, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->hstate, ctx->dstate, sizeof(StopState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->done_ev, s);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(ctx, e, "device-driven decode");
+        return true;
+    }
+    ctx->pending = hit;
+    ctx->prof.device_decodes += 1;
+    if (!wait) {
+        *st = DI_OK;
+        return true;
+    }
+    e = cudaEventSynchronize(ctx->done_ev);
+    if (e != cudaSuccess) {
+        ctx->pending = nullptr;
+        *st = cuda_fail(ctx, e, "cudaEventSynchronize");
+        return true;
+    }
+    *st = finish_device(ctx);
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -531,6 +942,10 @@ di_status di_create(const di_config* cfg, int device, di_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dsteps, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->dsteps, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->host, 4096);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dstate, sizeof(StopState));
+    if (e == cudaSuccess) e = cudaMemset(ctx->dstate, 0, sizeof(StopState));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->hstate, sizeof(StopState));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         di_status st = cuda_fail(ctx, e, "di_create");
         di_destroy(ctx);
@@ -552,6 +967,11 @@ void di_destroy(di_ctx* ctx) {
     }
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (int k = 0; k < 3; ++k)
+        if (ctx->cs[k]) cudaStreamDestroy(ctx->cs[k]);
+    if (ctx->dstate) cudaFree(ctx->dstate);
+    if (ctx->hstate) cudaFreeHost(ctx->hstate);
+    if (ctx->done_ev) cudaEventDestroy(ctx->done_ev);
     if (ctx->norm2) cudaFree(ctx->norm2);
     if (ctx->counts) cudaFree(ctx->counts);
     if (ctx->upd) cudaFree(ctx->upd);
@@ -598,14 +1018,34 @@ di_status di_reset_profile(di_ctx* ctx) {
     return DI_OK;
 }
 
-di_status di_get_stats(const di_ctx* ctx, di_stats* out) {
-    if (!ctx || !out) return DI_ERR_INVALID_ARG;
+di_status di_get_stats(const di_ctx* cctx, di_stats* out) {
+    if (!cctx || !out) return DI_ERR_INVALID_ARG;
+    di_ctx* ctx = const_cast<di_ctx*>(cctx);
+    if (ctx->pending) {
+        // the last call was enqueued without waiting: wait for its work and
+        // read its statistics now
+        if (cudaSetDevice(ctx->device) != cudaSuccess ||
+            cudaEventSynchronize(ctx->done_ev) != cudaSuccess) {
+            ctx->pending = nullptr;
+            return DI_ERR_CUDA;
+        }
+        ctx->stats.status = finish_device(ctx);
+    }
     *out = ctx->stats;
     return DI_OK;
 }
 
-di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, int height,
-                     int channels, float tol, float* u, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The decode of di_inpaint / di_inpaint_async.  The device-driven graph runs
+// it when the configuration allows (V-cycle schedule of the reduced FMG,
+// graph replay on, no profiling events, an even number of smoothing steps
+// per cycle, at least two levels); otherwise the host-driven loop below runs
+// it, synchronously.
+di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width, int height,
+                       int channels, float tol, float* u, void* stream, bool wait) {
     if (!ctx || !f || !c || !u || width < 1 || height < 1 || channels < 1 ||
         channels > kMaxChannels || !(tol > 0.f) || !std::isfinite(tol))
         return DI_ERR_INVALID_ARG;
@@ -616,6 +1056,7 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     if (num_levels(width, height, ctx->cfg.block) > kMaxLevels - 1) return DI_ERR_INVALID_ARG;
     std::memset(&ctx->stats, 0, sizeof ctx->stats);
     for (int k = 0; k < 4; ++k) ctx->stats.rel_residual[k] = -1.f;
+    ctx->pending = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DI_CUDA(ctx, cudaSetDevice(ctx->device));
     di_status st = ensure_workspace(ctx, width, height, channels);
@@ -624,6 +1065,16 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     const di_config& cfg = ctx->cfg;
     const int L = ctx->L;
     const int C = channels;
+
+    if (cfg.graph == DI_GRAPH_ON && !cfg.profile && cfg.schedule == DI_SCHED_REDUCED_FMG &&
+        (cfg.pre + cfg.post) % 2 == 0 && L >= 2 && !ctx->device_path_broken) {
+        Sched S{ctx, C, L, s};
+        if (cfg.stop_rule == DI_STOP_ERROR_ESTIMATE && cfg.local_stop > 0.f)
+            S.abs2 = (cfg.local_stop * tol) * (cfg.local_stop * tol);
+        if (device_decode(ctx, S, f, c, u, width, height, C, tol, wait, &st)) return st;
+        // the graph could not be built: the host-driven loop below
+        bind_levels(ctx, f, c, u, width, height, channels);
+    }
 
     // 1. pyramids and unknown counts
     unsigned long long* cnt = ctx->counts;
@@ -830,6 +1281,24 @@ di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, i
     ctx->stats.cycles = cycles;
     ctx->stats.converged = converged ? 1 : 0;
     return converged ? DI_OK : DI_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+di_status di_inpaint(di_ctx* ctx, const float* f, const uint8_t* c, int width, int height,
+                     int channels, float tol, float* u, void* stream) {
+    const di_status st = inpaint_impl(ctx, f, c, width, height, channels, tol, u, stream, true);
+    if (ctx) ctx->stats.status = st;
+    return st;
+}
+
+di_status di_inpaint_async(di_ctx* ctx, const float* f, const uint8_t* c, int width, int height,
+                           int channels, float tol, float* u, void* stream) {
+    const di_status st = inpaint_impl(ctx, f, c, width, height, channels, tol, u, stream, false);
+    if (ctx && !ctx->pending) ctx->stats.status = st;
+    return st;
 }
 
 // ---------------------------------------------------------------------------

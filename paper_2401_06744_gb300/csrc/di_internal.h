@@ -106,6 +106,59 @@ cudaError_t launch_cg_smooth(const float* in, int zero_in, const float* b, int r
                              float* r, float* p, float* q, float* x, double* partials, double* sc,
                              int* step_par, float* out, unsigned* maxupd, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Device-driven decode: the state of the stop test lives on the device, so a
+// whole decode runs as one CUDA graph without host round trips.
+// ---------------------------------------------------------------------------
+
+// Stop-test state of one decode (device memory, read back once at the end).
+struct StopState {
+    int cycles;          // V-cycles run
+    int status;          // di_status of the decode
+    int converged;       // 1 once the stop rule held
+    int levels_used;     // levels down to the first one without unknown pixels
+    float est;           // last error estimate (gray levels)
+    float prevU, prevQ;  // last cycle's update size and decay ratio (< 0: none yet)
+    float rel[kMaxChannels];       // relative residual per channel (relative-residual rule)
+    unsigned long long unknowns;   // unknown pixels on the finest level
+    double bnorm2[kMaxChannels];   // ||b||^2 per channel (relative-residual rule)
+    double norm2[kMaxChannels];    // ||b - A u||^2 per channel of the last cycle
+};
+
+// Stop rule parameters (rule: the DI_STOP_* value of the configuration).
+struct StopParams {
+    int rule, nslots, min_cycles, max_cycles, C;
+    float tol;
+};
+
+// Per-level branch values that the plan kernel gives the graph's conditional
+// nodes: cascade switch bodies (kCascSelect: u = b on the level, the start
+// of the cascade on a fully known level; kCascCoarsest: the single-block
+// solve of the coarsest level; kCascProlong: prolongation from the level
+// below and one smoothing step; kCascSkip: no body) and the "level active"
+// flag of the V-cycle bodies.
+enum { kCascSelect = 0, kCascCoarsest = 1, kCascProlong = 2, kCascBodies = 3, kCascSkip = 7 };
+
+struct PlanParams {
+    int L;                     // levels of the pyramid
+    int cascade;               // 1: the graph holds the cascade switch nodes
+    int max_cycles;
+    unsigned long long n0;     // pixels of the finest level
+    unsigned long long h_act[kMaxLevels];   // IF handles: level l >= 1 takes part in the cycles
+    unsigned long long h_casc[kMaxLevels];  // SWITCH handles of the cascade, per level
+    unsigned long long h_loop;              // WHILE handle of the V-cycle loop
+};
+
+// Levels in use and branch values of the decode from the unknown counts
+// (counts[1 + l]: unknown pixels of level l); initialises *st.
+cudaError_t launch_plan(const unsigned long long* counts, StopState* st, const PlanParams& p,
+                        cudaStream_t s);
+// The stop test after one V-cycle: reads and clears the update slots
+// (upd[0 .. nslots-1]; upd[kMaxUpdSlots] is the timeout flag), updates *st
+// and sets the loop handle to 0 once the decode is done.
+cudaError_t launch_stop(unsigned* upd, StopState* st, const StopParams& p,
+                        unsigned long long h_loop, cudaStream_t s);
+
 // Host-side geometry shared with the kernels.
 inline int axis_blocks(int n, int B, int o) {
     const int s = B - o;

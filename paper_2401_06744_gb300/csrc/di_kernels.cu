@@ -29,6 +29,7 @@
 // every plane pixel has one writer); the combine pass adds them in a fixed
 // order, which keeps the result deterministic without atomics.
 #include "di_internal.h"
+#include "../../include/di.h"
 
 #include <cfloat>
 #include <cstring>
@@ -1872,6 +1873,115 @@ k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restr
     u_out[ch * n + (size_t)y * w + x] = strips[at] + strips[at + side];
 }
 
+// ---------------------------------------------------------------------------
+// Device-driven decode: the plan and the stop test (Section 5.2 stop criterion;
+// the error-estimate rule in gray levels).  One thread each; they steer the
+// conditional nodes of the decode graph.
+// ---------------------------------------------------------------------------
+
+__global__ void k_plan(const unsigned long long* __restrict__ counts, StopState* __restrict__ st,
+                       PlanParams p) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int L = p.L;
+    const unsigned long long unk0 = counts[1];
+    // levels down to the first one without unknown pixels (max pooling keeps
+    // a known pixel known, so every coarser level is fully known too)
+    int Leff = L;
+    for (int l = 1; l < L; ++l)
+        if (counts[1 + l] == 0) { Leff = l; break; }
+    if (unk0 == 0) Leff = 0;
+    st->cycles = 0;
+    st->converged = 0;
+    st->levels_used = Leff;
+    st->est = INFINITY;
+    st->prevU = -1.f;
+    st->prevQ = -1.f;
+    st->unknowns = unk0;
+    for (int k = 0; k < kMaxChannels; ++k) st->rel[k] = -1.f;
+    const bool empty = unk0 == p.n0;
+    st->status = empty ? DI_ERR_EMPTY_MASK : DI_OK;
+    for (int l = 1; l < L; ++l)
+        cudaGraphSetConditional(p.h_act[l], (!empty && l < Leff) ? 1u : 0u);
+    if (p.cascade) {
+        // the cascade starts on the coarsest level (a single-block solve) or
+        // on the first fully known level (u = b there), then prolongs and
+        // smooths level by level; every pixel known: u = f on level 0
+        const int top = Leff == L ? L - 1 : Leff;
+        for (int l = 0; l < L; ++l) {
+            unsigned v = kCascSkip;
+            if (!empty) {
+                if (Leff == 0) v = l == 0 ? kCascSelect : kCascSkip;
+                else if (l == top) v = Leff == L ? kCascCoarsest : kCascSelect;
+                else if (l < top) v = kCascProlong;
+            }
+            cudaGraphSetConditional(p.h_casc[l], v);
+        }
+    }
+    if (Leff == 0 && !empty) st->converged = 1;
+    cudaGraphSetConditional(p.h_loop, (!empty && Leff > 0 && p.max_cycles > 0) ? 1u : 0u);
+}
+
+// The stop test of the host loop, on the device: the same float arithmetic
+// in the same order, so the decisions are identical.
+__global__ void k_stop(unsigned* __restrict__ upd, StopState* __restrict__ st, StopParams p,
+                       cudaGraphConditionalHandle h_loop) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int cycles = st->cycles + 1;
+    st->cycles = cycles;
+    bool stop = false;
+    if (upd[kMaxUpdSlots]) {
+        st->status = DI_ERR_TIMEOUT;
+        stop = true;
+    } else if (p.rule == DI_STOP_ERROR_ESTIMATE) {
+        float U = 0.f;
+        for (int k = 0; k < p.nslots; ++k) U += __uint_as_float(upd[k]);
+        float prevU = st->prevU, prevQ = st->prevQ, est;
+        if (!isfinite(U)) {
+            est = INFINITY;
+            prevU = -1.f;
+            prevQ = -1.f;
+        } else if (prevU > 0.f) {
+            // decay factor: the larger of the last two measured ratios
+            const float qk = __fdiv_rn(U, prevU);
+            const float q = prevQ > qk ? prevQ : qk;
+            prevQ = qk;
+            est = q < 1.f ? __fdiv_rn(__fmul_rn(U, q), __fsub_rn(1.f, q)) : INFINITY;
+        } else {
+            est = U;  // first cycle: no decay measured yet
+        }
+        prevU = U;
+        if (U == 0.f) est = 0.f;
+        st->prevU = prevU;
+        st->prevQ = prevQ;
+        st->est = est;
+        if (cycles >= p.min_cycles && est <= 0.5f * p.tol) {
+            st->converged = 1;
+            stop = true;
+        }
+    } else if (p.rule == DI_STOP_RELATIVE_RESIDUAL) {
+        bool ok = true;
+        for (int k = 0; k < p.C; ++k) {
+            const double b2 = st->bnorm2[k];
+            const double rr = b2 > 0 ? sqrt(st->norm2[k] / b2) : 0.0;
+            st->rel[k] = (float)rr;
+            if (!(rr <= (double)p.tol)) ok = false;
+        }
+        if (cycles >= p.min_cycles && ok) {
+            st->converged = 1;
+            stop = true;
+        }
+    } else if (cycles >= p.max_cycles) {  // fixed number of cycles
+        st->converged = 1;
+        stop = true;
+    }
+    if (!stop && cycles >= p.max_cycles) {
+        st->status = DI_ERR_NOT_CONVERGED;
+        stop = true;
+    }
+    for (int k = 0; k < p.nslots; ++k) upd[k] = 0u;
+    cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+}
+
 // Timing event on s; inside a stream capture it becomes an event record node
 // of the graph (recorded by every replay).
 void record_event(cudaEvent_t e, cudaStream_t s) {
@@ -2336,6 +2446,20 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
         default:
             return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_plan(const unsigned long long* counts, StopState* st, const PlanParams& p,
+                        cudaStream_t s) {
+    k_plan<<<1, 32, 0, s>>>(counts, st, p);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stop(unsigned* upd, StopState* st, const StopParams& p,
+                        unsigned long long h_loop, cudaStream_t s) {
+    k_stop<<<1, 32, 0, s>>>(upd, st, p, (cudaGraphConditionalHandle)h_loop);
+    count();
+    return cudaGetLastError();
 }
 
 }  // namespace di
