@@ -537,6 +537,14 @@ float bits_to_float(unsigned b) {
 // recursion of Sched::vcycle.  Results equal the host-driven loop bit for bit.
 // ---------------------------------------------------------------------------
 
+// Note why the whole-decode graph could not be built (di_last_error); the
+// decode then runs the host-driven loop.
+void capture_error(di_ctx* ctx, const char* step) {
+    const cudaError_t e = cudaGetLastError();
+    std::snprintf(ctx->err, sizeof ctx->err, "device-driven decode unavailable (%s: %s)", step,
+                  cudaGetErrorString(e));
+}
+
 // Add a conditional node after everything captured so far on `s` (which must
 // be capturing) and return its body graphs.
 bool add_conditional(cudaStream_t s, cudaGraphConditionalHandle h,
@@ -590,8 +598,8 @@ double* state_field(di_ctx* ctx, int which) {
 int cascade_case(int l, int L, int Leff) {
     if (Leff == 0) return l == 0 ? kCascSelect : kCascSkip;
     const int top = Leff == L ? L - 1 : Leff;
-    if (l == top) return Leff == L ? kCascCoarsest : kCascSelect;
-    return l < top ? kCascProlong : kCascSkip;
+    if (l == top) return Leff == L ? kCascSolve : kCascSelect;
+    return l < top ? kCascSolve : kCascSkip;
 }
 
 bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, float* u, int w,
@@ -611,15 +619,19 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
     pp.cascade = cfg.start != DI_START_GIVEN;
     pp.max_cycles = cfg.max_cycles;
     pp.n0 = (unsigned long long)w * h;
+    const char* step = "conditional handles";
     bool ok = cudaGraphConditionalHandleCreate(&pp.h_loop, g, 0, cudaGraphCondAssignDefault) ==
               cudaSuccess;
     for (int l = 1; l < L && ok; ++l)
-        ok = cudaGraphConditionalHandleCreate(&pp.h_act[l], g, 0, cudaGraphCondAssignDefault) ==
-             cudaSuccess;
+        ok = cudaGraphConditionalHandleCreate(&pp.h_dn[l], g, 0, cudaGraphCondAssignDefault) ==
+                 cudaSuccess &&
+             cudaGraphConditionalHandleCreate(&pp.h_up[l], g, 0, cudaGraphCondAssignDefault) ==
+                 cudaSuccess;
     for (int l = 0; l < L && ok && pp.cascade; ++l)
         ok = cudaGraphConditionalHandleCreate(&pp.h_casc[l], g, kCascSkip,
                                               cudaGraphCondAssignDefault) == cudaSuccess;
     if (!ok) {
+        capture_error(ctx, step);
         cudaGraphDestroy(g);
         return false;
     }
@@ -644,6 +656,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
         S.s = s0;
         auto run = [&]() -> bool {
             // 1. pyramids with the unknown counts, then the plan
+            step = "pyramid";
             if (cudaMemsetAsync(cnt, 0, (kMaxLevels + 1) * sizeof(unsigned long long), s0) ||
                 cudaMemsetAsync(ctx->upd, 0, (kMaxUpdSlots + 1) * sizeof(unsigned), s0))
                 return false;
@@ -665,22 +678,25 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             } else {
                 for (int l = L - 1; l >= 0; --l) {
                     cudaGraph_t* b = nullptr;
+                    step = "cascade switch node";
                     if (!add_conditional(s0, pp.h_casc[l], cudaGraphCondTypeSwitch, kCascBodies, &b))
                         return false;
                     Level& v = lv[l];
                     S.root = l;
                     S.s = s1;
+                    step = "cascade start body";
                     bool bok = capture_body(s1, b[kCascSelect], &dg.k_casc[l][kCascSelect], [&] {
                         return launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s1) == cudaSuccess;
                     });
+                    if (bok) step = "cascade solve body";
                     if (bok && l == L - 1)
-                        bok = capture_body(s1, b[kCascCoarsest], &dg.k_casc[l][kCascCoarsest], [&] {
+                        bok = capture_body(s1, b[kCascSolve], &dg.k_casc[l][kCascSolve], [&] {
                             return launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s1) == cudaSuccess &&
                                    S.run_oras(l, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr,
                                               kCoarseRtol2) == DI_OK;
                         });
-                    if (bok && l < L - 1)
-                        bok = capture_body(s1, b[kCascProlong], &dg.k_casc[l][kCascProlong], [&] {
+                    else if (bok)
+                        bok = capture_body(s1, b[kCascSolve], &dg.k_casc[l][kCascSolve], [&] {
                             Level& cv = lv[l + 1];
                             return launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr,
                                                   s1) == cudaSuccess &&
@@ -692,6 +708,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             }
             S.root = 0;
             // 3. reference norm of the relative-residual rule
+            step = "reference norm";
             if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL) {
                 if (launch_residual(nullptr, 1, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
                                     s0) ||
@@ -700,7 +717,9 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             }
             // 4. the V-cycle loop
             cudaGraph_t* wb = nullptr;
+            step = "while node";
             if (!add_conditional(s0, pp.h_loop, cudaGraphCondTypeWhile, 1, &wb)) return false;
+            step = "cycle body";
             S.s = s1;
             const bool lok = capture_body(s1, wb[0], &dg.k_body, [&] {
                 Level& v0 = lv[0];
@@ -712,7 +731,9 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
                 // down-sweep: restriction into level l, then its smoothing
                 for (int l = 1; l < L; ++l) {
                     cudaGraph_t* b = nullptr;
-                    if (!add_conditional(s1, pp.h_act[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    step = "down-sweep if node";
+                    if (!add_conditional(s1, pp.h_dn[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    step = "down-sweep body";
                     S.s = s2;
                     const bool bok = capture_body(s2, b[0], &dg.k_down[l], [&] {
                         Level& fl = lv[l - 1];
@@ -739,7 +760,9 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
                 // prolongated into level l - 1
                 for (int l = L - 1; l >= 1; --l) {
                     cudaGraph_t* b = nullptr;
-                    if (!add_conditional(s1, pp.h_act[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    step = "up-sweep if node";
+                    if (!add_conditional(s1, pp.h_up[l], cudaGraphCondTypeIf, 1, &b)) return false;
+                    step = "up-sweep body";
                     S.s = s2;
                     const bool bok = capture_body(s2, b[0], &dg.k_up[l], [&] {
                         Level& v = lv[l];
@@ -758,6 +781,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
                     S.s = s1;
                     if (!bok) return false;
                 }
+                step = "cycle body";
                 for (int k = 0; k < post; ++k, ++slot, cur ^= 1)
                     if (S.smooth(0, v0.u[cur], 0, v0.u[cur ^ 1], upd + slot)) return false;
                 if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
@@ -771,22 +795,27 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             return lok;
         };
         ok = run();
+        if (ok) step = "end of capture";
         cudaGraph_t out = nullptr;
         const cudaError_t e = cudaStreamEndCapture(s0, &out);
         ok = ok && e == cudaSuccess;
+    } else {
+        step = "begin capture";
     }
     S.s = caller;
     S.root = 0;
     // everything left after the bodies took theirs is the fixed part
     dg.k_pre = launch_count() - k0;
     add_launches(-dg.k_pre);
-    if (ok) ok = cudaGraphInstantiate(&dg.exec, g, 0) == cudaSuccess;
+    if (ok) {
+        step = "instantiate";
+        ok = cudaGraphInstantiate(&dg.exec, g, 0) == cudaSuccess;
+    }
     if (!ok) {
-        cudaGetLastError();
+        capture_error(ctx, step);
         if (dg.exec) cudaGraphExecDestroy(dg.exec);
         cudaGraphDestroy(g);
         dg = DecodeGraph();
-        ctx->err[0] = 0;
         return false;
     }
     dg.g = g;

@@ -133,18 +133,20 @@ struct StopParams {
 
 // Per-level branch values that the plan kernel gives the graph's conditional
 // nodes: cascade switch bodies (kCascSelect: u = b on the level, the start
-// of the cascade on a fully known level; kCascCoarsest: the single-block
-// solve of the coarsest level; kCascProlong: prolongation from the level
-// below and one smoothing step; kCascSkip: no body) and the "level active"
-// flag of the V-cycle bodies.
-enum { kCascSelect = 0, kCascCoarsest = 1, kCascProlong = 2, kCascBodies = 3, kCascSkip = 7 };
+// of the cascade on a fully known level; kCascSolve: on the coarsest level
+// the single-block solve, on the others prolongation from the level below
+// and one smoothing step; kCascSkip: no body) and the "level active" flags
+// of the V-cycle bodies (one handle per conditional node: down-sweep and
+// up-sweep bodies of a level have their own).
+enum { kCascSelect = 0, kCascSolve = 1, kCascBodies = 2, kCascSkip = 7 };
 
 struct PlanParams {
     int L;                     // levels of the pyramid
     int cascade;               // 1: the graph holds the cascade switch nodes
     int max_cycles;
     unsigned long long n0;     // pixels of the finest level
-    unsigned long long h_act[kMaxLevels];   // IF handles: level l >= 1 takes part in the cycles
+    unsigned long long h_dn[kMaxLevels];    // IF handles, down-sweep body of level l >= 1
+    unsigned long long h_up[kMaxLevels];    // IF handles, up-sweep body of level l >= 1
     unsigned long long h_casc[kMaxLevels];  // SWITCH handles of the cascade, per level
     unsigned long long h_loop;              // WHILE handle of the V-cycle loop
 };

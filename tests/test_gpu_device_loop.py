@@ -42,7 +42,8 @@ def _decode(di, f, c, tol, **cfg):
         pr = ctx.profile()
         # graph on: the decode ran as one device-driven graph; off: host loop
         device = cfg.get("graph", di.GRAPH_ON) == di.GRAPH_ON
-        assert pr["device_decodes"] == (1 if device else 0), pr
+        why = di.load().di_last_error(ctx._h).decode()
+        assert pr["device_decodes"] == (1 if device else 0), (pr, why)
         return u.cpu().numpy(), st, ctx.stats(), pr["launches"]
 
 
