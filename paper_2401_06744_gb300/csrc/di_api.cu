@@ -41,9 +41,9 @@ struct Level {
 
 // One whole decode as a CUDA graph (pyramid, plan, cascade, V-cycle loop with
 // the stop test), valid for the buffers and sizes it was captured for.  The
-// level structure that depends on the mask (levels in use, the cascade's
-// start) is steered on the device by conditional nodes, so the graph needs no
-// host round trip.  Kernel counts per body feed the launch counter.
+// number of levels in use, which depends on the mask, selects a body of the
+// graph on the device, so the graph needs no host round trip.  Kernel counts
+// per body feed the launch counter.
 struct DecodeGraph {
     bool valid = false;
     const float* f = nullptr;
@@ -54,9 +54,9 @@ struct DecodeGraph {
     unsigned long long ws_gen = 0;
     cudaGraph_t g = nullptr;
     cudaGraphExec_t exec = nullptr;
-    long long k_pre = 0, k_body = 0;
-    long long k_casc[kMaxLevels][kCascBodies] = {};
-    long long k_down[kMaxLevels] = {}, k_up[kMaxLevels] = {};
+    long long k_pre = 0;                    // kernels outside the switch bodies
+    long long k_sel[kMaxLevels + 1] = {};   // kernels of switch body v outside its loop
+    long long k_cycle[kMaxLevels + 1] = {}; // kernels of one cycle of body v
     unsigned long long used = 0;
 };
 
@@ -523,18 +523,14 @@ float bits_to_float(unsigned b) {
 //
 // The whole decode of one image is captured once (per buffers, size and
 // tolerance) into a CUDA graph and replayed: the pyramid with the unknown
-// counts, the plan kernel, the cascade and a WHILE node around the V-cycle
-// whose last kernel is the stop test.  What depends on the mask is decided on
-// the device: the plan kernel sets one IF node per coarse level (the level
-// takes part in the cycles iff it has unknown pixels, as the host-driven
-// recursion stops above the first fully known level) and one SWITCH node per
-// level of the cascade (its start on the coarsest or the first fully known
-// level, then prolongation and smoothing).  The V-cycle is written flat: the
-// down-sweep bodies (restriction into level l, then its pre-smoothing or the
-// coarsest solve) and the up-sweep bodies (post-smoothing of level l, then
-// prolongation of its correction) run under level l's IF node; because a
-// fully known level has only fully known levels below it, this is the
-// recursion of Sched::vcycle.  Results equal the host-driven loop bit for bit.
+// counts, the plan kernel, then one SWITCH node over the number of levels in
+// use (the levels down to the first one without unknown pixels, as the
+// host-driven loop finds them after the pyramid).  Body v holds the cascade
+// for v levels and a WHILE node whose body is one V-cycle recursing through v
+// levels followed by the stop test (k_stop, which ends the loop).  What
+// depends on the mask is thus decided on the device with one conditional node
+// per decode and one loop iteration per cycle, and the graph needs no host
+// round trip.  Results equal the host-driven loop bit for bit.
 // ---------------------------------------------------------------------------
 
 // Note why the whole-decode graph could not be built (di_last_error); the
@@ -594,12 +590,36 @@ double* state_field(di_ctx* ctx, int which) {
         base + (which == kBnorm2 ? offsetof(StopState, bnorm2) : offsetof(StopState, norm2)));
 }
 
-// Value of the cascade SWITCH of level l (mirror of the plan kernel).
-int cascade_case(int l, int L, int Leff) {
-    if (Leff == 0) return l == 0 ? kCascSelect : kCascSkip;
-    const int top = Leff == L ? L - 1 : Leff;
-    if (l == top) return Leff == L ? kCascSolve : kCascSelect;
-    return l < top ? kCascSolve : kCascSkip;
+// The cascade of the reduced FMG for `Leff` levels in use (Leff >= 1), on
+// S.s: the start on the coarsest level (a single-block solve) or on the first
+// fully known level (u = b there), then prolongation and one smoothing step
+// per level up to the finest.  The host-driven loop runs the same sequence.
+bool capture_cascade(di_ctx* ctx, Sched& S, int Leff) {
+    const di_config& cfg = ctx->cfg;
+    const int L = ctx->L, C = S.C;
+    Level* lv = ctx->lv;
+    int top;
+    if (Leff == L) {
+        top = L - 1;
+        Level& v = lv[top];
+        S.root = top;
+        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[1], S.s)) return false;
+        if (S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2))
+            return false;
+    } else {
+        top = Leff;
+        Level& v = lv[top];
+        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[0], S.s)) return false;
+    }
+    for (int l = top - 1; l >= 0; --l) {
+        Level& v = lv[l];
+        Level& cv = lv[l + 1];
+        S.root = l;
+        if (launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, S.s)) return false;
+        if (S.smooth(l, v.u[1], 0, v.u[0], nullptr)) return false;
+    }
+    S.root = 0;
+    return true;
 }
 
 bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, float* u, int w,
@@ -612,24 +632,23 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
     cudaStream_t s0 = ctx->cs[0], s1 = ctx->cs[1], s2 = ctx->cs[2];
     cudaStream_t caller = S.s;
     cudaGraph_t g = nullptr;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return false;
+    const char* step = "graph";
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        capture_error(ctx, step);
+        return false;
+    }
     PlanParams pp;
     std::memset(&pp, 0, sizeof pp);
     pp.L = L;
-    pp.cascade = cfg.start != DI_START_GIVEN;
     pp.max_cycles = cfg.max_cycles;
     pp.n0 = (unsigned long long)w * h;
-    const char* step = "conditional handles";
-    bool ok = cudaGraphConditionalHandleCreate(&pp.h_loop, g, 0, cudaGraphCondAssignDefault) ==
-              cudaSuccess;
-    for (int l = 1; l < L && ok; ++l)
-        ok = cudaGraphConditionalHandleCreate(&pp.h_dn[l], g, 0, cudaGraphCondAssignDefault) ==
-                 cudaSuccess &&
-             cudaGraphConditionalHandleCreate(&pp.h_up[l], g, 0, cudaGraphCondAssignDefault) ==
-                 cudaSuccess;
-    for (int l = 0; l < L && ok && pp.cascade; ++l)
-        ok = cudaGraphConditionalHandleCreate(&pp.h_casc[l], g, kCascSkip,
-                                              cudaGraphCondAssignDefault) == cudaSuccess;
+    const bool cascade = cfg.start != DI_START_GIVEN;
+    step = "conditional handles";
+    bool ok = cudaGraphConditionalHandleCreate(&pp.h_sel, g, kSelSkip,
+                                               cudaGraphCondAssignDefault) == cudaSuccess;
+    for (int v = 1; v <= L && ok; ++v)
+        ok = cudaGraphConditionalHandleCreate(&pp.h_loop[v], g, 0, cudaGraphCondAssignDefault) ==
+             cudaSuccess;
     if (!ok) {
         capture_error(ctx, step);
         cudaGraphDestroy(g);
@@ -646,8 +665,6 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
     sp.tol = tol;
     Level* lv = ctx->lv;
     int nparts = 0;
-    const int pre = cfg.pre, post = cfg.post;
-    const int cur0 = pre & 1;  // buffer of a level's iterate after its pre-smoothing
     unsigned long long* cnt = ctx->counts;
 
     ok = cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) ==
@@ -665,134 +682,62 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
                 Level& fl = lv[l - 1];
                 Level& cl = lv[l];
                 if (launch_mask_down(fl.c, fl.w, fl.h, const_cast<uint8_t*>(cl.c), s0)) return false;
-                if (pp.cascade &&
+                if (cascade &&
                     launch_values_down(fl.c, fl.b, fl.w, fl.h, C, cl.c, const_cast<float*>(cl.b),
                                        cfg.downsample == 0 ? 1 : 0, s0))
                     return false;
                 if (launch_pack_mask(cl.c, cl.w, cl.h, cl.mbits, cnt + 1 + l, s0)) return false;
             }
             if (launch_plan(cnt, ctx->dstate, pp, s0)) return false;
-            // 2. the cascade (or the given start)
-            if (!pp.cascade) {
-                if (launch_select(f, c, w, h, C, u, s0, 1)) return false;
-            } else {
-                for (int l = L - 1; l >= 0; --l) {
-                    cudaGraph_t* b = nullptr;
-                    step = "cascade switch node";
-                    if (!add_conditional(s0, pp.h_casc[l], cudaGraphCondTypeSwitch, kCascBodies, &b))
-                        return false;
-                    Level& v = lv[l];
-                    S.root = l;
-                    S.s = s1;
-                    step = "cascade start body";
-                    bool bok = capture_body(s1, b[kCascSelect], &dg.k_casc[l][kCascSelect], [&] {
-                        return launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s1) == cudaSuccess;
-                    });
-                    if (bok) step = "cascade solve body";
-                    if (bok && l == L - 1)
-                        bok = capture_body(s1, b[kCascSolve], &dg.k_casc[l][kCascSolve], [&] {
-                            return launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s1) == cudaSuccess &&
-                                   S.run_oras(l, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr,
-                                              kCoarseRtol2) == DI_OK;
-                        });
-                    else if (bok)
-                        bok = capture_body(s1, b[kCascSolve], &dg.k_casc[l][kCascSolve], [&] {
-                            Level& cv = lv[l + 1];
-                            return launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr,
-                                                  s1) == cudaSuccess &&
-                                   S.smooth(l, v.u[1], 0, v.u[0], nullptr) == DI_OK;
-                        });
-                    S.s = s0;
-                    if (!bok) return false;
-                }
-            }
-            S.root = 0;
-            // 3. reference norm of the relative-residual rule
+            // 2. the given start, and the reference norm of the relative-residual rule
+            if (!cascade && launch_select(f, c, w, h, C, u, s0, 1)) return false;
             step = "reference norm";
-            if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL) {
-                if (launch_residual(nullptr, 1, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
-                                    s0) ||
-                    launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kBnorm2), s0))
-                    return false;
-            }
-            // 4. the V-cycle loop
-            cudaGraph_t* wb = nullptr;
-            step = "while node";
-            if (!add_conditional(s0, pp.h_loop, cudaGraphCondTypeWhile, 1, &wb)) return false;
-            step = "cycle body";
+            if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
+                (launch_residual(nullptr, 1, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
+                                 s0) ||
+                 launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kBnorm2), s0)))
+                return false;
+            // 3. one body per number of levels in use: the cascade, then the
+            // V-cycle loop recursing through those levels
+            cudaGraph_t* b = nullptr;
+            step = "switch node";
+            if (!add_conditional(s0, pp.h_sel, cudaGraphCondTypeSwitch, L + 1, &b)) return false;
             S.s = s1;
-            const bool lok = capture_body(s1, wb[0], &dg.k_body, [&] {
-                Level& v0 = lv[0];
-                unsigned* upd = ctx->upd;
-                int cur = 0, slot = 0;
-                for (int k = 0; k < pre; ++k, ++slot, cur ^= 1)
-                    if (S.smooth(0, v0.u[cur], 0, v0.u[cur ^ 1], upd + slot)) return false;
-                const int slot_cc = slot++;
-                // down-sweep: restriction into level l, then its smoothing
-                for (int l = 1; l < L; ++l) {
-                    cudaGraph_t* b = nullptr;
-                    step = "down-sweep if node";
-                    if (!add_conditional(s1, pp.h_dn[l], cudaGraphCondTypeIf, 1, &b)) return false;
-                    step = "down-sweep body";
+            step = "all-known body";
+            if (!capture_body(s1, b[0], &dg.k_sel[0], [&] {
+                    return launch_select(f, c, w, h, C, u, s1) == cudaSuccess;
+                }))
+                return false;
+            for (int v = 1; v <= L; ++v) {
+                step = "level body";
+                const bool bok = capture_body(s1, b[v], &dg.k_sel[v], [&] {
+                    S.Leff = v;
+                    if (cascade && !capture_cascade(ctx, S, v)) return false;
+                    cudaGraph_t* wb = nullptr;
+                    step = "while node";
+                    if (!add_conditional(s1, pp.h_loop[v], cudaGraphCondTypeWhile, 1, &wb))
+                        return false;
+                    step = "cycle body";
                     S.s = s2;
-                    const bool bok = capture_body(s2, b[0], &dg.k_down[l], [&] {
-                        Level& fl = lv[l - 1];
-                        Level& v = lv[l];
-                        int rz;
-                        const float* rhs = S.rhs_of(l - 1, &rz);
-                        if (launch_restrict(fl.u[cur0], rhs, rz, fl.c, fl.w, fl.h, C, v.c, v.r, s2))
+                    const bool cok = capture_body(s2, wb[0], &dg.k_cycle[v], [&] {
+                        int which = -1;
+                        if (S.vcycle(0, false, &which, ctx->upd) || which != 0) return false;
+                        if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
+                            (launch_residual(lv[0].u[0], 0, f, 1, c, w, h, C, nullptr,
+                                             ctx->partials, &nparts, s2) ||
+                             launch_reduce_partials(ctx->partials, nparts, C,
+                                                    state_field(ctx, kNorm2), s2)))
                             return false;
-                        if (l == L - 1)  // one block: the exact coarse solve, from zero
-                            return S.run_oras(l, v.u[0], 1, v.u[1], cfg.coarse_iters, nullptr,
-                                              kCoarseRtol2) == DI_OK;
-                        int cc = 0;
-                        bool zero = true;
-                        for (int k = 0; k < pre; ++k, cc ^= 1, zero = false)
-                            if (S.smooth(l, v.u[cc], zero ? 1 : 0, v.u[cc ^ 1], nullptr)) return false;
-                        if (zero && cudaMemsetAsync(v.u[cc], 0, v.n * C * sizeof(float), s2))
-                            return false;
-                        return true;
-                    });
-                    S.s = s1;
-                    if (!bok) return false;
-                }
-                // up-sweep: post-smoothing of level l, then its correction
-                // prolongated into level l - 1
-                for (int l = L - 1; l >= 1; --l) {
-                    cudaGraph_t* b = nullptr;
-                    step = "up-sweep if node";
-                    if (!add_conditional(s1, pp.h_up[l], cudaGraphCondTypeIf, 1, &b)) return false;
-                    step = "up-sweep body";
-                    S.s = s2;
-                    const bool bok = capture_body(s2, b[0], &dg.k_up[l], [&] {
-                        Level& v = lv[l];
-                        Level& fl = lv[l - 1];
-                        int which = 1;  // the coarsest solve ends in u[1]
-                        if (l < L - 1) {
-                            int cc = cur0;
-                            for (int k = 0; k < post; ++k, cc ^= 1)
-                                if (S.smooth(l, v.u[cc], 0, v.u[cc ^ 1], nullptr)) return false;
-                            which = cc;
-                        }
-                        return launch_prolong(v.u[which], nullptr, fl.c, fl.w, fl.h, C, fl.u[cur0],
-                                              1, l == 1 ? upd + slot_cc : nullptr, s2) ==
+                        return launch_stop(ctx->upd, ctx->dstate, sp, pp.h_loop[v], s2) ==
                                cudaSuccess;
                     });
                     S.s = s1;
-                    if (!bok) return false;
-                }
-                step = "cycle body";
-                for (int k = 0; k < post; ++k, ++slot, cur ^= 1)
-                    if (S.smooth(0, v0.u[cur], 0, v0.u[cur ^ 1], upd + slot)) return false;
-                if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
-                    (launch_residual(v0.u[0], 0, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
-                                     s1) ||
-                     launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kNorm2), s1)))
-                    return false;
-                return launch_stop(upd, ctx->dstate, sp, pp.h_loop, s1) == cudaSuccess;
-            });
+                    return cok;
+                });
+                if (!bok) return false;
+            }
             S.s = s0;
-            return lok;
+            return true;
         };
         ok = run();
         if (ok) step = "end of capture";
@@ -804,6 +749,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
     }
     S.s = caller;
     S.root = 0;
+    S.Leff = L;
     // everything left after the bodies took theirs is the fixed part
     dg.k_pre = launch_count() - k0;
     add_launches(-dg.k_pre);
@@ -849,14 +795,9 @@ di_status finish_device(di_ctx* ctx) {
     ctx->stats.unknowns = (long long)hs.unknowns;
     if (dg && dg->valid) {
         long long k = dg->k_pre;  // the empty-mask case runs nothing else
-        if (ctx->cfg.start != DI_START_GIVEN && hs.status != DI_ERR_EMPTY_MASK)
-            for (int l = 0; l < L; ++l) {
-                const int cs = cascade_case(l, L, Leff);
-                if (cs < kCascBodies) k += dg->k_casc[l][cs];
-            }
-        long long per_cycle = dg->k_body;
-        for (int l = 1; l < Leff && l < L; ++l) per_cycle += dg->k_down[l] + dg->k_up[l];
-        add_launches(k + per_cycle * hs.cycles);
+        if (hs.status != DI_ERR_EMPTY_MASK && Leff >= 0 && Leff <= L)
+            k += dg->k_sel[Leff] + dg->k_cycle[Leff] * hs.cycles;
+        add_launches(k);
     }
     if (hs.status == DI_ERR_TIMEOUT) return timeout(ctx);
     if (hs.status == DI_ERR_EMPTY_MASK) return DI_ERR_EMPTY_MASK;

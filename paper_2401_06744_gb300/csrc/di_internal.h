@@ -131,24 +131,18 @@ struct StopParams {
     float tol;
 };
 
-// Per-level branch values that the plan kernel gives the graph's conditional
-// nodes: cascade switch bodies (kCascSelect: u = b on the level, the start
-// of the cascade on a fully known level; kCascSolve: on the coarsest level
-// the single-block solve, on the others prolongation from the level below
-// and one smoothing step; kCascSkip: no body) and the "level active" flags
-// of the V-cycle bodies (one handle per conditional node: down-sweep and
-// up-sweep bodies of a level have their own).
-enum { kCascSelect = 0, kCascSolve = 1, kCascBodies = 2, kCascSkip = 7 };
+// Conditional handles of the decode graph.  h_sel picks the body for the
+// number of levels in use (0: every pixel known, u = f; v >= 1: the cascade
+// and the V-cycle loop recursing through v levels; kSelSkip: the empty mask,
+// no body); h_loop[v] is the WHILE handle of body v's V-cycle loop.
+constexpr unsigned kSelSkip = 0xffffu;
 
 struct PlanParams {
     int L;                     // levels of the pyramid
-    int cascade;               // 1: the graph holds the cascade switch nodes
     int max_cycles;
     unsigned long long n0;     // pixels of the finest level
-    unsigned long long h_dn[kMaxLevels];    // IF handles, down-sweep body of level l >= 1
-    unsigned long long h_up[kMaxLevels];    // IF handles, up-sweep body of level l >= 1
-    unsigned long long h_casc[kMaxLevels];  // SWITCH handles of the cascade, per level
-    unsigned long long h_loop;              // WHILE handle of the V-cycle loop
+    unsigned long long h_sel;                  // SWITCH over the levels in use
+    unsigned long long h_loop[kMaxLevels + 1]; // WHILE handles, per body
 };
 
 // Levels in use and branch values of the decode from the unknown counts

@@ -1489,402 +1489,6 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 }
 
 
-// The same ORAS iteration with two adjacent columns per thread: thread
-// (wi, lane) holds block rows 16wi + 8rg .. 16wi + 8rg + 7 (rg = lane / 16) of
-// columns 2cp and 2cp + 1 (cp = lane % 16), every CG vector as 8 packed pairs,
-// one pair per row.  A horizontal neighbour is then the other half of the
-// pair or one 32-bit lane shuffle (within the 16 lanes of a row group), the
-// vertical neighbours are the neighbouring pairs, and the row groups meet
-// through one 64-bit exchange of lanes l and l ^ 16 (inside a warp) or the
-// shared seam row (between the warps).  The residual reads each tile row once
-// per column pair, and the weight-1 output is one 8-byte store per row.
-// Arithmetic, barriers and the local CG are those of k_oras_2w.
-__global__ void __launch_bounds__(64, 8)
-k_oras_2c(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
-          int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
-          int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
-          float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
-          const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
-          int use_tma, unsigned* __restrict__ errflag,
-          unsigned long long* __restrict__ step_count) {
-    constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
-    constexpr int TILE = Smem2W::USTRIDE;
-    extern __shared__ float smem_raw[];
-    float* const smem = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-    float* const s_u = smem;                     // [2][USTRIDE]
-    float* const s_wy = smem + Smem2W::WY;       // [B]
-    float* const s_b = smem + Smem2W::RHS;       // [2][BSTRIDE] if rhs_zero == 0
-    __shared__ float s_red1[2], s_red2[2];
-    __shared__ f2 s_seam[2][16];                 // seam row of r per warp (pairs)
-    __shared__ __align__(8) unsigned long long s_bar[2];
-
-    const int t = threadIdx.x;
-    const int lane = t & 31, wi = t >> 5;
-    const int cp = lane & 15, rg = lane >> 4;
-    const int c0 = 2 * cp;              // first of the thread's two block columns
-    const int ry0 = 16 * wi + 8 * rg;   // first of its eight block rows
-    // the lanes at the warp seam (block rows 15 | 16): warp 0's second row
-    // group (its row 7) and warp 1's first (its row 0)
-    const bool seam = wi == 0 ? rg == 1 : rg == 0;
-    const int s = B - o;
-    const size_t n = (size_t)w * h;
-    const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
-    const int nblk = nbx * nby;
-    auto next_task = [&](int& blk, int& ch) {
-        if (chan_inner) {
-            if (++ch == C) { ch = 0; blk += (int)gridDim.x; }
-        } else {
-            const int tt = blk * C + ch + (int)gridDim.x;
-            blk = tt / C;
-            ch = tt - blk * C;
-        }
-        return blk < nblk;
-    };
-    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
-    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
-        const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
-        if (use_tma) {
-            if (t == 0) {
-                const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[bs]);
-                const unsigned bytes = (zero_in ? 0u : (unsigned)Smem2W::TMA_U_BYTES) +
-                                       (rhs_zero ? 0u : (unsigned)Smem2W::TMA_B_BYTES);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                             :: "r"(bar), "r"(bytes) : "memory");
-                if (!zero_in)
-                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_u + bs * TILE), &tm_u,
-                                (px0 - 1) & ~3, py0 - 1, ch, bar);
-                if (!rhs_zero)
-                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_b + bs * Smem2W::BSTRIDE),
-                                &tm_b, px0 & ~3, py0, ch, bar);
-            }
-        } else if (!zero_in) {
-            const float* src = u_in + ch * n;
-            float* dst = s_u + bs * TILE;
-            const int gxa = px0 - 1 + lane, gxb = gxa + 32;
-            const bool oka = gxa >= 0 && gxa < w;
-            const bool okb = lane < TH - 32 && gxb < w;
-#pragma unroll 2
-            for (int ty = wi; ty < TH; ty += 2) {
-                const int gy = py0 - 1 + ty;
-                const bool rok = gy >= 0 && gy < h;
-                const float* row = src + (ptrdiff_t)gy * w;
-                cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
-                if (lane < TH - 32)
-                    cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
-            }
-        }
-        if (!use_tma && !rhs_zero) {
-            const float* src = rhs + ch * n;
-            float* dst = s_b + bs * Smem2W::BSTRIDE;
-            const int gx = px0 + lane;
-#pragma unroll 4
-            for (int ly = wi; ly < B; ly += 2) {
-                const int gy = py0 + ly;
-                const bool ok = gx < w && gy < h;
-                cp_async4(dst + ly * PB + lane, ok ? src + (size_t)gy * w + gx : src, ok);
-            }
-        }
-        if (!use_tma) cp_async_commit();
-        if (blk != have_blk && lane < 16) {
-            // lane l < 16 of warp wi: mask word of block row 16 wi + l
-            const int gy = py0 + 16 * wi + lane;
-            if (gy < h) {
-                const uint32_t* row = mbits + (size_t)gy * wpr + (px0 >> 5);
-                nlo = __ldg(row);
-                nhi = __ldg(row + 1);
-            } else {
-                nlo = nhi = 0xffffffffu;
-            }
-        }
-    };
-
-    int blk = chan_inner ? (int)blockIdx.x : (int)blockIdx.x / C;
-    int ch = chan_inner ? 0 : (int)blockIdx.x - blk * C;
-    if (blk >= nblk) return;  // block-uniform
-    if (use_tma) {
-        if (t == 0) {
-            for (int b = 0; b < 2; ++b)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
-                             :: "r"((unsigned)__cvta_generic_to_shared(&s_bar[b])) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        // no thread may probe a barrier before it is initialised
-        __syncthreads();
-    }
-    unsigned phase = 0;
-    prefetch(blk, ch, 0, -1);
-    int buf = 0, cur_blk = -1;
-    f2 ndg[NP], keep[NP];
-    f2 ml2 = 0ull, mr2 = 0ull;  // (left half, 1) / (1, right half) factors of the lane shuffles
-    float wx0 = 0.f, wx1 = 0.f, dh0 = 0.f, dh1 = 0.f;
-    int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
-    uint32_t rows_w = 0;  // bit ly: row ly of the block is in the image with weight > 0
-    float vmax = 0.f;
-    unsigned nsteps = 0;
-
-    for (;;) {
-        if (use_tma) {
-            const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[buf]);
-            bool ok = mbar_wait(bar, (phase >> buf) & 1u);
-            phase ^= 1u << buf;
-            if (__syncthreads_or(!ok)) {
-                if (!ok) mbar_wait(bar, ((phase >> buf) & 1u) ^ 1u);
-                if (t == 0 && errflag) atomicExch(errflag, 1u);
-                return;
-            }
-        } else {
-            cp_async_wait_all();
-            __syncthreads();
-        }
-        const uint32_t mlo = nlo, mhi = nhi;
-        int nb2 = blk, nc2 = ch;
-        const bool more = next_task(nb2, nc2);
-        if (more) prefetch(nb2, nc2, buf ^ 1, blk);
-
-        if (blk != cur_blk) {
-            cur_blk = blk;
-            kx = blk % nbx;
-            ky = blk / nbx;
-            x0 = kx * s;
-            y0 = ky * s;
-            const int bw = min(B, w - x0);
-            bh = min(B, h - y0);
-            const uint32_t rowm = __funnelshift_r(mlo, mhi, x0 & 31);  // lane < 16: row 16wi+lane
-            uint32_t mb = 0;  // bit 2k + e: row ry0 + k, column c0 + e known (or outside)
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const uint32_t v = __shfl_sync(kFull, rowm, 8 * rg + k);
-                mb |= ((v >> c0) & 3u) << (2 * k);
-            }
-            float hc[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int col = c0 + e, gx = x0 + col;
-                hc[e] = (col > 0 ? 1.f : (gx > 0 ? alpha : 0.f)) +
-                        (col + 1 < bw ? 1.f : (gx < w - 1 ? alpha : 0.f));
-            }
-            dh0 = (float)((x0 + c0 > 0) + (x0 + c0 < w - 1));
-            dh1 = (float)((x0 + c0 + 1 > 0) + (x0 + c0 + 1 < w - 1));
-            ml2 = pk(cp > 0 ? 1.f : 0.f, 1.f);
-            mr2 = pk(1.f, cp < 15 ? 1.f : 0.f);
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const int ly = ry0 + k, gy = y0 + ly;
-                const float vc = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
-                                 (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
-                ndg[k] = pk(-(hc[0] + vc), -(hc[1] + vc));
-                keep[k] = pk(((mb >> (2 * k)) & 1u) ? 0.f : 1.f,
-                             ((mb >> (2 * k + 1)) & 1u) ? 0.f : 1.f);
-            }
-            wx0 = ramp_weight(c0, kx, nbx, s, o, inv_o1);
-            wx1 = ramp_weight(c0 + 1, kx, nbx, s, o, inv_o1);
-            const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);  // row lane
-            if (t < B) s_wy[t] = wyl;
-            rows_w = __ballot_sync(kFull, wyl > 0.f && lane < bh);
-        }
-
-        // TMA tiles start at the 4-aligned column below the halo column
-        const int du = use_tma ? ((x0 - 1) & 3) : 0;
-        const int db = use_tma ? (x0 & 3) : 0;
-        const float* tu = s_u + buf * TILE + du;
-        const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
-
-        f2 x[NP], r[NP], p[NP], q[NP];
-        f2 acc0 = 0ull, acc1 = 0ull;
-        // r = b - A u on the block (0 on the mask), the stencil from the tile:
-        // each tile row is read once (its four columns c0 - 1 .. c0 + 2)
-        auto residual = [&](auto interior, auto rhs0) {
-            const float* tr = tu + ry0 * P + c0;  // tile row ry0 (block row ry0 - 1), column c0 - 1
-            float ua0 = 0.f, ua1 = 0.f;           // the row above: its two centres
-            if (!zero_in) { ua0 = tr[1]; ua1 = tr[2]; }
-            float uc0 = 0.f, uc1 = 0.f, ul = 0.f, ur = 0.f;
-            if (!zero_in) { ul = tr[P]; uc0 = tr[P + 1]; uc1 = tr[P + 2]; ur = tr[P + 3]; }
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const int ly = ry0 + k, gy = y0 + ly;
-                float v0 = 0.f, v1 = 0.f;
-                if (!decltype(rhs0)::value) {
-                    v0 = tb[ly * PB + c0];
-                    v1 = tb[ly * PB + c0 + 1];
-                }
-                float nl = 0.f, n0 = 0.f, n1 = 0.f, nr = 0.f;  // the row below
-                if (!zero_in) {
-                    const float* tn = tr + (k + 2) * P;
-                    nl = tn[0]; n0 = tn[1]; n1 = tn[2]; nr = tn[3];
-                    const float dv = decltype(interior)::value
-                                         ? 2.f : (float)((gy > 0) + (gy < h - 1));
-                    v0 -= (dh0 + dv) * uc0 - (ua0 + n0 + ul + uc1);
-                    v1 -= (dh1 + dv) * uc1 - (ua1 + n1 + uc0 + ur);
-                }
-                r[k] = mul2(pk(v0, v1), keep[k]);
-                p[k] = r[k];
-                x[k] = 0ull;
-                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
-                else acc0 = fma2(r[k], r[k], acc0);
-                ua0 = uc0; ua1 = uc1;
-                ul = nl; uc0 = n0; uc1 = n1; ur = nr;
-            }
-        };
-        if (y0 > 0 && y0 + B < h) {
-            if (rhs_zero) residual(std::true_type{}, std::true_type{});
-            else residual(std::true_type{}, std::false_type{});
-        } else {
-            if (rhs_zero) residual(std::false_type{}, std::true_type{});
-            else residual(std::false_type{}, std::false_type{});
-        }
-        acc0 = add2(acc0, acc1);
-        // seam rows: warp 0 publishes block row 15 (its rg 1, pair 7), warp 1
-        // block row 16 (its rg 0, pair 0)
-        if (seam) s_seam[wi][cp] = wi == 0 ? r[NP - 1] : r[0];
-        float part = warp_sum(lo2(acc0) + hi2(acc0));
-        if (lane == 0) s_red2[wi] = part;
-        __syncthreads();
-        float rr = s_red2[0] + s_red2[1];
-        f2 pb = seam ? s_seam[wi ^ 1][cp] : 0ull;  // the partner warp's seam row of p
-        const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
-                                           : fmaxf(1e-14f * rr, -rtol2);
-
-        for (int it = 0; it < iters; ++it) {
-            if (!(rr > rr_stop)) break;  // rr is identical in both warps
-            // the rows just above and below the thread's eight: the other row
-            // group of the warp (lane ^ 16), the other warp's seam row, or
-            // nothing (outside the block)
-            const f2 xo = __shfl_xor_sync(kFull, rg ? p[0] : p[NP - 1], 16);
-            const f2 pu = rg ? xo : (wi ? pb : 0ull);
-            const f2 pd = rg ? (wi ? 0ull : pb) : xo;
-            acc0 = 0ull;
-            acc1 = 0ull;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                const float hl = __shfl_up_sync(kFull, hi2(p[k]), 1, 16);    // column c0 - 1
-                const float lr = __shfl_down_sync(kFull, lo2(p[k]), 1, 16);  // column c0 + 2
-                const f2 up = k > 0 ? p[k - 1] : pu;
-                const f2 dn = k < NP - 1 ? p[k + 1] : pd;
-                f2 nbs = add2(up, dn);
-                nbs = fma2(ml2, pk(hl, lo2(p[k])), nbs);
-                nbs = fma2(mr2, pk(hi2(p[k]), lr), nbs);
-                const f2 qk = mul2(fma2(ndg[k], p[k], nbs), keep[k]);  // -(A_i p), 0 on the mask
-                q[k] = qk;
-                if (k & 1) acc1 = fma2(p[k], qk, acc1);
-                else acc0 = fma2(p[k], qk, acc0);
-            }
-            acc0 = add2(acc0, acc1);
-            part = warp_sum(lo2(acc0) + hi2(acc0));
-            if (lane == 0) s_red1[wi] = part;
-            __syncthreads();
-            const float pq = -(s_red1[0] + s_red1[1]);
-            if (!(pq > 0.f) || pq == INFINITY) break;
-            const float a = __fdividef(rr, pq);
-            const f2 a2 = pk(a, a);
-            acc0 = 0ull;
-            acc1 = 0ull;
-#pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                x[k] = fma2(a2, p[k], x[k]);
-                r[k] = fma2(a2, q[k], r[k]);
-                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
-                else acc0 = fma2(r[k], r[k], acc0);
-            }
-            acc0 = add2(acc0, acc1);
-            if (seam) s_seam[wi][cp] = wi == 0 ? r[NP - 1] : r[0];
-            part = warp_sum(lo2(acc0) + hi2(acc0));
-            if (lane == 0) s_red2[wi] = part;
-            __syncthreads();
-            const float rrn = s_red2[0] + s_red2[1];
-            const float beta = __fdividef(rrn, rr);
-            rr = rrn;
-            const f2 b2 = pk(beta, beta);
-#pragma unroll
-            for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
-            if (seam) pb = fma2(b2, pb, s_seam[wi ^ 1][cp]);
-            ++nsteps;
-        }
-
-        const int nsh = shared_per_seam(o);
-        float* uo = u_out + ch * n;
-        const bool ok0 = x0 + c0 < w, ok1 = x0 + c0 + 1 < w;
-        const float* tc = tu + (ry0 + 1) * P + c0 + 1;  // tile centre of (row ry0, column c0)
-        if (nsh == 0) {
-            // 0/1 weights (overlap 2): each pixel is written by the one block
-            // whose weight is 1 there, with u_in added
-            const bool w0 = ok0 && wx0 > 0.f, w1 = ok1 && wx1 > 0.f;
-            // both columns: one 8-byte store (even column, even width, 8-byte
-            // aligned image base)
-            const bool vec = w0 && w1 && (((x0 + c0) | w) & 1) == 0 &&
-                             (reinterpret_cast<uintptr_t>(uo) & 7) == 0;
-            float* uol = uo + (size_t)(y0 + ry0) * w + x0 + c0;
-            if (w0 || w1) {
-#pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    if (!((rows_w >> (ry0 + k)) & 1u)) continue;
-                    const float v0 = lo2(x[k]), v1 = hi2(x[k]);
-                    const float o0 = zero_in ? 0.f : tc[k * P], o1 = zero_in ? 0.f : tc[k * P + 1];
-                    if (vec) {
-                        *reinterpret_cast<float2*>(uol + (size_t)k * w) = make_float2(o0 + v0, o1 + v1);
-                        vmax = fmaxf(vmax, fmaxf(fabsf(v0), fabsf(v1)));
-                    } else {
-                        if (w0) { uol[(size_t)k * w] = o0 + v0; vmax = fmaxf(vmax, fabsf(v0)); }
-                        if (w1) { uol[(size_t)k * w + 1] = o1 + v1; vmax = fmaxf(vmax, fabsf(v1)); }
-                    }
-                }
-            }
-        } else {
-            const int first = shared_first(o);
-            const int par = (kx & 1) | ((ky & 1) << 1);
-            float* plane = planes + ((size_t)par * C + ch) * n;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int col = c0 + e;
-                if (!(e ? ok1 : ok0)) continue;
-                const float wx = e ? wx1 : wx0;
-                int sx_seam = -1, sx_side = 0, sx_j = 0;
-                if (kx > 0 && col >= first && col < first + nsh) {
-                    sx_seam = kx; sx_side = 1; sx_j = col - first;
-                } else if (kx < nbx - 1 && col - s >= first && col - s < first + nsh) {
-                    sx_seam = kx + 1; sx_side = 0; sx_j = col - s - first;
-                }
-                const size_t strip_row0 =
-                    ((size_t)(sx_side * C + ch) * (nbx - 1) + (sx_seam - 1)) * h;
-                float* strip = sx_seam > 0 ? planes + 4 * (size_t)C * n + strip_row0 * nsh + sx_j
-                                           : planes;
-                const bool xfirst = sx_seam < 0 || sx_side == 0;  // no left partner on x
-#pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    const int ly = ry0 + k;
-                    if (ly >= bh) continue;
-                    const float v = e ? hi2(x[k]) : lo2(x[k]);
-                    const float wyr = s_wy[ly];
-                    const float d = wx * wyr;
-                    const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
-                    const float uold = zero_in ? 0.f : tc[k * P + e];
-                    if (d == 1.f) {
-                        uo[gp] = uold + v;
-                    } else if (d > 0.f) {
-                        if (wyr < 1.f) {
-                            const bool yfirst = ly >= s;  // upper block of its row overlap
-                            plane[gp] = (xfirst && yfirst) ? uold + d * v : d * v;
-                        } else {
-                            strip[(size_t)(y0 + ly) * nsh] = xfirst ? uold + d * v : d * v;
-                        }
-                    }
-                    if (d > 0.f) vmax = fmaxf(vmax, fabsf(v));
-                }
-            }
-        }
-        if (!more) break;
-        blk = nb2;
-        ch = nc2;
-        buf ^= 1;
-    }
-    if (step_count && t == 0) atomicAdd(step_count, (unsigned long long)nsteps);
-    if (maxupd) {
-        vmax = warp_max(vmax);
-        if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
-    }
-}
-
 // ---- 16-bit storage variant of k_oras_2w ------------------------------------
 // The CG vectors, the stencil and the vector updates of each local solve run
 // in packed FP16 or BF16 (one 32-bit register per pixel pair, so half the
@@ -2289,35 +1893,20 @@ __global__ void k_plan(const unsigned long long* __restrict__ counts, StopState*
     st->cycles = 0;
     st->converged = 0;
     st->levels_used = Leff;
-    st->est = INFINITY;
+    st->est = 0.f;
     st->prevU = -1.f;
     st->prevQ = -1.f;
     st->unknowns = unk0;
     for (int k = 0; k < kMaxChannels; ++k) st->rel[k] = -1.f;
     const bool empty = unk0 == p.n0;
     st->status = empty ? DI_ERR_EMPTY_MASK : DI_OK;
-    for (int l = 1; l < L; ++l) {
-        const unsigned act = (!empty && l < Leff) ? 1u : 0u;
-        cudaGraphSetConditional(p.h_dn[l], act);
-        cudaGraphSetConditional(p.h_up[l], act);
+    if (empty) {
+        cudaGraphSetConditional(p.h_sel, kSelSkip);
+        return;
     }
-    if (p.cascade) {
-        // the cascade starts on the coarsest level (a single-block solve) or
-        // on the first fully known level (u = b there), then prolongs and
-        // smooths level by level; every pixel known: u = f on level 0
-        const int top = Leff == L ? L - 1 : Leff;
-        for (int l = 0; l < L; ++l) {
-            unsigned v = kCascSkip;
-            if (!empty) {
-                if (Leff == 0) v = l == 0 ? kCascSelect : kCascSkip;
-                else if (l == top) v = Leff == L ? kCascSolve : kCascSelect;
-                else if (l < top) v = kCascSolve;
-            }
-            cudaGraphSetConditional(p.h_casc[l], v);
-        }
-    }
-    if (Leff == 0 && !empty) st->converged = 1;
-    cudaGraphSetConditional(p.h_loop, (!empty && Leff > 0 && p.max_cycles > 0) ? 1u : 0u);
+    if (Leff == 0) st->converged = 1;  // every pixel known: u = f
+    cudaGraphSetConditional(p.h_sel, (unsigned)Leff);
+    if (Leff > 0) cudaGraphSetConditional(p.h_loop[Leff], p.max_cycles > 0 ? 1u : 0u);
 }
 
 // The stop test of the host loop, on the device: the same float arithmetic
@@ -2489,7 +2078,7 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
                   (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
                   (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
         smem = Smem2W::bytes(!rhs_zero);
-        kern = (const void*)k_oras_2c;
+        kern = (const void*)k_oras_2w;
         oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true), &nsm);
     } else {
         smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) * sizeof(float);
@@ -2503,7 +2092,7 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     if (grid < 1) grid = 1;
     if (ev) record_event(ev[0], s);
     if (precision == 0)
-        k_oras_2c<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
+        k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
                                          nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
                                          chan_inner, tm_u, tm_b, use_tma, errflag, step_count);
     else if (precision == 1)
