@@ -786,6 +786,11 @@ di_status finish_device(di_ctx* ctx) {
     const int L = ctx->L;
     const int Leff = hs.levels_used;
     std::memset(&ctx->stats, 0, sizeof ctx->stats);
+    for (int k = 0; k < 4; ++k) ctx->stats.rel_residual[k] = -1.f;
+    if (hs.status == DI_ERR_EMPTY_MASK) {  // as the host-driven loop reports it
+        if (dg && dg->valid) add_launches(dg->k_pre);
+        return DI_ERR_EMPTY_MASK;
+    }
     ctx->stats.levels = L;
     ctx->stats.levels_used = Leff;
     ctx->stats.cycles = hs.cycles;
