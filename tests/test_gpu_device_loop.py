@@ -123,7 +123,7 @@ def test_device_loop_not_converged_and_given_start(di):
     _, st, stats = _same(di, f, c, 1e-6, max_cycles=2)
     assert st == di.NOT_CONVERGED and stats["cycles"] == 2
     # the given start (a warm start from a converged result needs one cycle)
-    ref, st, _ = _decode(di, f, c, TOL)
+    ref, st, _, _ = _decode(di, f, c, TOL)
     assert st == di.OK
     for mode in (di.GRAPH_ON, di.GRAPH_OFF):
         with di.Context(start=di.START_GIVEN, graph=mode) as ctx:
