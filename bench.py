@@ -316,7 +316,10 @@ def run_ours(args):
 
             dist.barrier()
 
-    run_concurrent(decode, 0, max(args.warmup, S))
+    # warm-up: every frame on every decoder (a decoder's graph is captured on
+    # its first decode of a frame's buffers), at least W frames in all
+    for rep in range(max(1, -(-args.warmup // (S * len(cases))))):
+        run_concurrent(lambda t, i: decode(t, i // S), 0, S * len(cases))
     torch.cuda.synchronize(dev)
 
     # --- timed region: device-resident inputs -------------------------------
@@ -341,86 +344,45 @@ def run_ours(args):
         elapsed_ms = max_over_ranks(elapsed_ms, dev)
     value = job_rate(args.steps, ws, elapsed_ms)
 
-    # --- end to end: host buffers, copies inside the timed region -----------
-    # Each decoder overlaps its copies with its decodes: frame m + 1's inputs go
-    # up on the decoder's copy stream while frame m decodes, and frame m's result
-    # comes down while frame m + 1 decodes (two device buffer sets per decoder).
+    # --- end to end: host buffers through the C ABI's serving loop ----------
+    # di_server_submit / di_server_wait with page-locked host buffers: every
+    # request copies its f and c in and its u out inside the timed region; the
+    # server's slots (one per frame in flight) pipeline those copies with
+    # their decodes.  At most R requests are in flight, each with its own
+    # output buffer.
     e2e_steps = max(3 * S, min(args.steps, 12 * S))
     f_host = [torch.from_numpy(f).pin_memory() for f, _ in cases]
     c_host = [torch.from_numpy(c).pin_memory() for _, c in cases]
-    u_host = [[torch.empty(f_host[0].shape, dtype=torch.float32).pin_memory()
-               for _ in range(2)] for _ in range(S)]
-    f_buf = [[torch.empty_like(f_dev[0]) for _ in range(2)] for _ in range(S)]
-    c_buf = [[torch.empty_like(c_dev[0]) for _ in range(2)] for _ in range(S)]
-    u_buf = [[torch.empty_like(f_dev[0]) for _ in range(2)] for _ in range(S)]
-    copy_streams = [torch.cuda.Stream(dev) for _ in range(S)]
+    R = 4 * S
+    u_host = [torch.empty(f_host[0].shape, dtype=torch.float32).pin_memory() for _ in range(R)]
+    srv = di.Server(slots=S, device=local, precision=prec, block=args.block,
+                    overlap=args.overlap, local_iters=args.local_iters,
+                    local_iters_coarse=args.local_iters_coarse)
 
-    def e2e_run(first, n):
-        errs = []
+    def e2e_run(n):
+        tickets = []
+        for i in range(n):
+            if i >= R:
+                _, info = srv.wait(tickets[i - R])
+                if info["status"] != di.OK:
+                    raise RuntimeError(di.status_string(info["status"]))
+            k = i % len(cases)
+            tickets.append(srv.submit(f_host[k], c_host[k], TOL, out=u_host[i % R]))
+        for t in tickets[max(0, n - R):]:
+            _, info = srv.wait(t)
+            if info["status"] != di.OK:
+                raise RuntimeError(di.status_string(info["status"]))
 
-        def worker(t):
-            try:
-                cs, ds = copy_streams[t], streams[t]
-                mine = [first + j for j in range(t, n, S)]
-                decoded = [None, None]  # per buffer set: its last decode finished
-
-                def upload(m):
-                    slot = m & 1
-                    k = mine[m] % len(cases)
-                    with torch.cuda.stream(cs):
-                        if decoded[slot] is not None:
-                            cs.wait_event(decoded[slot])
-                        f_buf[t][slot].copy_(f_host[k], non_blocking=True)
-                        c_buf[t][slot].copy_(c_host[k], non_blocking=True)
-                        ev = torch.cuda.Event()
-                        ev.record(cs)
-                    return ev
-
-                up = upload(0) if mine else None
-                for m in range(len(mine)):
-                    slot = m & 1
-                    nxt = upload(m + 1) if m + 1 < len(mine) else None
-                    ds.wait_event(up)
-                    _, st = ctxs[t].inpaint(f_buf[t][slot], c_buf[t][slot], tol=TOL,
-                                            out=u_buf[t][slot], stream=ds)
-                    if st != di.OK:
-                        raise RuntimeError(di.status_string(st))
-                    ev = torch.cuda.Event()
-                    ev.record(ds)
-                    decoded[slot] = ev
-                    with torch.cuda.stream(cs):
-                        cs.wait_event(ev)
-                        u_host[t][slot].copy_(u_buf[t][slot], non_blocking=True)
-                    up = nxt
-            except Exception as e:  # surfaced after the join
-                errs.append(e)
-
-        th = [threading.Thread(target=worker, args=(t,)) for t in range(S)]
-        for x in th:
-            x.start()
-        for x in th:
-            x.join()
-        if errs:
-            raise errs[0]
-
-    e2e_run(0, S)
-    torch.cuda.synchronize(dev)
+    e2e_run(6 * S)  # warm-up: every slot's buffer sets and graphs
     barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(main)
-    for st_ in streams + copy_streams:
-        st_.wait_event(e0)
-    e2e_run(0, e2e_steps)
-    for st_ in streams + copy_streams:
-        main.wait_stream(st_)
-    e1.record(main)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    e2e_run(e2e_steps)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    srv.close()
     if ws > 1:
         e2e_ms = max_over_ranks(e2e_ms, dev)
     h2d = f_host[0].numel() * 4 + c_host[0].numel()
-    d2h = u_host[0][0].numel() * 4
+    d2h = u_host[0].numel() * 4
 
     # --- latency: LATENCY_FRAMES frames with S decoders in flight, then the
     # same number through one decoder alone (one frame at a time) -------------
@@ -636,7 +598,11 @@ def run_ours(args):
                       "model": "N C (46 + 83 k) bytes per frame, k V-cycles"},
         "hbm_measured": hbm_measured,
         "e2e": {"value": round(job_rate(e2e_steps, ws, e2e_ms), 3), "unit": UNIT,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "frames": e2e_steps,
+                "path": f"C ABI di_server_submit / di_server_wait, {S} slots, page-locked "
+                        "host buffers, host wall clock from the first submit to the last "
+                        "result"},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -708,14 +674,21 @@ def run_decode_once(args):
     _build.build()
     import paper_2401_06744_gb300 as di
 
+    import synth
+
     dev = torch.device("cuda", 0)
-    cases = _make_cases()
+    if args.small:  # the same frames at 960x540 (pass-count probes before a capture)
+        cases = [synth.make_case(960, 540, C4K, d, kind, _case_seed(i))
+                 for i, (d, kind) in enumerate(CASES)]
+    else:
+        cases = _make_cases()
     fd = [torch.from_numpy(f).to(dev) for f, _ in cases]
     cd = [torch.from_numpy(c).to(dev) for _, c in cases]
     out = torch.empty_like(fd[0])
     cyc = []
+    graph = di.GRAPH_OFF if args.graph == "off" else di.GRAPH_ON
     with di.Context(device=0, block=args.block, overlap=args.overlap,
-                    local_iters=args.local_iters,
+                    local_iters=args.local_iters, graph=graph,
                     local_iters_coarse=args.local_iters_coarse) as ctx:
         for k in range(len(cases)):
             ctx.inpaint(fd[k], cd[k], tol=TOL, out=out)
@@ -728,7 +701,7 @@ def run_decode_once(args):
         torch.cuda.synchronize(dev)
         launches = ctx.profile()["launches"]
     print(json.dumps({"frames": len(cases), "cycles": cyc, "launches": launches,
-                      "warmup_launches": warm,
+                      "warmup_launches": warm, "graph": args.graph,
                       "block": args.block, "overlap": args.overlap,
                       "local_iters": args.local_iters}), flush=True)
 
@@ -1030,27 +1003,35 @@ def _compare_configs(args, di, dev, s):
     for i, (w, h) in enumerate([(1280, 720), (1920, 1080), (3840, 2160)] * 4):
         d = float(gs.uniform(0.005, 0.10))
         kind = "uniform" if i % 2 == 0 else "edge"
-        pool_imgs.append(synth.make_case(w, h, 3, d, kind, 7000 + i))
+        f, c = synth.make_case(w, h, 3, d, kind, 7000 + i)
+        # page-locked host buffers: the server's copies run by DMA
+        pool_imgs.append((torch.from_numpy(f).pin_memory(), torch.from_numpy(c).pin_memory()))
+    ring = 32  # output buffers, one per request in flight
+    outs = [torch.empty((3, 2160, 3840), dtype=torch.float32).pin_memory() for _ in range(ring)]
     for lam in (60.0, 120.0, 240.0):
         n = int(2 * lam)  # about two seconds of offered load
         gaps = gs.exponential(1.0 / lam, size=n)
         pick = gs.integers(0, len(pool_imgs), size=n)
         with di.Server(slots=4, **cfg) as srv:
-            # warm-up: four 4K requests at once, one per slot (workspaces at 4K)
-            warm = [srv.submit(*pool_imgs[2], TOL) for _ in range(4)]
+            # warm-up: every size on every slot and buffer set (workspaces, graphs)
+            warm = [srv.submit(*pool_imgs[k % 3], TOL) for k in range(36)]
             for t_ in warm:
                 srv.wait(t_)
             tickets = []
+            res = []
             t_first = time.perf_counter()
             due = t_first
-            for gap, k in zip(gaps, pick):
+            for j, (gap, k) in enumerate(zip(gaps, pick)):
                 due += gap
                 now = time.perf_counter()
                 if due > now:
                     time.sleep(due - now)
                 f, c = pool_imgs[int(k)]
-                tickets.append(srv.submit(f, c, TOL))
-            res = [srv.wait(t)[1] for t in tickets]
+                if j >= ring:  # the output buffer's previous request is done
+                    res.append(srv.wait(tickets[j - ring])[1])
+                o = outs[j % ring].view(-1)[:f.numel()].view(f.shape)
+                tickets.append(srv.submit(f, c, TOL, out=o))
+            res += [srv.wait(t)[1] for t in tickets[max(0, len(tickets) - ring):]]
             t_last = time.perf_counter()
         lat = sorted(r["latency_ms"] for r in res)
         print(json.dumps({"config": 5, "workload": "Poisson stream, 720p/1080p/4K RGB, 0.5-10 %",
@@ -1085,6 +1066,12 @@ def main():
                     help="CG steps of the local block solves on the coarser levels")
     ap.add_argument("--streams", type=int, default=4,
                     help="frames in flight: decoders, each with its own context and stream")
+    ap.add_argument("--graph", choices=["on", "off"], default="on",
+                    help="--decode-once: the device-driven graph (on) or kernel-by-kernel "
+                         "launches with the stop rule on the host (off; same kernels, the "
+                         "form ncu profiles per kernel)")
+    ap.add_argument("--small", action="store_true",
+                    help="--decode-once on 960x540 frames instead of 3840x2160")
     ap.add_argument("--decode-once", action="store_true",
                     help="decode the six bench frames once each after a warm-up pass "
                          "(for whole-decode ncu captures) and exit")

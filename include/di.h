@@ -187,7 +187,7 @@ void di_destroy(di_ctx *ctx);
  * cascade's start chosen on the device from the mask (IF / SWITCH nodes), so
  * no host round trip happens during the decode.  The graph is captured on
  * the first call with a given (f, c, u, size, tol) and replayed by later
- * calls with the same buffers (a context keeps the last 8); the buffers'
+ * calls with the same buffers (a context keeps the last 16); the buffers'
  * contents may change between calls.  di_inpaint then waits for the stream
  * once, at the end.  Host-driven (every other configuration): the host
  * evaluates the stop rule, waiting for the stream after the pyramid and once
@@ -291,8 +291,12 @@ di_status di_autotune(const di_config *base, int device, const di_image *sample,
  * and started on a free slot once their device footprint (di_plan workspace
  * plus device copies of f, c, u) fits within `mem_budget` bytes next to the
  * requests in flight (0 = no limit; a lone request always starts).  Each
- * slot copies its request in, decodes and copies the result out on its own
- * stream. */
+ * slot is a pipeline of three host threads -- copy in, decode, copy out --
+ * on streams of its own, with three device buffer sets, so a slot's copies
+ * of the next and the previous request overlap its decode.  Host buffers in
+ * page-locked memory (cudaMallocHost / cudaHostRegister) are copied by DMA at
+ * full speed; pageable buffers work too, with the runtime's slower staged
+ * copies.  A request is taken by a slot whose decoder has nothing waiting. */
 typedef struct di_server di_server;
 
 typedef struct {

@@ -482,15 +482,23 @@ class Server:
         self._h = h
         self._live = {}
 
-    def submit(self, f, c, tol=0.05):
+    def submit(self, f, c, tol=0.05, out=None):
+        """Queue one request.  f [C,H,W] (or [H,W]) float32 and c [H,W] uint8 are
+        host arrays (numpy, or CPU tensors, e.g. pinned ones, whose memory is
+        used in place); out (optional, same shape as f) receives u."""
         import numpy as np
 
-        f = np.ascontiguousarray(f, dtype=np.float32)
+        def host(a, dt):
+            if isinstance(a, torch.Tensor):
+                a = a.numpy()
+            return np.ascontiguousarray(a, dtype=dt)
+
+        f = host(f, np.float32)
         if f.ndim == 2:
             f = f[None]
-        c = np.ascontiguousarray(c, dtype=np.uint8)
+        c = host(c, np.uint8)
         C, H, W = f.shape
-        u = np.empty_like(f)
+        u = np.empty_like(f) if out is None else host(out, np.float32).reshape(f.shape)
         t = ctypes.c_longlong()
         _check(load().di_server_submit(self._h, f.ctypes.data, c.ctypes.data, W, H, C, float(tol),
                                        u.ctypes.data, ctypes.byref(t)))

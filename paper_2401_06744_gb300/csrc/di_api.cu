@@ -109,7 +109,7 @@ struct di_ctx {
     StopState* hstate = nullptr;
     cudaEvent_t done_ev = nullptr;
     cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
-    static constexpr int kGraphs = 8;
+    static constexpr int kGraphs = 16;
     DecodeGraph graphs[kGraphs];
     unsigned long long graph_clock = 0;
     unsigned long long ws_gen = 0;     // workspace generation (graphs bake its addresses)

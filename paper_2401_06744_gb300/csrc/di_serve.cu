@@ -227,6 +227,17 @@ extern "C" di_status di_autotune(const di_config* base, int device, const di_ima
 
 // ---------------------------------------------------------------------------
 // Serving loop
+//
+// Every slot is a three-stage pipeline with its own host thread per stage:
+// input (copy a request's f and c to the device on the slot's input stream),
+// decode (di_inpaint on the slot's context and stream) and output (copy u
+// back on the slot's output stream and complete the request).  Three device
+// buffer sets rotate through the stages, so a slot copies the next request in
+// and the previous result out while it decodes, and a copy from pageable host
+// memory (which the runtime performs synchronously) blocks only its own stage.
+// A slot's input stage takes a request from the queue only when the slot's
+// decoder has nothing waiting, so a request does not queue behind a busy slot
+// while another is idle.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -242,16 +253,62 @@ struct Request {
     std::chrono::steady_clock::time_point t_submit, t_start, t_done;
     di_status status = DI_OK;
     int cycles = 0;
+    int set = -1;  // buffer set of its slot
     bool done = false;
 };
 
+struct BufSet {
+    float* f = nullptr;
+    uint8_t* c = nullptr;
+    float* u = nullptr;
+    size_t cap = 0, cap_px = 0;  // pixel-channels and pixels of the buffers
+};
+
+// Hand-off between two stages of a slot.
+template <class T>
+struct Chan {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<T> q;
+    bool closed = false;
+    void push(T v) {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            q.push_back(v);
+        }
+        cv.notify_all();
+    }
+    bool pop(T& v) {  // false once closed and drained
+        std::unique_lock<std::mutex> lock(mu);
+        cv.wait(lock, [&] { return closed || !q.empty(); });
+        if (q.empty()) return false;
+        v = q.front();
+        q.pop_front();
+        cv.notify_all();
+        return true;
+    }
+    void wait_empty() {
+        std::unique_lock<std::mutex> lock(mu);
+        cv.wait(lock, [&] { return q.empty(); });
+    }
+    void close() {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            closed = true;
+        }
+        cv.notify_all();
+    }
+};
+
+constexpr int kSets = 3;
+
 struct ServerSlot {
-    Slot s;
-    float* f_dev = nullptr;
-    uint8_t* c_dev = nullptr;
-    float* u_dev = nullptr;
-    size_t cap = 0;  // pixel-channels of the device buffers
-    size_t cap_px = 0;
+    Slot s;  // context and decode stream
+    cudaStream_t in_stream = nullptr, out_stream = nullptr;
+    BufSet sets[kSets];
+    Chan<int> free_sets;
+    Chan<Request*> to_decode, to_output;
+    std::thread t_in, t_dec, t_out;
 };
 
 }  // namespace
@@ -260,8 +317,7 @@ struct di_server {
     di_config cfg;
     int device = 0;
     size_t budget = 0;
-    std::vector<ServerSlot> slots;
-    std::vector<std::thread> threads;
+    std::vector<ServerSlot*> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request*> queue;
@@ -281,76 +337,127 @@ size_t footprint(const di_config& cfg, int w, int h, int C) {
     return (size_t)p.workspace_bytes + (size_t)w * h * (2 * C * sizeof(float) + 1);
 }
 
-bool ensure_buffers(ServerSlot& sl, size_t pxch, size_t px) {
-    if (pxch <= sl.cap && px <= sl.cap_px) return true;
-    if (sl.f_dev) cudaFree(sl.f_dev);
-    if (sl.u_dev) cudaFree(sl.u_dev);
-    if (sl.c_dev) cudaFree(sl.c_dev);
-    sl.f_dev = sl.u_dev = nullptr;
-    sl.c_dev = nullptr;
-    sl.cap = sl.cap_px = 0;
-    if (cudaMalloc(&sl.f_dev, pxch * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&sl.u_dev, pxch * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&sl.c_dev, px) != cudaSuccess)
+bool ensure_buffers(BufSet& b, size_t pxch, size_t px) {
+    if (pxch <= b.cap && px <= b.cap_px) return true;
+    if (b.f) cudaFree(b.f);
+    if (b.u) cudaFree(b.u);
+    if (b.c) cudaFree(b.c);
+    b = BufSet();
+    if (cudaMalloc(&b.f, pxch * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&b.u, pxch * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&b.c, px) != cudaSuccess) {
+        cudaGetLastError();
         return false;
-    sl.cap = pxch;
-    sl.cap_px = px;
+    }
+    b.cap = pxch;
+    b.cap_px = px;
     return true;
 }
 
-void serve_loop(di_server* srv, int k) {
-    ServerSlot& sl = srv->slots[k];
+void complete(di_server* srv, Request* r) {
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        r->t_done = std::chrono::steady_clock::now();
+        r->done = true;
+        srv->in_flight_bytes -= r->bytes;
+        ++srv->completed;
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+}
+
+void input_stage(di_server* srv, ServerSlot* sl) {
     cudaSetDevice(srv->device);
     for (;;) {
+        int set = -1;
+        if (!sl->free_sets.pop(set)) break;
+        sl->to_decode.wait_empty();  // the decoder is about to be free
         Request* r = nullptr;
         {
             std::unique_lock<std::mutex> lock(srv->mu);
             // admission: the queue head runs once its footprint fits the budget
             // next to what is already in flight (a lone request always runs)
             srv->cv_work.wait(lock, [&] {
-                if (srv->stop) return true;
+                if (srv->stop && srv->queue.empty()) return true;
                 if (srv->queue.empty()) return false;
                 Request* head = srv->queue.front();
                 return srv->in_flight_bytes == 0 ||
                        srv->in_flight_bytes + head->bytes <= srv->budget;
             });
-            if (srv->stop && srv->queue.empty()) return;
-            if (srv->queue.empty()) continue;
+            if (srv->queue.empty()) break;  // stopping
             r = srv->queue.front();
             srv->queue.pop_front();
             srv->in_flight_bytes += r->bytes;
         }
         r->t_start = std::chrono::steady_clock::now();
+        r->set = set;
+        BufSet& b = sl->sets[set];
         const size_t px = (size_t)r->w * r->h, pxch = px * r->ch;
-        di_status st = DI_OK;
-        if (!ensure_buffers(sl, pxch, px)) st = DI_ERR_OOM;
-        if (st == DI_OK) {
-            cudaMemcpyAsync(sl.f_dev, r->f, pxch * sizeof(float), cudaMemcpyHostToDevice,
-                            sl.s.stream);
-            cudaMemcpyAsync(sl.c_dev, r->c, px, cudaMemcpyHostToDevice, sl.s.stream);
-            st = di_inpaint(sl.s.ctx, sl.f_dev, sl.c_dev, r->w, r->h, r->ch, r->tol, sl.u_dev,
-                            sl.s.stream);
-            if (st == DI_OK || st == DI_ERR_NOT_CONVERGED)
-                cudaMemcpyAsync(r->u, sl.u_dev, pxch * sizeof(float), cudaMemcpyDeviceToHost,
-                                sl.s.stream);
-            // whatever the status, nothing of this request stays queued
-            if (cudaStreamSynchronize(sl.s.stream) != cudaSuccess && st == DI_OK)
-                st = DI_ERR_CUDA;
+        if (!ensure_buffers(b, pxch, px)) {
+            r->status = DI_ERR_OOM;
+        } else if (cudaMemcpyAsync(b.f, r->f, pxch * sizeof(float), cudaMemcpyHostToDevice,
+                                   sl->in_stream) != cudaSuccess ||
+                   cudaMemcpyAsync(b.c, r->c, px, cudaMemcpyHostToDevice, sl->in_stream) !=
+                       cudaSuccess ||
+                   cudaStreamSynchronize(sl->in_stream) != cudaSuccess) {
+            cudaGetLastError();
+            r->status = DI_ERR_CUDA;
         }
-        di_stats ss;
-        di_get_stats(sl.s.ctx, &ss);
-        {
-            std::lock_guard<std::mutex> lock(srv->mu);
+        sl->to_decode.push(r);
+    }
+    sl->to_decode.close();
+}
+
+void decode_stage(di_server* srv, ServerSlot* sl) {
+    cudaSetDevice(srv->device);
+    Request* r = nullptr;
+    while (sl->to_decode.pop(r)) {
+        if (r->status == DI_OK) {
+            BufSet& b = sl->sets[r->set];
+            di_status st = di_inpaint(sl->s.ctx, b.f, b.c, r->w, r->h, r->ch, r->tol, b.u,
+                                      sl->s.stream);
+            // whatever the status, nothing of this request stays queued
+            if (cudaStreamSynchronize(sl->s.stream) != cudaSuccess && st == DI_OK)
+                st = DI_ERR_CUDA;
+            di_stats ss;
+            di_get_stats(sl->s.ctx, &ss);
             r->status = st;
             r->cycles = ss.cycles;
-            r->t_done = std::chrono::steady_clock::now();
-            r->done = true;
-            srv->in_flight_bytes -= r->bytes;
-            ++srv->completed;
         }
-        srv->cv_done.notify_all();
-        srv->cv_work.notify_all();
+        sl->to_output.push(r);
     }
+    sl->to_output.close();
+}
+
+void output_stage(di_server* srv, ServerSlot* sl) {
+    cudaSetDevice(srv->device);
+    Request* r = nullptr;
+    while (sl->to_output.pop(r)) {
+        if (r->status == DI_OK || r->status == DI_ERR_NOT_CONVERGED) {
+            BufSet& b = sl->sets[r->set];
+            const size_t pxch = (size_t)r->w * r->h * r->ch;
+            if (cudaMemcpyAsync(r->u, b.u, pxch * sizeof(float), cudaMemcpyDeviceToHost,
+                                sl->out_stream) != cudaSuccess ||
+                cudaStreamSynchronize(sl->out_stream) != cudaSuccess) {
+                cudaGetLastError();
+                r->status = DI_ERR_CUDA;
+            }
+        }
+        if (r->set >= 0) sl->free_sets.push(r->set);
+        complete(srv, r);
+    }
+}
+
+void free_server_slot(ServerSlot* sl) {
+    for (auto& b : sl->sets) {
+        if (b.f) cudaFree(b.f);
+        if (b.u) cudaFree(b.u);
+        if (b.c) cudaFree(b.c);
+    }
+    if (sl->in_stream) cudaStreamDestroy(sl->in_stream);
+    if (sl->out_stream) cudaStreamDestroy(sl->out_stream);
+    free_slot(&sl->s);
+    delete sl;
 }
 
 }  // namespace
@@ -365,16 +472,28 @@ extern "C" di_status di_server_create(const di_config* cfg, int device, int slot
     if (cfg) srv->cfg = *cfg;
     srv->device = device;
     srv->budget = mem_budget > 0 ? (size_t)mem_budget : (size_t)-1;
-    srv->slots.resize(slots);
-    for (int k = 0; k < slots; ++k) {
-        di_status st = make_slot(&srv->cfg, device, &srv->slots[k].s);
-        if (st != DI_OK) {
-            for (auto& sl : srv->slots) free_slot(&sl.s);
-            delete srv;
-            return st;
-        }
+    di_status st = DI_OK;
+    for (int k = 0; k < slots && st == DI_OK; ++k) {
+        ServerSlot* sl = new (std::nothrow) ServerSlot();
+        if (!sl) { st = DI_ERR_OOM; break; }
+        srv->slots.push_back(sl);
+        st = make_slot(&srv->cfg, device, &sl->s);
+        if (st == DI_OK &&
+            (cudaStreamCreateWithFlags(&sl->in_stream, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaStreamCreateWithFlags(&sl->out_stream, cudaStreamNonBlocking) != cudaSuccess))
+            st = DI_ERR_CUDA;
+        for (int b = 0; b < kSets; ++b) sl->free_sets.push(b);
     }
-    for (int k = 0; k < slots; ++k) srv->threads.emplace_back(serve_loop, srv, k);
+    if (st != DI_OK) {
+        for (auto* sl : srv->slots) free_server_slot(sl);
+        delete srv;
+        return st;
+    }
+    for (auto* sl : srv->slots) {
+        sl->t_in = std::thread(input_stage, srv, sl);
+        sl->t_dec = std::thread(decode_stage, srv, sl);
+        sl->t_out = std::thread(output_stage, srv, sl);
+    }
     *out = srv;
     return DI_OK;
 }
@@ -438,14 +557,15 @@ extern "C" void di_server_destroy(di_server* srv) {
         srv->stop = true;
     }
     srv->cv_work.notify_all();
-    for (auto& t : srv->threads) t.join();
-    cudaSetDevice(srv->device);
-    for (auto& sl : srv->slots) {
-        if (sl.f_dev) cudaFree(sl.f_dev);
-        if (sl.u_dev) cudaFree(sl.u_dev);
-        if (sl.c_dev) cudaFree(sl.c_dev);
-        free_slot(&sl.s);
+    // the input stages finish the queue and close their pipelines
+    for (auto* sl : srv->slots) sl->free_sets.close();
+    for (auto* sl : srv->slots) {
+        if (sl->t_in.joinable()) sl->t_in.join();
+        if (sl->t_dec.joinable()) sl->t_dec.join();
+        if (sl->t_out.joinable()) sl->t_out.join();
     }
+    cudaSetDevice(srv->device);
+    for (auto* sl : srv->slots) free_server_slot(sl);
     for (auto& kv : srv->reqs) delete kv.second;
     delete srv;
 }
