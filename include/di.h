@@ -59,11 +59,16 @@ typedef enum {
  * DI_STOP_FIXED_CYCLES: exactly max_cycles V-cycles. */
 enum { DI_STOP_ERROR_ESTIMATE = 0, DI_STOP_RELATIVE_RESIDUAL = 1, DI_STOP_FIXED_CYCLES = 2 };
 
-/* Precision of the block-local CG iterates.  DI_PREC_FP16 / DI_PREC_BF16:
- * vectors, stencil and updates of every local solve in packed 16-bit
- * arithmetic with FP32 dot products; the block residual is normalised before
- * it is narrowed; the FP32 outer iteration refines the result.  Applies to
- * 32x32 blocks; other block sizes compute in FP32. */
+/* Precision modes.  DI_PREC_FP32: everything FP32.  DI_PREC_FP16 /
+ * DI_PREC_BF16: (1) the block-local CG iterates -- vectors, stencil and
+ * updates of every local solve -- in packed 16-bit arithmetic with FP32 dot
+ * products (the block residual is normalised before it is narrowed); (2) the
+ * coarse levels' iterates and restricted residuals, i.e. the coarse-grid
+ * corrections of Section 4.1, stored in that 16-bit type (read, widened and
+ * computed in FP32, rounded once when stored).  The finest grid keeps FP32
+ * iterates and FP32 residuals, so the outer FP32 iteration refines whatever
+ * the narrow parts leave (cfg.refine_fp64 adds FP64 residuals there).
+ * Requires 32x32 blocks and the block smoother. */
 enum { DI_PREC_FP32 = 0, DI_PREC_FP16 = 1, DI_PREC_BF16 = 2 };
 
 /* Schedules (Sections 4.2 and 5).  REDUCED_FMG: the cascade with one
@@ -119,9 +124,9 @@ typedef struct {
     int stop_rule;    /* DI_STOP_* [DI_STOP_ERROR_ESTIMATE] */
     int profile;      /* 1: time every finest-level ORAS block launch with CUDA events
                          recorded on the call's stream (see di_get_profile) [0] */
-    int precision;    /* DI_PREC_*: storage of the local CG iterates of 32x32 blocks
+    int precision;    /* DI_PREC_*: the local CG iterates and the coarse levels' storage
                          [DI_PREC_FP32]; the residual that starts each local solve and
-                         the update of u are FP32 in every mode */
+                         the update of u are computed in FP32 in every mode */
     int schedule;     /* DI_SCHED_* [DI_SCHED_REDUCED_FMG] */
     int smoother;     /* DI_SMOOTH_* [DI_SMOOTH_ORAS] */
     int graph;        /* DI_GRAPH_*: replay of the finest-level V-cycle [DI_GRAPH_ON] */
@@ -133,6 +138,11 @@ typedef struct {
                          most local_stop * tol gray -- a local correction that small is
                          below what the stop rule resolves (Section 3.1 stops the local
                          solves on their residual too); < 0 disables [0.2] */
+    int refine_fp64;  /* 1: the residuals of the finest grid (the block solves' start, the
+                         restriction to the first coarse level, the relative-residual stop
+                         rule) are formed in FP64 from the FP32 iterate and rounded once --
+                         the outer refinement for tolerances near FP32's resolution of
+                         values up to 255; FP64 is used nowhere else [0] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */
@@ -389,10 +399,12 @@ di_status di_residual_norm_noalloc(const float *u, const float *b, int rhs_zero,
 /* Residual restriction (Algorithm 3 steps 2-3, Section 4.4): for every coarse
  * cell with cH == 0, rH = 4 * mean over its fine children of (b - A u) (the
  * factor 4 = (H/h)^2 rescales the unit-spacing stencil to the coarse
- * spacing); rH = 0 where cH == 1.  Arguments as for di_residual_norm. */
+ * spacing); rH = 0 where cH == 1.  fp64 = 1: the children's residuals are
+ * formed and summed in FP64 and rounded once (the finest-grid refinement
+ * residual of cfg.refine_fp64).  Other arguments as for di_residual_norm. */
 di_status di_restrict_residual(const float *u, const float *b, int rhs_zero,
                                const uint8_t *c, int width, int height, int channels,
-                               const uint8_t *cH, float *rH, void *stream);
+                               const uint8_t *cH, float *rH, int fp64, void *stream);
 
 /* Cell-centred bilinear prolongation (Section 4.4) from uH
  * [ch][ceil(h/2)][ceil(w/2)] to the fine grid [ch][h][w] (weights 9/16, 3/16,

@@ -35,7 +35,7 @@ class di_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("graph", ctypes.c_int),
                 ("start", ctypes.c_int), ("local_iters_coarse", ctypes.c_int),
-                ("local_stop", ctypes.c_float)]
+                ("local_stop", ctypes.c_float), ("refine_fp64", ctypes.c_int)]
 
 
 class di_stats(ctypes.Structure):
@@ -112,7 +112,7 @@ _SIGS = {
     "di_values_downsample": (_I, [_P, _P, _I, _I, _I, _P, _P, _I, _P]),
     "di_residual_norm": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_residual_norm_noalloc": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
-    "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
+    "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P]),
     "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
     "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     "di_selftest_bounded_wait": (_I, [_I, _I, _P]),
@@ -347,13 +347,13 @@ def residual_norm_noalloc(u, b, c, rhs_zero=False, want_r=True, stream=None):
     return r, n2
 
 
-def restrict_residual(u, b, c, cH, rhs_zero=False, stream=None):
+def restrict_residual(u, b, c, cH, rhs_zero=False, fp64=False, stream=None):
     u3, b3, c, cH = _img(u, "u"), _img(b, "b"), _mask(c), _mask(cH)
     C, H, W = u3.shape
     rH = torch.empty((C, (H + 1) // 2, (W + 1) // 2), dtype=torch.float32, device=u3.device)
     _check(load().di_restrict_residual(u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
                                        c.data_ptr(), W, H, C, cH.data_ptr(), rH.data_ptr(),
-                                       _stream(stream)))
+                                       int(bool(fp64)), _stream(stream)))
     return rH
 
 

@@ -161,6 +161,11 @@ bool config_ok(const di_config& c) {
     if (c.start < 0 || c.start > 1) return false;
     if (c.local_iters_coarse < 0) return false;
     if (!std::isfinite(c.local_stop)) return false;
+    if (c.refine_fp64 != 0 && c.refine_fp64 != 1) return false;
+    // the 16-bit modes store the coarse levels narrow: 32x32 blocks and the
+    // block smoother only (the global CG smoother keeps FP32 vectors)
+    if (c.precision != DI_PREC_FP32 && (c.block != 32 || c.smoother != DI_SMOOTH_ORAS))
+        return false;
     return true;
 }
 
@@ -225,8 +230,9 @@ void free_workspace(di_ctx* ctx) {
     ctx->cap_w = ctx->cap_h = ctx->cap_c = 0;
 }
 
-// Byte size of the pooled level buffers for an image of (w, h, C).
-size_t pool_bytes(int w, int h, int C, int L) {
+// Byte size of the pooled level buffers for an image of (w, h, C); the coarse
+// levels' iterates and right-hand sides are stored as `stor` (Storage).
+size_t pool_bytes(int w, int h, int C, int L, int stor) {
     size_t total = 0;
     int lw = w, lh = h;
     for (int l = 0; l < L; ++l) {
@@ -235,8 +241,9 @@ size_t pool_bytes(int w, int h, int C, int L) {
         if (l == 0) {
             total += align_up(n * C * sizeof(float));  // u[1]
         } else {
-            total += align_up(n);                           // c
-            total += 4 * align_up(n * C * sizeof(float));  // b, u[0], u[1], r
+            total += align_up(n);                                  // c
+            total += align_up(n * C * sizeof(float));             // b
+            total += 3 * align_up(n * C * storage_bytes(stor));  // u[0], u[1], r
         }
         coarse_dims(lw, lh, &lw, &lh);
     }
@@ -252,7 +259,7 @@ di_status ensure_workspace(di_ctx* ctx, int w, int h, int C) {
     const int nc = C > ctx->cap_c ? C : ctx->cap_c;
     free_workspace(ctx);
     const int L = num_levels(nw, nh, ctx->cfg.block);
-    cudaError_t e = cudaMalloc(&ctx->pool, pool_bytes(nw, nh, nc, L));
+    cudaError_t e = cudaMalloc(&ctx->pool, pool_bytes(nw, nh, nc, L, ctx->cfg.precision));
     if (e != cudaSuccess) { ctx->pool = nullptr; return cuda_fail(ctx, e, "cudaMalloc(pool)"); }
     e = cudaMalloc(&ctx->planes,
                    oras_scratch_floats(nw, nh, nc, ctx->cfg.block, ctx->cfg.overlap) * sizeof(float));
@@ -284,6 +291,7 @@ void bind_levels(di_ctx* ctx, const float* f, const uint8_t* c, float* u, int w,
         v.h = lh;
         v.n = (size_t)lw * lh;
         const size_t fb = align_up(v.n * C * sizeof(float));
+        const size_t nb = align_up(v.n * C * storage_bytes(ctx->cfg.precision));
         v.mbits = reinterpret_cast<uint32_t*>(p);
         p += align_up((size_t)lh * mask_words_per_row(lw) * sizeof(uint32_t));
         if (l == 0) {
@@ -295,9 +303,10 @@ void bind_levels(di_ctx* ctx, const float* f, const uint8_t* c, float* u, int w,
         } else {
             v.c = reinterpret_cast<uint8_t*>(p); p += align_up(v.n);
             v.b = reinterpret_cast<float*>(p); p += fb;
-            v.u[0] = reinterpret_cast<float*>(p); p += fb;
-            v.u[1] = reinterpret_cast<float*>(p); p += fb;
-            v.r = reinterpret_cast<float*>(p); p += fb;
+            // stored as the coarse levels' Storage (the pointers are untyped there)
+            v.u[0] = reinterpret_cast<float*>(p); p += nb;
+            v.u[1] = reinterpret_cast<float*>(p); p += nb;
+            v.r = reinterpret_cast<float*>(p); p += nb;
         }
         v.unknowns = 0;
         coarse_dims(lw, lh, &lw, &lh);
@@ -325,6 +334,12 @@ struct Sched {
     cudaStream_t s;
     int root = 0;  // level whose own problem is being solved (the others solve A e = r)
     float abs2 = 0.f;  // absolute local stop r.r <= abs2 of the smoothing ORAS calls (0: none)
+
+    // Storage of level l's iterates and restricted residual: FP32 on the
+    // finest level, the precision's type on the coarse levels.
+    int stor(int l) const { return l == 0 ? (int)kF32 : ctx->cfg.precision; }
+    // FP64 residuals on the finest level (cfg.refine_fp64)
+    bool f64(int l) const { return l == 0 && ctx->cfg.refine_fp64; }
 
     // Right-hand side of level l: the root level solves A u = b_l (level 0:
     // b = C f; coarse levels: the downsampled mask values), whose right-hand
@@ -369,7 +384,8 @@ struct Sched {
                                  ctx->cfg.overlap, ctx->cfg.alpha, iters, rtol2, out,
                                  ctx->planes, maxupd, s, ev, ctx->cfg.precision,
                                  ctx->upd + kMaxUpdSlots,
-                                 l == 0 && ctx->cfg.profile ? ctx->dsteps : nullptr));
+                                 l == 0 && ctx->cfg.profile ? ctx->dsteps : nullptr, stor(l),
+                                 f64(l)));
         return DI_OK;
     }
 
@@ -420,19 +436,20 @@ struct Sched {
             zero = false;
         }
         if (zero) {  // pre = 0 on a zero start: materialise the zero iterate
-            DI_CUDA(ctx, cudaMemsetAsync(v.u[cur], 0, v.n * C * sizeof(float), s));
+            DI_CUDA(ctx, cudaMemsetAsync(v.u[cur], 0, v.n * C * storage_bytes(stor(l)), s));
             zero = false;
         }
         if (l + 1 < Leff) {
             Level& cv = ctx->lv[l + 1];
             int rz;
             const float* rhs = rhs_of(l, &rz);
-            DI_CUDA(ctx, launch_restrict(v.u[cur], rhs, rz, v.c, v.w, v.h, C, cv.c, cv.r, s));
+            DI_CUDA(ctx, launch_restrict(v.u[cur], rhs, rz, v.c, v.w, v.h, C, cv.c, cv.r, s, stor(l),
+                                         rz ? (int)kF32 : stor(l), stor(l + 1), f64(l)));
             int cw = 0;
             st = vcycle(l + 1, true, &cw, nullptr);
             if (st) return st;
             DI_CUDA(ctx, launch_prolong(cv.u[cw], nullptr, v.c, v.w, v.h, C, v.u[cur], 1,
-                                        upd ? &upd[slot] : nullptr, s));
+                                        upd ? &upd[slot] : nullptr, s, stor(l + 1), stor(l)));
         }
         ++slot;
         for (int k = 0; k < cfg.post; ++k) {
@@ -603,19 +620,21 @@ bool capture_cascade(di_ctx* ctx, Sched& S, int Leff) {
         top = L - 1;
         Level& v = lv[top];
         S.root = top;
-        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[1], S.s)) return false;
+        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[1], S.s, 0, S.stor(top))) return false;
         if (S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2))
             return false;
     } else {
         top = Leff;
         Level& v = lv[top];
-        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[0], S.s)) return false;
+        if (launch_select(v.b, v.c, v.w, v.h, C, v.u[0], S.s, 0, S.stor(top))) return false;
     }
     for (int l = top - 1; l >= 0; --l) {
         Level& v = lv[l];
         Level& cv = lv[l + 1];
         S.root = l;
-        if (launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, S.s)) return false;
+        if (launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, S.s, S.stor(l + 1),
+                           S.stor(l)))
+            return false;
         if (S.smooth(l, v.u[1], 0, v.u[0], nullptr)) return false;
     }
     S.root = 0;
@@ -694,7 +713,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             step = "reference norm";
             if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
                 (launch_residual(nullptr, 1, f, 1, c, w, h, C, nullptr, ctx->partials, &nparts,
-                                 s0) ||
+                                 s0, cfg.refine_fp64 != 0) ||
                  launch_reduce_partials(ctx->partials, nparts, C, state_field(ctx, kBnorm2), s0)))
                 return false;
             // 3. one body per number of levels in use: the cascade, then the
@@ -724,7 +743,8 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
                         if (S.vcycle(0, false, &which, ctx->upd) || which != 0) return false;
                         if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL &&
                             (launch_residual(lv[0].u[0], 0, f, 1, c, w, h, C, nullptr,
-                                             ctx->partials, &nparts, s2) ||
+                                             ctx->partials, &nparts, s2,
+                                             cfg.refine_fp64 != 0) ||
                              launch_reduce_partials(ctx->partials, nparts, C,
                                                     state_field(ctx, kNorm2), s2)))
                             return false;
@@ -882,7 +902,7 @@ di_status di_plan(const di_config* cfg, int width, int height, int channels,
         coarse_dims(lw, lh, &lw, &lh);
     }
     out->local_problems = (long long)out->blocks_x[0] * out->blocks_y[0] * channels;
-    out->workspace_bytes = (long long)(pool_bytes(width, height, channels, L) +
+    out->workspace_bytes = (long long)(pool_bytes(width, height, channels, L, c.precision) +
                                        oras_scratch_floats(width, height, channels, c.block,
                                                            c.overlap) * sizeof(float) +
                                        residual_partials_per_channel(width, height) * channels *
@@ -1109,13 +1129,13 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
             top = L - 1;
             Level& v = ctx->lv[top];
             S.root = top;
-            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s));
+            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[1], s, 0, S.stor(top)));
             st = S.run_oras(top, v.u[1], 0, v.u[0], cfg.coarse_iters, nullptr, kCoarseRtol2);
             if (st) return st;
         } else {
             top = Leff;  // fully known level: u = b there
             Level& v = ctx->lv[top];
-            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s));
+            DI_CUDA(ctx, launch_select(v.b, v.c, v.w, v.h, C, v.u[0], s, 0, S.stor(top)));
         }
         for (int l = top - 1; l >= 0; --l) {
             Level& v = ctx->lv[l];
@@ -1123,14 +1143,16 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
             S.root = l;
             if (cfg.schedule == DI_SCHED_FULL_FMG) {
                 // full FMG: a V-cycle on every level of the cascade
-                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[0], 0, nullptr, s));
+                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[0], 0, nullptr, s,
+                                            S.stor(l + 1), S.stor(l)));
                 int which = 0;
                 st = S.vcycle(l, false, &which, nullptr);
                 if (st) return st;
                 if (which != 0) std::swap(v.u[0], v.u[1]);
             } else {
                 // reduced FMG and multilevel: one smoothing step per level
-                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s));
+                DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s,
+                                            S.stor(l + 1), S.stor(l)));
                 st = S.smooth(l, v.u[1], 0, v.u[0], nullptr);
                 if (st) return st;
             }
@@ -1160,7 +1182,7 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
     int nparts = 0;
     if (cfg.stop_rule == DI_STOP_RELATIVE_RESIDUAL) {
         DI_CUDA(ctx, launch_residual(nullptr, 1, f, 1, c, width, height, C, nullptr,
-                                     ctx->partials, &nparts, s));
+                                     ctx->partials, &nparts, s, cfg.refine_fp64 != 0));
         DI_CUDA(ctx, launch_reduce_partials(ctx->partials, nparts, C, ctx->norm2, s));
         DI_CUDA(ctx, cudaMemcpyAsync(hnorm, ctx->norm2, C * sizeof(double), cudaMemcpyDeviceToHost, s));
         DI_CUDA(ctx, cudaStreamSynchronize(s));
@@ -1222,7 +1244,7 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
             if (cycles >= cfg.min_cycles && est <= 0.5f * tol) { converged = true; break; }
         } else {
             DI_CUDA(ctx, launch_residual(v0.u[0], 0, f, 1, c, width, height, C, nullptr,
-                                         ctx->partials, &nparts, s));
+                                         ctx->partials, &nparts, s, cfg.refine_fp64 != 0));
             DI_CUDA(ctx, launch_reduce_partials(ctx->partials, nparts, C, ctx->norm2, s));
             DI_CUDA(ctx, cudaMemcpyAsync(hnorm, ctx->norm2, C * sizeof(double),
                                          cudaMemcpyDeviceToHost, s));
@@ -1330,12 +1352,13 @@ di_status di_residual_norm_noalloc(const float* u, const float* b, int rhs_zero,
 
 di_status di_restrict_residual(const float* u, const float* b, int rhs_zero, const uint8_t* c,
                                int width, int height, int channels, const uint8_t* cH,
-                               float* rH, void* stream) {
+                               float* rH, int fp64, void* stream) {
     if (!u || !b || !c || !cH || !rH || width < 1 || height < 1 || channels < 1 ||
-        channels > kMaxChannels)
+        channels > kMaxChannels || (fp64 != 0 && fp64 != 1))
         return DI_ERR_INVALID_ARG;
     cudaError_t e = launch_restrict(u, b, rhs_zero ? 1 : 0, c, width, height, channels, cH, rH,
-                                    static_cast<cudaStream_t>(stream));
+                                    static_cast<cudaStream_t>(stream), kF32, kF32, kF32,
+                                    fp64 != 0);
     return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
 }
 
@@ -1368,7 +1391,8 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels,
                              ctx->cfg.block, ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f,
                              u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision,
-                             ctx->upd + kMaxUpdSlots));
+                             ctx->upd + kMaxUpdSlots, nullptr, kF32,
+                             ctx->cfg.refine_fp64 != 0));
     return DI_OK;
 }
 

@@ -24,6 +24,12 @@ void add_launches(long long k);
 constexpr int kMaxLevels = 24;
 constexpr int kMaxUpdSlots = 16;
 
+// Storage of the iterate and right-hand-side arrays a kernel reads or writes:
+// FP32, or FP16 / BF16 (the coarse levels in the 16-bit precision modes; the
+// values match DI_PREC_*).  Arithmetic is FP32 (or FP64 where stated).
+enum Storage { kF32 = 0, kF16 = 1, kBF16 = 2 };
+inline size_t storage_bytes(int stor) { return stor == kF32 ? 4 : 2; }
+
 // cH = 2x2 max pool of c.
 cudaError_t launch_mask_down(const uint8_t* c, int w, int h, uint8_t* cH, cudaStream_t s);
 
@@ -32,10 +38,11 @@ cudaError_t launch_values_down(const uint8_t* c, const float* b, int w, int h, i
                                const uint8_t* cH, float* bH, int modified, cudaStream_t s);
 
 // r = b - A u (r may be null) and per-CTA partial sums of r^2 into
-// partials[ch * nparts + cta]; returns nparts through *nparts.
+// partials[ch * nparts + cta]; returns nparts through *nparts.  f64: the
+// residual formed in FP64 (the finest-grid refinement residual).
 cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_zero,
                             const uint8_t* c, int w, int h, int C, float* r, double* partials,
-                            int* nparts, cudaStream_t s);
+                            int* nparts, cudaStream_t s, bool f64 = false);
 size_t residual_partials_per_channel(int w, int h);
 
 // The same residual + norm with the partial sums in the library's static
@@ -49,18 +56,22 @@ cudaError_t launch_residual_noalloc(const float* u, const float* b, int rhs_zero
 cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, double* out,
                                    cudaStream_t s);
 
-// rH = 4 * mean over children of (b - A u) where cH == 0, else 0.
+// rH = 4 * mean over children of (b - A u) where cH == 0, else 0.  u, b and
+// rH are stored as su, sb, sr (Storage); f64: the children's residuals in FP64.
 cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const uint8_t* c,
-                            int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s);
+                            int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s,
+                            int su = kF32, int sb = kF32, int sr = kF32, bool f64 = false);
 
 // mode 0: u = c ? b : P uH.  mode 1: u += c ? 0 : P uH, max |P uH| (unknown
-// pixels) folded into *maxupd (as float bits, nullable).
+// pixels) folded into *maxupd (as float bits, nullable).  uH and u are stored
+// as suH and su; b is FP32.
 cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, int w, int h,
-                           int C, float* u, int mode, unsigned* maxupd, cudaStream_t s);
+                           int C, float* u, int mode, unsigned* maxupd, cudaStream_t s,
+                           int suH = kF32, int su = kF32);
 
-// u = c ? b : 0 (keep = 0) or u = c ? b : u (keep = 1).
+// u = c ? b : 0 (keep = 0) or u = c ? b : u (keep = 1); u stored as su.
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
-                          cudaStream_t s, int keep = 0);
+                          cudaStream_t s, int keep = 0, int su = kF32);
 
 // One CTA waits, with the block kernel's bounded mbarrier wait (`limit`
 // polls), on a barrier nothing completes; *flag = 1 when the wait ran out.
@@ -91,11 +102,15 @@ inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
 // errflag (nullable): set to 1 when a bounded device-side wait of the FP32
 // 32x32 kernel ran out (its tile copies did not arrive).  step_count
 // (nullable): gains the local CG steps completed, summed over the tasks.
+// stor: storage of u_in, rhs and u_out (kF32, or on the coarse levels of the
+// 16-bit modes the precision's type; 32x32 blocks only); f64: the block
+// residual in FP64.
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev = nullptr, int precision = 0,
-                        unsigned* errflag = nullptr, unsigned long long* step_count = nullptr);
+                        unsigned* errflag = nullptr, unsigned long long* step_count = nullptr,
+                        int stor = kF32, bool f64 = false);
 
 // Global CG smoother: `steps` CG steps on the level's reduced system from the
 // iterate `in`, out = in + correction; restart = 0 continues the previous

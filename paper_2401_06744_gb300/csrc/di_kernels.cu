@@ -71,6 +71,21 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
+// Element access of an array stored as float, FP16 or BF16 (the narrow
+// coarse-level storage); arithmetic is FP32 throughout.
+template <class T> __device__ __forceinline__ float ldf(const T* p);
+template <> __device__ __forceinline__ float ldf<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float ldf<__half>(const __half* p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat162float(*p);
+}
+template <class T> __device__ __forceinline__ void stf(T* p, float v);
+template <> __device__ __forceinline__ void stf<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stf<__half>(__half* p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void stf<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+
 // Block index k = min(g / s, nb - 1) without an integer division: a float
 // estimate from the reciprocal, corrected by one step either way.
 __device__ __forceinline__ int block_of(int g, int s, float inv_s, int nb) {
@@ -182,25 +197,28 @@ __global__ void k_values_down(const uint8_t* __restrict__ c, const float* __rest
 // product")
 // ---------------------------------------------------------------------------
 
+template <bool F64 = false>
 __device__ __forceinline__ float residual_at(const float* __restrict__ u, int zero_u,
                                              const float* __restrict__ b, int rhs_zero,
                                              const uint8_t* __restrict__ c, int w, int h,
                                              int x, int y) {
+    typedef typename std::conditional<F64, double, float>::type R;
     const size_t p = (size_t)y * w + x;
     if (c[p]) return b[p] - (zero_u ? 0.f : u[p]);
-    const float rhs = rhs_zero ? 0.f : b[p];
-    if (zero_u) return rhs;
-    const float uc = u[p];
-    float lu = 0.f;
-    if (x > 0) lu += uc - u[p - 1];
-    if (x < w - 1) lu += uc - u[p + 1];
-    if (y > 0) lu += uc - u[p - w];
-    if (y < h - 1) lu += uc - u[p + w];
-    return rhs - lu;
+    const R rhs = rhs_zero ? (R)0 : (R)b[p];
+    if (zero_u) return (float)rhs;
+    const R uc = u[p];
+    R lu = 0;
+    if (x > 0) lu += uc - (R)u[p - 1];
+    if (x < w - 1) lu += uc - (R)u[p + 1];
+    if (y > 0) lu += uc - (R)u[p - w];
+    if (y < h - 1) lu += uc - (R)u[p + w];
+    return (float)(rhs - lu);
 }
 
 constexpr int kResBX = 32, kResBY = 8;
 
+template <bool F64>
 __global__ void __launch_bounds__(kResBX * kResBY)
 k_residual(const float* __restrict__ u, int zero_u, const float* __restrict__ b, int rhs_zero,
            const uint8_t* __restrict__ c, int w, int h, float* __restrict__ r,
@@ -211,7 +229,7 @@ k_residual(const float* __restrict__ u, int zero_u, const float* __restrict__ b,
     const size_t n = (size_t)w * h;
     float rv = 0.f;
     if (x < w && y < h) {
-        rv = residual_at(u + ch * n, zero_u, b + ch * n, rhs_zero, c, w, h, x, y);
+        rv = residual_at<F64>(u + ch * n, zero_u, b + ch * n, rhs_zero, c, w, h, x, y);
         if (r) r[ch * n + (size_t)y * w + x] = rv;
     }
     // FP32 within the warp, FP64 across the warps and CTAs (fixed order)
@@ -415,19 +433,23 @@ k_reduce_slot(const double* __restrict__ partials, int nparts, double* __restric
 // One thread per coarse cell.  A coarse cell off the coarse mask has four
 // unknown children (max pooling), so their residuals need no mask loads: the
 // 4x4 patch of u around the children is read at once (zero outside the image)
-// and the in-image neighbour count gives the reflecting boundary.
-template <bool VEC>
+// and the in-image neighbour count gives the reflecting boundary.  u is stored
+// as TU, the right-hand side b as TB, rH as TO (FP16/BF16 on the coarse levels
+// in the 16-bit precision modes).  F64: the children's residuals are formed
+// and summed in FP64 (the finest-grid refinement residual) and rounded once.
+template <bool VEC, class TU, class TB, class TO, bool F64>
 __global__ void __launch_bounds__(256)
-k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zero,
-           int w, int h, const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH,
+k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
+           int w, int h, const uint8_t* __restrict__ cH, TO* __restrict__ rH, int wH,
            int hH) {
+    typedef typename std::conditional<F64, double, float>::type R;
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
     const int ch = blockIdx.z;
     if (X >= wH || Y >= hH) return;
     const size_t n = (size_t)w * h, nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
-    if (cH[P]) { rH[ch * nH + P] = 0.f; return; }
-    const float* uc = u + ch * n;
+    if (cH[P]) { stf(rH + ch * nH + P, 0.f); return; }
+    const TU* uc = u + ch * n;
     const int x0 = 2 * X - 1, y0 = 2 * Y - 1;
     float t[4][4];
 #pragma unroll
@@ -442,18 +464,18 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
             t[j][1] = mid.x;
             t[j][2] = mid.y;
             const bool inner = j == 1 || j == 2;
-            t[j][0] = (inner && yok && x0 >= 0) ? uc[(size_t)y * w + x0] : 0.f;
-            t[j][3] = (inner && yok && x0 + 3 < w) ? uc[(size_t)y * w + x0 + 3] : 0.f;
+            t[j][0] = (inner && yok && x0 >= 0) ? ldf(uc + (size_t)y * w + x0) : 0.f;
+            t[j][3] = (inner && yok && x0 + 3 < w) ? ldf(uc + (size_t)y * w + x0 + 3) : 0.f;
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int x = x0 + i;
                 const bool corner = (i == 0 || i == 3) && (j == 0 || j == 3);
-                t[j][i] = (!corner && yok && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
+                t[j][i] = (!corner && yok && x >= 0 && x < w) ? ldf(uc + (size_t)y * w + x) : 0.f;
             }
         }
     }
-    float sum = 0.f;
+    R sum = 0;
     int cnt = 0;
 #pragma unroll
     for (int j = 1; j <= 2; ++j) {
@@ -465,15 +487,16 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
             const int x = x0 + i, y = y0 + j;
             if (x >= w || y >= h) continue;
             const int deg = (x > 0) + (x < w - 1) + (y > 0) + (y < h - 1);
-            const float lu = (float)deg * t[j][i] - (t[j][i - 1] + t[j][i + 1] + t[j - 1][i] + t[j + 1][i]);
-            const float rhs = rhs_zero ? 0.f
-                              : VEC ? (i == 1 ? rb.x : rb.y)
-                                    : b[ch * n + (size_t)y * w + x];
+            const R lu = (R)deg * (R)t[j][i] -
+                         ((R)t[j][i - 1] + (R)t[j][i + 1] + (R)t[j - 1][i] + (R)t[j + 1][i]);
+            const R rhs = rhs_zero ? (R)0
+                          : VEC ? (R)(i == 1 ? rb.x : rb.y)
+                                : (R)ldf(b + ch * n + (size_t)y * w + x);
             sum += rhs - lu;
             ++cnt;
         }
     }
-    rH[ch * nH + P] = 4.f * sum / (float)cnt;
+    stf(rH + ch * nH + P, (float)((R)4 * sum / (R)cnt));
 }
 
 // Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
@@ -485,11 +508,13 @@ k_restrict(const float* __restrict__ u, const float* __restrict__ b, int rhs_zer
 // once, the column blend the same with X - 1 (left child) or X + 1.
 // mode 0: u = c ? b : P uH;  mode 1: u += c ? 0 : P uH (largest |P uH| over
 // the updated pixels into *maxupd).  VEC: each child pair is one 8-byte word
-// of u and b and one 2-byte word of c (w even, aligned base pointers).
-template <bool VEC>
+// of u and b and one 2-byte word of c (w even, aligned base pointers; FP32 u).
+// uH is stored as TC and u as TF (FP16/BF16 on the coarse levels in the
+// 16-bit precision modes); b is FP32.
+template <bool VEC, class TC, class TF>
 __global__ void __launch_bounds__(256)
-k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
-          const uint8_t* __restrict__ c, int w, int h, float* __restrict__ u, int mode,
+k_prolong(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
+          const uint8_t* __restrict__ c, int w, int h, TF* __restrict__ u, int mode,
           unsigned* __restrict__ maxupd) {
     const int X = blockIdx.x * blockDim.x + threadIdx.x;
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -497,16 +522,16 @@ k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict_
     float amax = 0.f;
     if (X < wH && Y < hH) {
         const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
-        const float* e = uH + ch * nH;
+        const TC* e = uH + ch * nH;
         const int Xl = max(X - 1, 0), Xr = min(X + 1, wH - 1);
-        const float* rc = e + (size_t)Y * wH;
-        const float* ru = e + (size_t)max(Y - 1, 0) * wH;
-        const float* rd = e + (size_t)min(Y + 1, hH - 1) * wH;
-        const float cl = rc[Xl], cc = rc[X], cr = rc[Xr];
-        const float ul = ru[Xl], uc = ru[X], ur = ru[Xr];
-        const float dl = rd[Xl], dc = rd[X], dr = rd[Xr];
+        const TC* rc = e + (size_t)Y * wH;
+        const TC* ru = e + (size_t)max(Y - 1, 0) * wH;
+        const TC* rd = e + (size_t)min(Y + 1, hH - 1) * wH;
+        const float cl = ldf(rc + Xl), cc = ldf(rc + X), cr = ldf(rc + Xr);
+        const float ul = ldf(ru + Xl), uc = ldf(ru + X), ur = ldf(ru + Xr);
+        const float dl = ldf(rd + Xl), dc = ldf(rd + X), dr = ldf(rd + Xr);
         const int x = 2 * X;
-        float* ucn = u + ch * n;
+        TF* ucn = u + ch * n;
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
             const int y = 2 * Y + dy;
@@ -536,11 +561,11 @@ k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict_
                     if (x + dx >= w) break;
                     const float v = dx ? a1 : a0;
                     if (c[p + dx]) {
-                        if (mode == 0) ucn[p + dx] = b[ch * n + p + dx];
+                        if (mode == 0) stf(ucn + p + dx, b[ch * n + p + dx]);
                     } else if (mode == 0) {
-                        ucn[p + dx] = v;
+                        stf(ucn + p + dx, v);
                     } else {
-                        ucn[p + dx] += v;
+                        stf(ucn + p + dx, ldf(ucn + p + dx) + v);
                         amax = fmaxf(amax, fabsf(v));
                     }
                 }
@@ -564,13 +589,15 @@ k_prolong(const float* __restrict__ uH, int wH, int hH, const float* __restrict_
 }
 
 // keep == 0: u = c ? b : 0;  keep == 1: u = c ? b : u (a given iterate).
+// u is stored as TU.
+template <class TU>
 __global__ void k_select(const float* __restrict__ b, const uint8_t* __restrict__ c, size_t n,
-                         float* __restrict__ u, int keep) {
+                         TU* __restrict__ u, int keep) {
     const int ch = blockIdx.y;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
-        if (c[i]) u[ch * n + i] = b[ch * n + i];
-        else if (!keep) u[ch * n + i] = 0.f;
+        if (c[i]) stf(u + ch * n + i, b[ch * n + i]);
+        else if (!keep) stf(u + ch * n + i, 0.f);
     }
 }
 
@@ -603,6 +630,17 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     f2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
+}
+
+// r = b - ((deg) u_c - (up + down + left + right)) at one pixel; F64: in FP64
+// (the finest-grid refinement residual), rounded once to FP32.
+template <bool F64>
+__device__ __forceinline__ float res_stencil(float b, float deg, float c, float up, float dn,
+                                             float l, float r) {
+    if (F64)
+        return (float)((double)b - ((double)deg * (double)c -
+                                    ((double)up + (double)dn + (double)l + (double)r)));
+    return b - (deg * c - (up + dn + l + r));
 }
 
 // Partition-of-unity weight of block k (of nb along an axis, stride s,
@@ -1098,6 +1136,7 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 // use_tma: the tiles come by TMA (tm_u over u_in, tm_b over rhs, both FP32
 // [C][h][w] with w a multiple of 4); otherwise by 4-byte cp.async.  errflag:
 // set to 1 if a TMA wait ran out (the CTA then stops).
+template <bool F64>
 __global__ void __launch_bounds__(64, 8)
 k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
           int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
@@ -1327,7 +1366,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                         const float* c0 = tu + (ly + 1) * P + col + 1;
                         const float dv = decltype(interior)::value
                                              ? 2.f : (float)((gy > 0) + (gy < h - 1));
-                        v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                        v = res_stencil<F64>(v, dh + dv, c0[0], c0[-P], c0[P], c0[-1], c0[1]);
                     }
                     rv[e] = v;
                 }
@@ -1521,13 +1560,18 @@ struct Bf16T {
     }
 };
 
-template <class H>
+// TU: storage of u_in, rhs and u_out -- float on the finest level (tiles by
+// 4-byte cp.async, prefetched while the previous task solves), FP16/BF16 on
+// the coarse levels in the 16-bit precision modes (tiles read and widened to
+// FP32 at the start of each task).  F64: the block residual in FP64.
+template <class H, class TU, bool F64>
 __global__ void __launch_bounds__(64, 10)
-k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
+k_oras_2w_h(const TU* __restrict__ u_in, int zero_in, const TU* __restrict__ rhs,
             int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
-            int nbx, int nby, float alpha, int iters, float rtol2, float* __restrict__ u_out,
+            int nbx, int nby, float alpha, int iters, float rtol2, TU* __restrict__ u_out,
             float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
             unsigned long long* __restrict__ step_count) {
+    constexpr bool kAsync = std::is_same<TU, float>::value;
     typedef typename H::T2 T2;
     constexpr int B = 32, NP = 8, TH = Tile2W::TH, P = Tile2W::P, TILE = Tile2W::TILE;
     extern __shared__ float smem[];
@@ -1556,10 +1600,13 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
         return blk < nblk;
     };
     uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
-    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
+    // the u tile (block + one-pixel halo) and the right-hand-side tile of a
+    // task into buffer bs: asynchronous 4-byte copies (FP32 storage) or plain
+    // loads widened to FP32 (16-bit storage)
+    auto tiles = [&](int blk, int ch, int bs) {
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
         if (!zero_in) {
-            const float* src = u_in + ch * n;
+            const TU* src = u_in + ch * n;
             float* dst = s_u + bs * TILE;
             const int gxa = px0 - 1 + lane, gxb = gxa + 32;
             const bool oka = gxa >= 0 && gxa < w;
@@ -1568,24 +1615,42 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
             for (int ty = wi; ty < TH; ty += 2) {
                 const int gy = py0 - 1 + ty;
                 const bool rok = gy >= 0 && gy < h;
-                const float* row = src + (ptrdiff_t)gy * w;
-                cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
-                if (lane < TH - 32)
-                    cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
+                const TU* row = src + (ptrdiff_t)gy * w;
+                if (kAsync) {
+                    cp_async4(dst + ty * P + lane,
+                              reinterpret_cast<const float*>((rok && oka) ? row + gxa : src),
+                              rok && oka);
+                    if (lane < TH - 32)
+                        cp_async4(dst + ty * P + lane + 32,
+                                  reinterpret_cast<const float*>((rok && okb) ? row + gxb : src),
+                                  rok && okb);
+                } else {
+                    dst[ty * P + lane] = (rok && oka) ? ldf(row + gxa) : 0.f;
+                    if (lane < TH - 32) dst[ty * P + lane + 32] = (rok && okb) ? ldf(row + gxb) : 0.f;
+                }
             }
         }
         if (!rhs_zero) {
-            const float* src = rhs + ch * n;
+            const TU* src = rhs + ch * n;
             float* dst = s_b + bs * B * B;
             const int gx = px0 + lane;
 #pragma unroll 4
             for (int ly = wi; ly < B; ly += 2) {
                 const int gy = py0 + ly;
                 const bool ok = gx < w && gy < h;
-                cp_async4(dst + ly * B + lane, ok ? src + (size_t)gy * w + gx : src, ok);
+                if (kAsync)
+                    cp_async4(dst + ly * B + lane,
+                              reinterpret_cast<const float*>(ok ? src + (size_t)gy * w + gx : src),
+                              ok);
+                else
+                    dst[ly * B + lane] = ok ? ldf(src + (size_t)gy * w + gx) : 0.f;
             }
         }
-        cp_async_commit();
+        if (kAsync) cp_async_commit();
+    };
+    auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
+        const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
+        if (kAsync) tiles(blk, ch, bs);
         if (blk != have_blk && lane < 16) {
             const int gy = py0 + row0 + lane;
             if (gy < h) {
@@ -1610,8 +1675,13 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
     unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
     for (int i = 0;; ++i) {
-        cp_async_wait_all();
+        if (kAsync) cp_async_wait_all();
         __syncthreads();
+        if (!kAsync) {
+            // the previous readers of this buffer finished before the barrier
+            tiles(blk, ch, buf);
+            __syncthreads();
+        }
         const uint32_t mlo = nlo, mhi = nhi;
         int nb2, nc2;
         const bool more = task_of(i + 1, nb2, nc2);
@@ -1670,7 +1740,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 if (!zero_in) {
                     const float* c0 = tu + (ly + 1) * P + col + 1;
                     const float dv = (float)((gy > 0) + (gy < h - 1));
-                    v -= (dh + dv) * c0[0] - (c0[-P] + c0[P] + c0[-1] + c0[1]);
+                    v = res_stencil<F64>(v, dh + dv, c0[0], c0[-P], c0[P], c0[-1], c0[1]);
                 }
                 v *= e ? H::hi(keep[k]) : H::lo(keep[k]);
                 rv[k][e] = v;
@@ -1768,7 +1838,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
 
         const int par = (kx & 1) | ((ky & 1) << 1);
         float* plane = planes + ((size_t)par * C + ch) * n;
-        float* uo = u_out + ch * n;
+        TU* uo = u_out + ch * n;
         const bool colok = x0 + col < w;
         const int nsh = shared_per_seam(o), first = shared_first(o);
         int sx_seam = -1, sx_side = 0, sx_j = 0;
@@ -1794,7 +1864,7 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
                 const size_t gp = (size_t)(y0 + ly) * w + x0 + col;
                 const float uold = zero_in ? 0.f : tu[(ly + 1) * P + col + 1];
                 if (d == 1.f) {
-                    uo[gp] = uold + v;
+                    stf(uo + gp, uold + v);
                 } else if (d > 0.f) {
                     const float wyr = s_wy[ly];
                     const bool xfirst = sx_seam < 0 || sx_side == 0;
@@ -1823,10 +1893,11 @@ k_oras_2w_h(const float* __restrict__ u_in, int zero_in, const float* __restrict
 // Shared rows (the interior rows of every horizontal overlap), full width:
 // contributions from the parity planes (two block rows; two block columns
 // where the pixel is also shared along x).
+template <class TU>
 __global__ void __launch_bounds__(256)
-k_combine_rows(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
+k_combine_rows(const float* __restrict__ planes,
                int w, int h, int s, int o, int nbx, int nby, float inv_s,
-               float* __restrict__ u_out) {
+               TU* __restrict__ u_out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ch = blockIdx.z, C = gridDim.z;
     if (x >= w) return;
@@ -1845,16 +1916,17 @@ k_combine_rows(const float* __restrict__ u_in, int zero_in, const float* __restr
     if (nx == 2) acc += pl[(size_t)((kx1 & 1) | (pu << 1)) * cs];
     acc += pl[(size_t)((kx0 & 1) | (pdn << 1)) * cs];
     if (nx == 2) acc += pl[(size_t)((kx1 & 1) | (pdn << 1)) * cs];
-    u_out[ch * n + gp] = acc;
+    stf(u_out + ch * n + gp, acc);
 }
 
 // Pixels shared along x only: thread (j, row) adds the strip entries of the
 // left and right block for pixel j of the seam's shared run in that row (j
 // fastest, so the strip reads of a warp are contiguous).
+template <class TU>
 __global__ void __launch_bounds__(256)
-k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restrict__ planes,
+k_combine_cols(const float* __restrict__ planes,
                int w, int h, int s, int o, int nbx, int nby, float inv_s,
-               float* __restrict__ u_out) {
+               TU* __restrict__ u_out) {
     const int j = threadIdx.x;
     const int y = blockIdx.x * blockDim.y + threadIdx.y;
     const int seam = (int)blockIdx.y + 1;
@@ -1870,7 +1942,7 @@ k_combine_cols(const float* __restrict__ u_in, int zero_in, const float* __restr
     const size_t side = (size_t)C * (nbx - 1) * h * nsh;
     const size_t at = (((size_t)ch * (nbx - 1) + (seam - 1)) * h + y) * nsh + j;
     // the left block's entry already carries u_in
-    u_out[ch * n + (size_t)y * w + x] = strips[at] + strips[at + side];
+    stf(u_out + ch * n + (size_t)y * w + x, strips[at] + strips[at + side]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1985,8 +2057,8 @@ inline dim3 grid2(int w, int h, dim3 blk, int z = 1) {
                 (unsigned)z);
 }
 
-cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
-                           int B, int o, int nbx, int nby, float* u_out, cudaStream_t s);
+cudaError_t launch_combine(float* planes, int w, int h, int C, int B, int o, int nbx, int nby,
+                           float* u_out, cudaStream_t s, int stor);
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -2057,12 +2129,34 @@ int cached_occupancy(const void* kern, int threads, size_t smem, size_t smem_max
 
 // precision: 0 FP32 (tiles by TMA where the image allows it), 1 FP16, 2 BF16
 // local iterates
+// The 16-bit block kernel for iterate type H and storage TU.
+template <class H, class TU, bool F64>
+void run_oras_2w_h(int grid, size_t smem, cudaStream_t s, const float* u_in, int zero_in,
+                   const float* rhs, int rhs_zero, const uint32_t* mbits, int wpr, int w, int h,
+                   int C, int o, int nbx, int nby, float alpha, int iters, float rtol2,
+                   float* u_out, float* planes, unsigned* maxupd, int chan_inner,
+                   unsigned long long* step_count) {
+    k_oras_2w_h<H, TU, F64><<<grid, 64, smem, s>>>(
+        reinterpret_cast<const TU*>(u_in), zero_in, reinterpret_cast<const TU*>(rhs), rhs_zero,
+        mbits, wpr, w, h, C, o, nbx, nby, alpha, iters, rtol2, reinterpret_cast<TU*>(u_out),
+        planes, maxupd, chan_inner, step_count);
+}
+
+template <class H, class TU, bool F64>
+const void* oras_2w_h_fn() {
+    return (const void*)k_oras_2w_h<H, TU, F64>;
+}
+
+// precision: 0 FP32 iterates (tiles by TMA where the image allows it), 1 FP16,
+// 2 BF16 iterates; stor: storage of u_in, rhs, u_out (kF32, or the iterate
+// type on the coarse levels of the 16-bit modes); f64: FP64 block residual.
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                            cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
-                           unsigned long long* step_count) {
+                           unsigned long long* step_count, int stor, bool f64) {
     constexpr int B = 32;
+    if (stor != kF32 && stor != precision) return cudaErrorInvalidValue;
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
     const int nblk = nbx * nby;
@@ -2078,11 +2172,18 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
                   (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
                   (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
         smem = Smem2W::bytes(!rhs_zero);
-        kern = (const void*)k_oras_2w;
+        kern = f64 ? (const void*)k_oras_2w<true> : (const void*)k_oras_2w<false>;
         oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true), &nsm);
     } else {
         smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) * sizeof(float);
-        kern = precision == 1 ? (const void*)k_oras_2w_h<HalfT> : (const void*)k_oras_2w_h<Bf16T>;
+        if (precision == 1)
+            kern = stor != kF32 ? oras_2w_h_fn<HalfT, __half, false>()
+                   : f64        ? oras_2w_h_fn<HalfT, float, true>()
+                                : oras_2w_h_fn<HalfT, float, false>();
+        else
+            kern = stor != kF32 ? oras_2w_h_fn<Bf16T, __nv_bfloat16, false>()
+                   : f64        ? oras_2w_h_fn<Bf16T, float, true>()
+                                : oras_2w_h_fn<Bf16T, float, false>();
         oc = cached_occupancy(kern, 64, smem, ((size_t)Tile2W::FIXED + (size_t)2 * B * B) *
                                                   sizeof(float), &nsm);
     }
@@ -2091,23 +2192,38 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     int grid = chan_inner ? slots : (ntasks < slots ? ntasks : slots);
     if (grid < 1) grid = 1;
     if (ev) record_event(ev[0], s);
-    if (precision == 0)
-        k_oras_2w<<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o,
-                                         nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd,
-                                         chan_inner, tm_u, tm_b, use_tma, errflag, step_count);
-    else if (precision == 1)
-        k_oras_2w_h<HalfT><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
-                                                  C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                  planes, maxupd, chan_inner, step_count);
-    else
-        k_oras_2w_h<Bf16T><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
-                                                  C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                  planes, maxupd, chan_inner, step_count);
+    if (precision == 0) {
+        if (f64)
+            k_oras_2w<true><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
+                                                   C, o, nbx, nby, alpha, iters, rtol2, u_out,
+                                                   planes, maxupd, chan_inner, tm_u, tm_b,
+                                                   use_tma, errflag, step_count);
+        else
+            k_oras_2w<false><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w,
+                                                    h, C, o, nbx, nby, alpha, iters, rtol2, u_out,
+                                                    planes, maxupd, chan_inner, tm_u, tm_b,
+                                                    use_tma, errflag, step_count);
+    } else {
+#define DI_ORAS_H(H, TU, F)                                                                     \
+    run_oras_2w_h<H, TU, F>(grid, smem, s, u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, \
+                            nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd, chan_inner,   \
+                            step_count)
+        if (precision == 1) {
+            if (stor != kF32) DI_ORAS_H(HalfT, __half, false);
+            else if (f64) DI_ORAS_H(HalfT, float, true);
+            else DI_ORAS_H(HalfT, float, false);
+        } else {
+            if (stor != kF32) DI_ORAS_H(Bf16T, __nv_bfloat16, false);
+            else if (f64) DI_ORAS_H(Bf16T, float, true);
+            else DI_ORAS_H(Bf16T, float, false);
+        }
+#undef DI_ORAS_H
+    }
     count();
     if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);
+    return launch_combine(planes, w, h, C, B, o, nbx, nby, u_out, s, stor);
 }
 
 template <int B>
@@ -2149,11 +2265,12 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     if (ev) record_event(ev[1], s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_combine(u_in, zero_in, planes, w, h, C, B, o, nbx, nby, u_out, s);
+    return launch_combine(planes, w, h, C, B, o, nbx, nby, u_out, s, kF32);
 }
 
-cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w, int h, int C,
-                           int B, int o, int nbx, int nby, float* u_out, cudaStream_t s) {
+template <class TU>
+cudaError_t launch_combine_t(float* planes, int w, int h, int C, int B, int o, int nbx, int nby,
+                             TU* u_out, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     // Overlap 2 gives 0/1 weights: no pixel is shared, the combine is empty.
     const int nsh = shared_per_seam(o);
@@ -2161,8 +2278,7 @@ cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w,
     const float inv_s = 1.f / (float)sb;
     if (nsh > 0 && nby > 1) {
         dim3 grid_r((unsigned)((w + 255) / 256), (unsigned)((nby - 1) * nsh), (unsigned)C);
-        k_combine_rows<<<grid_r, 256, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby, inv_s,
-                                             u_out);
+        k_combine_rows<TU><<<grid_r, 256, 0, s>>>(planes, w, h, sb, o, nbx, nby, inv_s, u_out);
         count();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -2172,12 +2288,21 @@ cudaError_t launch_combine(const float* u_in, int zero_in, float* planes, int w,
         const int rows = 256 / nsh > 0 ? 256 / nsh : 1;
         dim3 blk_c((unsigned)nsh, (unsigned)rows);
         dim3 grid_c((unsigned)((h + rows - 1) / rows), (unsigned)nseams, (unsigned)C);
-        k_combine_cols<<<grid_c, blk_c, 0, s>>>(u_in, zero_in, planes, w, h, sb, o, nbx, nby,
-                                               inv_s, u_out);
+        k_combine_cols<TU><<<grid_c, blk_c, 0, s>>>(planes, w, h, sb, o, nbx, nby, inv_s, u_out);
         count();
         e = cudaGetLastError();
     }
     return e;
+}
+
+cudaError_t launch_combine(float* planes, int w, int h, int C, int B, int o, int nbx, int nby,
+                           float* u_out, cudaStream_t s, int stor) {
+    if (stor == kF16)
+        return launch_combine_t(planes, w, h, C, B, o, nbx, nby, reinterpret_cast<__half*>(u_out), s);
+    if (stor == kBF16)
+        return launch_combine_t(planes, w, h, C, B, o, nbx, nby,
+                                reinterpret_cast<__nv_bfloat16*>(u_out), s);
+    return launch_combine_t(planes, w, h, C, B, o, nbx, nby, u_out, s);
 }
 
 }  // namespace
@@ -2211,11 +2336,14 @@ size_t residual_partials_per_channel(int w, int h) {
 
 cudaError_t launch_residual(const float* u, int zero_u, const float* b, int rhs_zero,
                             const uint8_t* c, int w, int h, int C, float* r, double* partials,
-                            int* nparts, cudaStream_t s) {
+                            int* nparts, cudaStream_t s, bool f64) {
     dim3 blk(kResBX, kResBY);
     dim3 grid = grid2(w, h, blk, C);
     *nparts = (int)(grid.x * grid.y);
-    k_residual<<<grid, blk, 0, s>>>(u, zero_u, b, rhs_zero, c, w, h, r, partials);
+    if (f64)
+        k_residual<true><<<grid, blk, 0, s>>>(u, zero_u, b, rhs_zero, c, w, h, r, partials);
+    else
+        k_residual<false><<<grid, blk, 0, s>>>(u, zero_u, b, rhs_zero, c, w, h, r, partials);
     count();
     return cudaGetLastError();
 }
@@ -2296,51 +2424,137 @@ cudaError_t launch_reduce_partials(const double* partials, int nparts, int C, do
     return cudaGetLastError();
 }
 
+template <class TU, class TB, class TO, bool F64>
+void run_restrict(dim3 grid, dim3 blk, cudaStream_t s, const float* u, const float* b,
+                  int rhs_zero, int w, int h, const uint8_t* cH, float* rH, int wH, int hH) {
+    k_restrict<false, TU, TB, TO, F64><<<grid, blk, 0, s>>>(
+        reinterpret_cast<const TU*>(u), reinterpret_cast<const TB*>(b), rhs_zero, w, h, cH,
+        reinterpret_cast<TO*>(rH), wH, hH);
+}
+
 cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const uint8_t* c,
-                            int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s) {
+                            int w, int h, int C, const uint8_t* cH, float* rH, cudaStream_t s,
+                            int su, int sb, int sr, bool f64) {
     (void)c;  // children of an unmasked coarse cell are unknown by construction
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
-    const bool vec = (w % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) |
-                                       reinterpret_cast<uintptr_t>(rhs_zero ? nullptr : b)) %
-                                      8 == 0);
-    if (vec)
-        k_restrict<true><<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH,
-                                                               hH);
-    else
-        k_restrict<false><<<grid2(wH, hH, blk, C), blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH,
-                                                                wH, hH);
+    const dim3 grid = grid2(wH, hH, blk, C);
+    if (rhs_zero) sb = kF32;  // b is not read
+    const bool vec = su == kF32 && sb == kF32 && (w % 2 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(u) |
+                       reinterpret_cast<uintptr_t>(rhs_zero ? nullptr : b)) % 8 == 0);
+    if (su == kF32 && sb == kF32 && sr == kF32) {
+        if (vec && f64)
+            k_restrict<true, float, float, float, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h,
+                                                                            cH, rH, wH, hH);
+        else if (vec)
+            k_restrict<true, float, float, float, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h,
+                                                                             cH, rH, wH, hH);
+        else if (f64)
+            run_restrict<float, float, float, true>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH, hH);
+        else
+            run_restrict<float, float, float, false>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH,
+                                                     hH);
+    } else if (su == kF32 && sb == kF32 && sr == kF16) {  // finest level, FP16 coarse levels
+        if (vec && f64)
+            k_restrict<true, float, float, __half, true><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, reinterpret_cast<__half*>(rH), wH, hH);
+        else if (vec)
+            k_restrict<true, float, float, __half, false><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, reinterpret_cast<__half*>(rH), wH, hH);
+        else if (f64)
+            run_restrict<float, float, __half, true>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH, hH);
+        else
+            run_restrict<float, float, __half, false>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH,
+                                                      hH);
+    } else if (su == kF32 && sb == kF32 && sr == kBF16) {
+        if (vec && f64)
+            k_restrict<true, float, float, __nv_bfloat16, true><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, reinterpret_cast<__nv_bfloat16*>(rH), wH, hH);
+        else if (vec)
+            k_restrict<true, float, float, __nv_bfloat16, false><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, reinterpret_cast<__nv_bfloat16*>(rH), wH, hH);
+        else if (f64)
+            run_restrict<float, float, __nv_bfloat16, true>(grid, blk, s, u, b, rhs_zero, w, h, cH,
+                                                            rH, wH, hH);
+        else
+            run_restrict<float, float, __nv_bfloat16, false>(grid, blk, s, u, b, rhs_zero, w, h, cH,
+                                                             rH, wH, hH);
+    } else if (su == kF16 && (sb == kF16 || rhs_zero) && sr == kF16) {  // coarse levels
+        run_restrict<__half, __half, __half, false>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH,
+                                                    hH);
+    } else if (su == kBF16 && (sb == kBF16 || rhs_zero) && sr == kBF16) {
+        run_restrict<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16, false>(grid, blk, s, u, b,
+                                                                         rhs_zero, w, h, cH, rH,
+                                                                         wH, hH);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     count();
     return cudaGetLastError();
 }
 
+template <bool VEC, class TC, class TF>
+void run_prolong(dim3 grid, dim3 blk, cudaStream_t s, const float* uH, int wH, int hH,
+                 const float* b, const uint8_t* c, int w, int h, float* u, int mode,
+                 unsigned* maxupd) {
+    k_prolong<VEC, TC, TF><<<grid, blk, 0, s>>>(reinterpret_cast<const TC*>(uH), wH, hH, b, c, w,
+                                                h, reinterpret_cast<TF*>(u), mode, maxupd);
+}
+
 cudaError_t launch_prolong(const float* uH, const float* b, const uint8_t* c, int w, int h,
-                           int C, float* u, int mode, unsigned* maxupd, cudaStream_t s) {
+                           int C, float* u, int mode, unsigned* maxupd, cudaStream_t s, int suH,
+                           int su) {
     int wH, hH;
     coarse_dims(w, h, &wH, &hH);
     dim3 blk(32, 8);
     const dim3 grid = grid2(wH, hH, blk, C);  // one thread per coarse cell
-    const bool vec = (w % 2 == 0) && ((reinterpret_cast<uintptr_t>(u) |
-                                       reinterpret_cast<uintptr_t>(b)) % 8 == 0) &&
+    const bool vec = su == kF32 && (w % 2 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(b)) % 8 == 0) &&
                      reinterpret_cast<uintptr_t>(c) % 2 == 0;
-    if (vec)
-        k_prolong<true><<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
-                                             mode == 1 ? maxupd : nullptr);
-    else
-        k_prolong<false><<<grid, blk, 0, s>>>(uH, wH, hH, b, c, w, h, u, mode,
-                                              mode == 1 ? maxupd : nullptr);
+    unsigned* mu = mode == 1 ? maxupd : nullptr;
+    if (su == kF32) {
+        if (suH == kF32) {
+            if (vec) run_prolong<true, float, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u, mode, mu);
+            else run_prolong<false, float, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u, mode, mu);
+        } else if (suH == kF16) {
+            if (vec) run_prolong<true, __half, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u, mode, mu);
+            else run_prolong<false, __half, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u, mode, mu);
+        } else {
+            if (vec)
+                run_prolong<true, __nv_bfloat16, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u,
+                                                        mode, mu);
+            else
+                run_prolong<false, __nv_bfloat16, float>(grid, blk, s, uH, wH, hH, b, c, w, h, u,
+                                                         mode, mu);
+        }
+    } else if (su == kF16 && suH == kF16) {
+        run_prolong<false, __half, __half>(grid, blk, s, uH, wH, hH, b, c, w, h, u, mode, mu);
+    } else if (su == kBF16 && suH == kBF16) {
+        run_prolong<false, __nv_bfloat16, __nv_bfloat16>(grid, blk, s, uH, wH, hH, b, c, w, h, u,
+                                                         mode, mu);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     count();
     return cudaGetLastError();
 }
 
 cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C, float* u,
-                          cudaStream_t s, int keep) {
+                          cudaStream_t s, int keep, int su) {
     const size_t n = (size_t)w * h;
     size_t blocks = (n + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
-    k_select<<<dim3((unsigned)blocks, (unsigned)C), 256, 0, s>>>(b, c, n, u, keep);
+    const dim3 grid((unsigned)blocks, (unsigned)C);
+    if (su == kF16)
+        k_select<__half><<<grid, 256, 0, s>>>(b, c, n, reinterpret_cast<__half*>(u), keep);
+    else if (su == kBF16)
+        k_select<__nv_bfloat16><<<grid, 256, 0, s>>>(b, c, n, reinterpret_cast<__nv_bfloat16*>(u),
+                                                     keep);
+    else
+        k_select<float><<<grid, 256, 0, s>>>(b, c, n, u, keep);
     count();
     return cudaGetLastError();
 }
@@ -2418,13 +2632,14 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
-                        unsigned long long* step_count) {
+                        unsigned long long* step_count, int stor, bool f64) {
     const int wpr = mask_words_per_row(w);
+    if (B != 32 && (stor != kF32 || f64)) return cudaErrorInvalidValue;
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                   iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag,
-                                  step_count);
+                                  step_count, stor, f64);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev, step_count);

@@ -70,7 +70,10 @@ def test_plan_matches_oracle_tiling(di, w, h, B, o):
 
 @pytest.mark.parametrize("kw", [dict(block=12), dict(block=8, overlap=5), dict(alpha=-1.0),
                                 dict(downsample=3), dict(stop_rule=7),
-                                dict(min_cycles=5, max_cycles=2)])
+                                dict(min_cycles=5, max_cycles=2), dict(refine_fp64=2),
+                                # the 16-bit modes store the coarse levels narrow: 32x32
+                                # blocks and the block smoother only
+                                dict(precision=1, block=16), dict(precision=2, smoother=1)])
 def test_plan_rejects_bad_config(di, kw):
     with pytest.raises(di.DiError):
         di.plan(64, 64, 1, **kw)
@@ -80,3 +83,12 @@ def test_plan_rejects_bad_sizes(di):
     for args in [(0, 5, 1), (5, 0, 1), (5, 5, 0), (5, 5, 5)]:
         with pytest.raises(di.DiError):
             di.plan(*args)
+
+
+def test_plan_counts_narrow_coarse_storage(di):
+    # 16-bit modes: the coarse levels' u[0], u[1] and r take 2 bytes per value
+    p32 = di.plan(3840, 2160, 3)
+    p16 = di.plan(3840, 2160, 3, precision=1)
+    coarse = sum(w * h for (w, h) in p32["sizes"][1:]) * 3
+    slack = 3 * 256 * p32["levels"]  # per-buffer alignment
+    assert abs(p32["workspace_bytes"] - p16["workspace_bytes"] - 3 * 2 * coarse) <= slack

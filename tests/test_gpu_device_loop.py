@@ -90,6 +90,10 @@ def test_device_loop_matches_host_loop_stop_rules(di, stop):
     (180, 100, 2, 0.04, "edge", {"pre": 2, "post": 2}),
     # the bench's solver setting
     (640, 360, 3, 0.04, "edge", {"overlap": 2, "local_iters": 10, "local_iters_coarse": 8}),
+    # 16-bit coarse storage and local iterates; FP64 finest-grid residuals
+    (400, 240, 3, 0.01, "edge", {"precision": 1}),
+    (400, 240, 3, 0.04, "uniform", {"precision": 2, "overlap": 4}),
+    (300, 200, 2, 0.02, "edge", {"refine_fp64": 1}),
 ])
 def test_device_loop_matches_host_loop_configurations(di, w, h, C, d, kind, cfg):
     f, c = synth.make_case(w, h, C, d, kind, 1000 + w + h)

@@ -1,6 +1,8 @@
-"""Narrow local iterates (the precision workload): block CG vectors in FP16 or
-BF16 with FP32 dot products, FP32 residuals and FP32 update of u.  The decode
-must still reach 0.05 gray max-abs of the FP64 oracle on every channel; the
+"""The precision workload: block CG vectors in FP16 or BF16 with FP32 dot
+products, the coarse levels' corrections (iterates and restricted residuals)
+stored in the same 16-bit type, FP32 residuals and FP32 update of u on the
+finest grid, and optionally FP64 finest-grid residuals.  The decode must
+still reach 0.05 gray max-abs of the FP64 oracle on every channel; the
 per-channel errors are printed (pytest -s) for the record."""
 import numpy as np
 import pytest
@@ -91,3 +93,53 @@ def test_narrow_oras_iteration_close_to_oracle_cg(di, prec):
     scale = np.abs(ref - u).max()
     assert np.abs(out - ref).max() < 0.05 * scale
     assert np.array_equal(out[:, c == 1], u[:, c == 1])
+
+
+def _decode_cfg(di, f, c, tol, **cfg):
+    with di.Context(**cfg) as ctx:
+        u, st = ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), tol=tol)
+        torch.cuda.synchronize()
+        stats = ctx.stats()
+    return u.cpu().numpy(), st, stats
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+def test_fp64_refinement_residual_reaches_a_tight_target(di, prec):
+    # sixteen fixed V-cycles: with FP64 finest-grid residuals the decode ends
+    # at least as close to the FP64 oracle as with FP32 residuals, far inside
+    # the 0.05 gray bar, in every precision mode
+    code = {"fp32": di.PREC_FP32, "fp16": di.PREC_FP16, "bf16": di.PREC_BF16}[prec]
+    f, c = synth.make_case(640, 360, 3, 0.01, "edge", 4242)
+    ref = oracle.cg_inpaint(f, c)
+    errs = {}
+    for refine in (0, 1):
+        u, st, stats = _decode_cfg(di, f, c, TOL, precision=code, refine_fp64=refine,
+                                   stop_rule=di.STOP_FIXED_CYCLES, max_cycles=16,
+                                   min_cycles=16)
+        assert st == di.OK and stats["cycles"] == 16
+        assert np.array_equal(u[:, c == 1], f[:, c == 1])
+        errs[refine] = float(np.abs(u.astype(np.float64) - ref).max())
+    print(f"{prec}: max error after 16 cycles, FP32 residuals {errs[0]:.2e}, "
+          f"FP64 residuals {errs[1]:.2e}")
+    assert errs[1] <= 0.01
+    assert errs[1] <= errs[0] + 1e-3
+
+
+def test_fp64_restriction_matches_oracle_more_closely(di):
+    # the refinement residual of one restriction (finest level to the first
+    # coarse level) against the oracle's FP64 restriction: FP64 arithmetic
+    # errs no more than FP32
+    g = np.random.default_rng(9)
+    f, c = synth.make_case(250, 130, 2, 0.04, "uniform", 19)
+    u = np.where(c.astype(bool), f, f + g.normal(scale=1e-3, size=f.shape)).astype(np.float32)
+    cH = M.mask_downsample(c)
+    ref = M.restrict_residual(M.residual(u, M.rhs(f, c), c), cH)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+    out = {}
+    for refine in (0, 1):
+        rH = di.restrict_residual(T(u), T(f), T(c), T(cH.astype(np.uint8)), rhs_zero=True,
+                                  fp64=bool(refine))
+        torch.cuda.synchronize()
+        out[refine] = float(np.abs(rH.cpu().numpy() - ref).max())
+    assert out[1] <= out[0] + 1e-7
+    assert out[1] <= 1e-5
