@@ -288,11 +288,29 @@ di_status di_pool_create(const di_config *cfg, int device, int concurrency, di_p
 di_status di_pool_inpaint(di_pool *pool, di_image *imgs, int n, void *stream);
 void di_pool_destroy(di_pool *pool);
 
-/* Time every (block, overlap) pair of the given lists on the sample images
- * (`reps` timed passes after one warm-up pass, CUDA events) and return the
- * fastest configuration whose decodes all converge, with its mean time per
- * pass.  Pairs that are not valid configurations are skipped.  Returns
- * DI_ERR_NOT_CONVERGED if no pair qualifies. */
+/* Search space of the autotuner: candidate values per parameter (an empty
+ * list, count 0, keeps the base configuration's value).  blocks: B;
+ * overlaps: o; local_iters: CG steps of each local solve on the finest level;
+ * smoothing: the V-cycle type V(k, k) -- k pre- and k post-smoothing steps;
+ * schedules: DI_SCHED_REDUCED_FMG or DI_SCHED_FULL_FMG (the cycle scheme). */
+typedef struct {
+    const int *blocks;      int nblocks;
+    const int *overlaps;    int noverlaps;
+    const int *local_iters; int nlocal_iters;
+    const int *smoothing;   int nsmoothing;
+    const int *schedules;   int nschedules;
+} di_tune_space;
+
+/* Time every combination of the search space on the sample images (`reps`
+ * timed passes after one warm-up pass, CUDA events) and return the fastest
+ * configuration whose decodes all converge, with its mean time per pass.
+ * Combinations that are not valid configurations are skipped.  Returns
+ * DI_ERR_NOT_CONVERGED if none qualifies. */
+di_status di_autotune_space(const di_config *base, int device, const di_image *sample, int n,
+                            const di_tune_space *space, int reps, di_config *best,
+                            double *best_ms);
+
+/* di_autotune_space over (block, overlap) pairs only. */
 di_status di_autotune(const di_config *base, int device, const di_image *sample, int n,
                       const int *blocks, int nblocks, const int *overlaps, int noverlaps,
                       int reps, di_config *best, double *best_ms);

@@ -65,6 +65,14 @@ class di_image(ctypes.Structure):
                 ("u", ctypes.c_void_p), ("status", ctypes.c_int), ("cycles", ctypes.c_int)]
 
 
+class di_tune_space(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.POINTER(ctypes.c_int)), ("nblocks", ctypes.c_int),
+                ("overlaps", ctypes.POINTER(ctypes.c_int)), ("noverlaps", ctypes.c_int),
+                ("local_iters", ctypes.POINTER(ctypes.c_int)), ("nlocal_iters", ctypes.c_int),
+                ("smoothing", ctypes.POINTER(ctypes.c_int)), ("nsmoothing", ctypes.c_int),
+                ("schedules", ctypes.POINTER(ctypes.c_int)), ("nschedules", ctypes.c_int)]
+
+
 class di_request_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
@@ -101,6 +109,9 @@ _SIGS = {
     "di_autotune": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I,
                          ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _I, _I,
                          ctypes.POINTER(di_config), ctypes.POINTER(ctypes.c_double)]),
+    "di_autotune_space": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I,
+                               ctypes.POINTER(di_tune_space), _I, ctypes.POINTER(di_config),
+                               ctypes.POINTER(ctypes.c_double)]),
     "di_server_create": (_I, [ctypes.POINTER(di_config), _I, _I, ctypes.c_longlong,
                               ctypes.POINTER(_P)]),
     "di_server_submit": (_I, [_P, _P, _P, _I, _I, _I, _F, _P, ctypes.POINTER(ctypes.c_longlong)]),
@@ -450,20 +461,34 @@ class Pool:
             pass
 
 
-def autotune(items, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=2, device=None, **config):
-    """Fastest converging (block, overlap) on the sample (f, c, tol) list:
-    returns (config dict, ms per pass)."""
+def autotune(items, blocks=(8, 16, 32), overlaps=(1, 2, 4), local_iters=(), smoothing=(),
+             schedules=(), reps=2, device=None, **config):
+    """Fastest converging configuration on the sample (f, c, tol) list over
+    block x overlap x local CG steps x V(k, k) smoothing x schedule (empty
+    lists keep the base value): returns (config dict, ms per pass)."""
     if device is None:
         device = torch.cuda.current_device()
     base = make_config(**config)
     arr, _ = _images(items)
-    bl = (ctypes.c_int * len(blocks))(*blocks)
-    ov = (ctypes.c_int * len(overlaps))(*overlaps)
+
+    def arr_of(v):
+        v = list(v)
+        return (ctypes.c_int * max(1, len(v)))(*v), len(v)
+
+    sp = di_tune_space()
+    keep = []
+    for name, vals in (("blocks", blocks), ("overlaps", overlaps), ("local_iters", local_iters),
+                       ("smoothing", smoothing), ("schedules", schedules)):
+        a, k = arr_of(vals)
+        keep.append(a)
+        setattr(sp, name, ctypes.cast(a, ctypes.POINTER(ctypes.c_int)))
+        setattr(sp, "n" + name, k)
     best = di_config()
     ms = ctypes.c_double()
-    _check(load().di_autotune(ctypes.byref(base), int(device), arr, len(items), bl, len(blocks),
-                              ov, len(overlaps), int(reps), ctypes.byref(best), ctypes.byref(ms)))
-    return {k: getattr(best, k) for k, _ in di_config._fields_ }, ms.value
+    _check(load().di_autotune_space(ctypes.byref(base), int(device), arr, len(items),
+                                    ctypes.byref(sp), int(reps), ctypes.byref(best),
+                                    ctypes.byref(ms)))
+    return {k: getattr(best, k) for k, _ in di_config._fields_}, ms.value
 
 
 class Server:

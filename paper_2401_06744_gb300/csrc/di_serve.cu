@@ -164,16 +164,56 @@ extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image
 // Autotuner over block size and overlap
 // ---------------------------------------------------------------------------
 
-extern "C" di_status di_autotune(const di_config* base, int device, const di_image* sample, int n,
-                                 const int* blocks, int nblocks, const int* overlaps,
-                                 int noverlaps, int reps, di_config* best, double* best_ms) {
-    if (!sample || n < 1 || !best || !blocks || nblocks < 1 || !overlaps || noverlaps < 1 ||
-        reps < 1)
+namespace {
+
+// Mean time of `reps` passes over the sample with configuration c (after one
+// warm-up pass, which allocates the workspace and captures the graphs); a
+// negative result if a decode fails or does not converge.
+double time_config(const di_config& c, int device, const di_image* sample, int n, int reps,
+                   cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+    di_plan_info plan;
+    if (di_plan(&c, 1, 1, 1, &plan) != DI_OK) return -1.0;  // not a valid configuration
+    di_ctx* ctx = nullptr;
+    if (di_create(&c, device, &ctx) != DI_OK) return -1.0;
+    bool ok = true;
+    for (int i = 0; i < n && ok; ++i)
+        ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width, sample[i].height,
+                        sample[i].channels, sample[i].tol, sample[i].u, s) == DI_OK;
+    double t = 0.0;
+    for (int r = 0; r < reps && ok; ++r) {
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < n && ok; ++i)
+            ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width, sample[i].height,
+                            sample[i].channels, sample[i].tol, sample[i].u, s) == DI_OK;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t += ms;
+    }
+    di_destroy(ctx);
+    return ok ? t / reps : -1.0;
+}
+
+}  // namespace
+
+extern "C" di_status di_autotune_space(const di_config* base, int device, const di_image* sample,
+                                       int n, const di_tune_space* space, int reps,
+                                       di_config* best, double* best_ms) {
+    if (!sample || n < 1 || !best || !space || reps < 1) return DI_ERR_INVALID_ARG;
+    if ((space->nblocks > 0 && !space->blocks) || (space->noverlaps > 0 && !space->overlaps) ||
+        (space->nlocal_iters > 0 && !space->local_iters) ||
+        (space->nsmoothing > 0 && !space->smoothing) ||
+        (space->nschedules > 0 && !space->schedules) || space->nblocks < 0 ||
+        space->noverlaps < 0 || space->nlocal_iters < 0 || space->nsmoothing < 0 ||
+        space->nschedules < 0)
         return DI_ERR_INVALID_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return DI_ERR_CUDA;
     di_config b;
     std::memset(&b, 0, sizeof b);
     if (base) b = *base;
+    // an empty list keeps the base configuration's value
+    auto count = [](int k) { return k > 0 ? k : 1; };
     double best_t = 1e300;
     bool found = false;
     cudaStream_t s;
@@ -181,48 +221,43 @@ extern "C" di_status di_autotune(const di_config* base, int device, const di_ima
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int bi = 0; bi < nblocks; ++bi) {
-        for (int oi = 0; oi < noverlaps; ++oi) {
-            di_config c = b;
-            c.block = blocks[bi];
-            c.overlap = overlaps[oi];
-            di_plan_info plan;
-            if (di_plan(&c, 1, 1, 1, &plan) != DI_OK) continue;  // invalid (B, o) pair
-            di_ctx* ctx = nullptr;
-            if (di_create(&c, device, &ctx) != DI_OK) continue;
-            bool ok = true;
-            // warm-up (allocates the workspace), then timed repetitions
-            for (int i = 0; i < n && ok; ++i)
-                ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width, sample[i].height,
-                                sample[i].channels, sample[i].tol, sample[i].u, s) == DI_OK;
-            double t = 0.0;
-            for (int r = 0; r < reps && ok; ++r) {
-                cudaEventRecord(e0, s);
-                for (int i = 0; i < n && ok; ++i)
-                    ok = di_inpaint(ctx, sample[i].f, sample[i].c, sample[i].width,
-                                    sample[i].height, sample[i].channels, sample[i].tol,
-                                    sample[i].u, s) == DI_OK;
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                t += ms;
-            }
-            di_destroy(ctx);
-            if (!ok) continue;  // did not converge or failed: not a candidate
-            t /= reps;
-            if (t < best_t) {
-                best_t = t;
-                *best = c;
-                found = true;
-            }
-        }
-    }
+    for (int bi = 0; bi < count(space->nblocks); ++bi)
+        for (int oi = 0; oi < count(space->noverlaps); ++oi)
+            for (int ki = 0; ki < count(space->nlocal_iters); ++ki)
+                for (int vi = 0; vi < count(space->nsmoothing); ++vi)
+                    for (int si = 0; si < count(space->nschedules); ++si) {
+                        di_config c = b;
+                        if (space->nblocks) c.block = space->blocks[bi];
+                        if (space->noverlaps) c.overlap = space->overlaps[oi];
+                        if (space->nlocal_iters) c.local_iters = space->local_iters[ki];
+                        if (space->nsmoothing) c.pre = c.post = space->smoothing[vi];
+                        if (space->nschedules) c.schedule = space->schedules[si];
+                        const double t = time_config(c, device, sample, n, reps, s, e0, e1);
+                        if (t < 0.0) continue;  // invalid, failed or not converged
+                        if (t < best_t) {
+                            best_t = t;
+                            *best = c;
+                            found = true;
+                        }
+                    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     if (best_ms) *best_ms = found ? best_t : -1.0;
     return found ? DI_OK : DI_ERR_NOT_CONVERGED;
+}
+
+extern "C" di_status di_autotune(const di_config* base, int device, const di_image* sample, int n,
+                                 const int* blocks, int nblocks, const int* overlaps,
+                                 int noverlaps, int reps, di_config* best, double* best_ms) {
+    if (!blocks || nblocks < 1 || !overlaps || noverlaps < 1) return DI_ERR_INVALID_ARG;
+    di_tune_space sp;
+    std::memset(&sp, 0, sizeof sp);
+    sp.blocks = blocks;
+    sp.nblocks = nblocks;
+    sp.overlaps = overlaps;
+    sp.noverlaps = noverlaps;
+    return di_autotune_space(base, device, sample, n, &sp, reps, best, best_ms);
 }
 
 // ---------------------------------------------------------------------------

@@ -192,3 +192,22 @@ def test_pool_reuse_matches_solo(di):
             assert all(s == di.OK for s in sts), sts
             for (f, c), u in zip(cases, outs):
                 assert np.array_equal(u.cpu().numpy(), _solo(di, f, c))
+
+
+def test_autotune_over_local_steps_cycle_type_and_schedule(di):
+    # the autotuner's full search space: block x overlap x local CG steps x
+    # V(k, k) cycle type x schedule; the winner is one of the candidates and
+    # decodes the sample within the bar
+    sample_cases = [_case(320, 192, 3, 0.04, "edge", 31), _case(256, 256, 1, 0.02, "uniform", 32)]
+    sample = [(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), TOL)
+              for f, c in sample_cases]
+    best, ms = di.autotune(sample, blocks=(32,), overlaps=(2, 4), local_iters=(6, 10),
+                           smoothing=(1, 2), schedules=(di.SCHED_REDUCED_FMG, di.SCHED_FULL_FMG),
+                           reps=1)
+    assert ms > 0
+    assert best["block"] == 32 and best["overlap"] in (2, 4)
+    assert best["local_iters"] in (6, 10) and best["pre"] == best["post"] in (1, 2)
+    assert best["schedule"] in (di.SCHED_REDUCED_FMG, di.SCHED_FULL_FMG)
+    cfg = {k: best[k] for k in ("block", "overlap", "local_iters", "pre", "post", "schedule")}
+    for f, c in sample_cases:
+        _check_oracle(_solo(di, f, c, **cfg), f, c)
