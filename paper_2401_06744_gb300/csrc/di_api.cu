@@ -474,7 +474,7 @@ bool capture_vcycle(di_ctx* ctx, Sched& S) {
         return false;
     }
     const di_profile p0 = ctx->prof;
-    const long long k0 = launch_count();
+    const long long k0 = thread_launch_count();
     cudaStream_t s = S.s;
     ctx->g_pairs = 0;
     if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
@@ -493,7 +493,7 @@ bool capture_vcycle(di_ctx* ctx, Sched& S) {
     ctx->capturing = false;
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
-    ctx->g_kernels = launch_count() - k0;
+    ctx->g_kernels = thread_launch_count() - k0;
     add_launches(-ctx->g_kernels);  // captured, not launched
     ctx->g_oras = ctx->prof.oras_l0_launches - p0.oras_l0_launches;
     ctx->g_pxch = ctx->prof.oras_l0_pixel_channels - p0.oras_l0_pixel_channels;
@@ -589,11 +589,11 @@ bool capture_body(cudaStream_t s, cudaGraph_t body, long long* kern, Fn&& fn) {
     if (cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed) != cudaSuccess)
         return false;
-    const long long k0 = launch_count();
+    const long long k0 = thread_launch_count();
     const bool ok = fn();
     cudaGraph_t out = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &out);
-    const long long k = launch_count() - k0;
+    const long long k = thread_launch_count() - k0;
     add_launches(-k);
     if (kern) *kern += k;
     return ok && e == cudaSuccess;
@@ -674,7 +674,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
         return false;
     }
     dg = DecodeGraph();
-    const long long k0 = launch_count();
+    const long long k0 = thread_launch_count();
     StopParams sp;
     sp.rule = cfg.stop_rule;
     sp.nslots = cfg.pre + 1 + cfg.post;
@@ -771,7 +771,7 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
     S.root = 0;
     S.Leff = L;
     // everything left after the bodies took theirs is the fixed part
-    dg.k_pre = launch_count() - k0;
+    dg.k_pre = thread_launch_count() - k0;
     add_launches(-dg.k_pre);
     if (ok) {
         step = "instantiate";

@@ -16,8 +16,10 @@ inline int axis_blocks_decl(int n, int B, int o) {
     return nb < 1 ? 1 : nb;
 }
 
-// Kernels enqueued by the launch wrappers below (process-wide counter).
+// Kernels enqueued by the launch wrappers below (process-wide counter), and
+// those the calling thread enqueued (for counting the kernels of a capture).
 long long launch_count();
+long long thread_launch_count();
 // Adjust the launch counter (graph replays add their kernels, captures that
 // launched nothing take theirs back).
 void add_launches(long long k);

@@ -46,14 +46,24 @@
 namespace di {
 
 static std::atomic<long long> g_launches{0};
+// the calling thread's own launches: captures count their kernels with it, so
+// that decodes finishing on other threads meanwhile do not enter the count
+static thread_local long long t_launches = 0;
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
-void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
+void add_launches(long long k) {
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    t_launches += k;
+}
 
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-inline void count(int k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+inline void count(int k = 1) {
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+    t_launches += k;
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
