@@ -271,12 +271,38 @@ typedef struct {
     int cycles; /* out: V-cycles used */
 } di_image;
 
-/* Decode n images with up to `concurrency` slots (0 = 4), largest first.
+/* Decode n images.  When the configuration allows the batched form (see
+ * di_batch_create) the batch runs as one di_batch graph; otherwise the images
+ * are spread over up to `concurrency` worker slots (0 = 4), largest first.
  * The work starts after what is already queued on `stream` and the call
  * returns when every image is done (`stream` then also waits for it).
  * Returns DI_OK, or the first non-OK image status. */
 di_status di_inpaint_batch(const di_config *cfg, int device, di_image *imgs, int n,
                            int concurrency, void *stream);
+
+/* The batched form: the n images of a batch (device pointers, uneven sizes,
+ * 1..4 channels, each with its own tol) decoded together, with ONE kernel
+ * launch per step of the method over every image -- the pyramid level by
+ * level, the cascade level by level, then per V(1,1)-cycle one restriction,
+ * one block-kernel and one prolongation launch per level -- and the whole
+ * batch captured once into one CUDA graph whose V-cycle loop (a WHILE node)
+ * ends when every image's stop rule holds; an image drops out of the cycles
+ * as soon as its own rule holds.  The block kernel is persistent over a task
+ * list of (image, block, channel) units of all images.  di_batch_create
+ * plans the workspace of these images and captures the graph (the buffers,
+ * sizes and tolerances become part of it; their contents may change between
+ * runs).  Configurations: 32x32 blocks, overlap 2, FP32, the reduced FMG
+ * with V(1,1)-cycles, the error-estimate or fixed-cycle stop rule, images of
+ * at least two levels; other configurations return DI_ERR_INVALID_ARG (use
+ * di_pool_inpaint).  Each image's result equals its single-image decode. */
+typedef struct di_batch di_batch;
+di_status di_batch_create(const di_config *cfg, int device, const di_image *imgs, int n,
+                          di_batch **out);
+/* One decode of the batch: imgs must be the images it was created for; their
+ * status and cycles are filled.  Waits for the work; returns DI_OK or the
+ * first non-OK image status. */
+di_status di_batch_run(di_batch *b, di_image *imgs, int n, void *stream);
+void di_batch_destroy(di_batch *b);
 
 /* A persistent pool of `concurrency` decoder slots (0 = 4), each with its own
  * context, stream and host thread, reused by every di_pool_inpaint call, so

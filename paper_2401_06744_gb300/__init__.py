@@ -16,9 +16,9 @@ from ._lib import (  # noqa: F401
     SMOOTH_ORAS, SMOOTH_CG, GRAPH_ON, GRAPH_OFF, START_CASCADE, START_GIVEN,
     STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
     exported_symbols, load, mask_downsample, plan, prolong, residual_norm_noalloc,
-    restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server, Pool,
+    restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server, Pool, Batch,
     selftest_bounded_wait)
 
 __all__ = ["Context", "DiError", "load", "plan", "mask_downsample", "values_downsample",
-           "residual_norm_noalloc", "inpaint_batch", "autotune", "Server", "Pool",
+           "residual_norm_noalloc", "inpaint_batch", "autotune", "Server", "Pool", "Batch",
            "restrict_residual", "prolong", "status_string", "exported_symbols", "LIB_PATH"]

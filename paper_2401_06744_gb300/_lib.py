@@ -103,6 +103,10 @@ _SIGS = {
     "di_reset_profile": (_I, [_P]),
     "di_inpaint_batch": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I, _I,
                               _P]),
+    "di_batch_create": (_I, [ctypes.POINTER(di_config), _I, ctypes.POINTER(di_image), _I,
+                             ctypes.POINTER(_P)]),
+    "di_batch_run": (_I, [_P, ctypes.POINTER(di_image), _I, _P]),
+    "di_batch_destroy": (None, [_P]),
     "di_pool_create": (_I, [ctypes.POINTER(di_config), _I, _I, ctypes.POINTER(_P)]),
     "di_pool_inpaint": (_I, [_P, ctypes.POINTER(di_image), _I, _P]),
     "di_pool_destroy": (None, [_P]),
@@ -421,6 +425,48 @@ def selftest_bounded_wait(limit=4096, device=None, stream=None) -> int:
     if device is None:
         device = torch.cuda.current_device()
     return load().di_selftest_bounded_wait(int(device), int(limit), _stream(stream))
+
+
+class Batch:
+    """The batched form (di_batch_*): a fixed list of (f, c, tol[, out]) images
+    decoded together, one kernel launch per step over every image, the whole
+    batch one CUDA graph.  run() decodes the images' current contents."""
+
+    def __init__(self, items, device=None, **config):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.config = make_config(**config)
+        self._arr, self.outputs = _images(items)
+        self._keep = list(items)
+        self._n = len(self.outputs)
+        h = _P()
+        self._h = None
+        _check(load().di_batch_create(ctypes.byref(self.config), int(device), self._arr, self._n,
+                                      ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        """Decode the batch; returns (outputs, statuses, cycles)."""
+        load().di_batch_run(self._h, self._arr, self._n, _stream(stream))
+        return (self.outputs, [self._arr[i].status for i in range(self._n)],
+                [self._arr[i].cycles for i in range(self._n)])
+
+    def close(self):
+        if self._h:
+            load().di_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Pool:

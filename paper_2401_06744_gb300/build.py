@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdi.so")
-SOURCES = ["di_kernels.cu", "di_api.cu", "di_serve.cu"]
+SOURCES = ["di_kernels.cu", "di_api.cu", "di_serve.cu", "di_batch.cu"]
 HEADERS = [os.path.join(CSRC, "di_internal.h"), os.path.join(ROOT, "include", "di.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -172,6 +172,75 @@ cudaError_t launch_plan(const unsigned long long* counts, StopState* st, const P
 cudaError_t launch_stop(unsigned* upd, StopState* st, const StopParams& p,
                         unsigned long long h_loop, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched form: one launch per step over the images of a batch.  Each image's
+// part of a launch is a segment: its level's size and buffers, its first CTA
+// (grid kernels) or first block unit (the block kernel) in the launch, and
+// when it takes part, which depends on the image's levels in use, the start
+// level of its cascade and whether its decode has converged -- values the
+// batch's plan and stop kernels keep on the device.
+// ---------------------------------------------------------------------------
+
+enum BatchWhen {
+    kWhenAlways = 0,         // pyramid steps
+    kWhenTopEq = 1,          // cascade start: level == the image's start level
+    kWhenCoarsestStart = 2,  // cascade start on the coarsest level (all levels in use)
+    kWhenBelowTop = 3,       // cascade: level below the image's start level
+    kWhenCycle = 4           // V-cycle step: not converged and level < levels in use
+};
+
+enum BatchKind {  // grid kernels of the batched form
+    kBMaskDown = 0, kBValuesDown = 1, kBPack = 2, kBSelect = 3, kBRestrict = 4, kBProlong = 5
+};
+
+struct BatchSeg {
+    int first;             // first CTA (grid kernels) or block unit (block kernel)
+    int gx, gy;            // grid kernels: CTAs along x and y per channel plane
+    int w, h, C;           // level size (the fine level for restriction and prolongation)
+    int img, level, when;  // image, level and participation (BatchWhen)
+    int L;                 // the image's pyramid depth
+    const void* in0;       // mask_down, values_down, pack: c; restrict: u; prolong: uH; block: u_in
+    const void* in1;       // values_down: b; select: b; restrict: b; prolong: b; block: rhs
+    const void* in2;       // values_down: cH; select: c; restrict: cH; prolong: c
+    void* out0;            // mask_down: cH; values_down: bH; select: u; restrict: rH; prolong, block: u
+    void* out1;            // select: a second u written alike (nullable)
+    const uint32_t* mbits; // pack: bits out; block: the level's packed mask
+    unsigned* maxupd;      // prolong, block: the image's update slot (nullable)
+    unsigned long long* counter;  // pack: the image's unknown count of this level
+    int zero_in, rhs_zero, iters, nbx, nby, wpr, mode, keep;
+    float rtol2;
+};
+
+// Per-image decode state of a batch (device arrays of n images).
+struct BatchState {
+    int* leff;   // levels in use
+    int* top;    // start level of the cascade (-1: none)
+    int* done;   // 1 once converged, failed or not to be solved
+    StopState* st;
+    unsigned* upd;  // [n][kMaxUpdSlots + 1]
+    unsigned long long* counts;  // [n][kMaxLevels + 1]
+    const float* tol;  // stop-rule target per image
+};
+
+// A batched grid kernel over nseg segments (segs in device memory, ordered by
+// first) covering nctas CTAs.
+cudaError_t launch_batch_grid(int kind, const BatchSeg* segs, int nseg, int nctas,
+                              const BatchState& bs, cudaStream_t s);
+// The batched block kernel (32x32 blocks, 0/1 weights) over nunits block units.
+cudaError_t launch_batch_oras(const BatchSeg* segs, int nseg, int nunits, int o, float alpha,
+                              const BatchState& bs, cudaStream_t s);
+// Plan of every image (levels in use, cascade start, initial state); L[i]
+// and n0[i] are the images' pyramid depths and pixel counts (device arrays).
+cudaError_t launch_batch_plan(int n, const int* L, const unsigned long long* n0,
+                              const BatchState& bs, cudaStream_t s);
+// The stop test of every image still running; the loop handle is set to 0
+// once none is.
+cudaError_t launch_batch_stop(int n, const StopParams& p, const BatchState& bs,
+                              unsigned long long h_loop, cudaStream_t s);
+// CTAs per channel plane of the grid kernels for a level of w x h (2D kinds:
+// 32 x 8 threads; pack and select: 256 threads).
+void batch_grid_dims(int kind, int w, int h, int* gx, int* gy);
+
 // Host-side geometry shared with the kernels.
 inline int axis_blocks(int n, int B, int o) {
     const int s = B - o;

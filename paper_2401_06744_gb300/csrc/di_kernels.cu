@@ -127,10 +127,10 @@ __device__ __forceinline__ int axis_contrib(int g, int s, int o, int nb, int& k0
 // Mask pyramid (Section 4.3)
 // ---------------------------------------------------------------------------
 
-__global__ void k_mask_down(const uint8_t* __restrict__ c, int w, int h,
-                            uint8_t* __restrict__ cH, int wH, int hH) {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void mask_down_body(const uint8_t* __restrict__ c, int w, int h,
+                            uint8_t* __restrict__ cH, int wH, int hH, int bx, int by) {
+    const int X = bx * blockDim.x + threadIdx.x;
+    const int Y = by * blockDim.y + threadIdx.y;
     if (X >= wH || Y >= hH) return;
     const int x = 2 * X, y = 2 * Y;
     const bool x1 = x + 1 < w, y1 = y + 1 < h;
@@ -145,12 +145,17 @@ __global__ void k_mask_down(const uint8_t* __restrict__ c, int w, int h,
     cH[(size_t)Y * wH + X] = m ? 1 : 0;
 }
 
+__global__ void k_mask_down(const uint8_t* __restrict__ c, int w, int h,
+                            uint8_t* __restrict__ cH, int wH, int hH) {
+    mask_down_body(c, w, h, cH, wH, hH, blockIdx.x, blockIdx.y);
+}
+
 // One coarse cell: weights of its (up to four) fine children.
-__global__ void k_values_down(const uint8_t* __restrict__ c, const float* __restrict__ b,
+__device__ __forceinline__ void values_down_body(const uint8_t* __restrict__ c, const float* __restrict__ b,
                               int w, int h, int C, const uint8_t* __restrict__ cH,
-                              float* __restrict__ bH, int wH, int hH, int modified) {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+                              float* __restrict__ bH, int wH, int hH, int modified, int bx, int by) {
+    const int X = bx * blockDim.x + threadIdx.x;
+    const int Y = by * blockDim.y + threadIdx.y;
     if (X >= wH || Y >= hH) return;
     const size_t n = (size_t)w * h, nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
     if (!cH[P]) {
@@ -200,6 +205,12 @@ __global__ void k_values_down(const uint8_t* __restrict__ c, const float* __rest
             if (wt[k] != 0.f) num += wt[k] * bc[idx[k]];
         bH[ch * nH + P] = num * inv;
     }
+}
+
+__global__ void k_values_down(const uint8_t* __restrict__ c, const float* __restrict__ b,
+                              int w, int h, int C, const uint8_t* __restrict__ cH,
+                              float* __restrict__ bH, int wH, int hH, int modified) {
+    values_down_body(c, b, w, h, C, cH, bH, wH, hH, modified, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,14 +459,13 @@ k_reduce_slot(const double* __restrict__ partials, int nparts, double* __restric
 // in the 16-bit precision modes).  F64: the children's residuals are formed
 // and summed in FP64 (the finest-grid refinement residual) and rounded once.
 template <bool VEC, class TU, class TB, class TO, bool F64>
-__global__ void __launch_bounds__(256)
-k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
+__device__ __forceinline__ void restrict_body(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
            int w, int h, const uint8_t* __restrict__ cH, TO* __restrict__ rH, int wH,
-           int hH) {
+           int hH, int bx, int by, int bz) {
     typedef typename std::conditional<F64, double, float>::type R;
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int ch = blockIdx.z;
+    const int X = bx * blockDim.x + threadIdx.x;
+    const int Y = by * blockDim.y + threadIdx.y;
+    const int ch = bz;
     if (X >= wH || Y >= hH) return;
     const size_t n = (size_t)w * h, nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
     if (cH[P]) { stf(rH + ch * nH + P, 0.f); return; }
@@ -509,6 +519,15 @@ k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
     stf(rH + ch * nH + P, (float)((R)4 * sum / (R)cnt));
 }
 
+template <bool VEC, class TU, class TB, class TO, bool F64>
+__global__ void __launch_bounds__(256)
+k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
+           int w, int h, const uint8_t* __restrict__ cH, TO* __restrict__ rH, int wH,
+           int hH) {
+    restrict_body<VEC, TU, TB, TO, F64>(u, b, rhs_zero, w, h, cH, rH, wH, hH, blockIdx.x, blockIdx.y,
+                                        blockIdx.z);
+}
+
 // Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
 // coarse cell, 3/16 of each of the two edge neighbours of the parent on the
 // child's side and 1/16 of the diagonal one (coarse indices clamped at the
@@ -522,13 +541,12 @@ k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
 // uH is stored as TC and u as TF (FP16/BF16 on the coarse levels in the
 // 16-bit precision modes); b is FP32.
 template <bool VEC, class TC, class TF>
-__global__ void __launch_bounds__(256)
-k_prolong(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
+__device__ __forceinline__ void prolong_body(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
           const uint8_t* __restrict__ c, int w, int h, TF* __restrict__ u, int mode,
-          unsigned* __restrict__ maxupd) {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
-    const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int ch = blockIdx.z;
+          unsigned* __restrict__ maxupd, int bx, int by, int bz) {
+    const int X = bx * blockDim.x + threadIdx.x;
+    const int Y = by * blockDim.y + threadIdx.y;
+    const int ch = bz;
     float amax = 0.f;
     if (X < wH && Y < hH) {
         const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
@@ -598,17 +616,32 @@ k_prolong(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b
     }
 }
 
+template <bool VEC, class TC, class TF>
+__global__ void __launch_bounds__(256)
+k_prolong(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
+          const uint8_t* __restrict__ c, int w, int h, TF* __restrict__ u, int mode,
+          unsigned* __restrict__ maxupd) {
+    prolong_body<VEC, TC, TF>(uH, wH, hH, b, c, w, h, u, mode, maxupd, blockIdx.x, blockIdx.y,
+                              blockIdx.z);
+}
+
 // keep == 0: u = c ? b : 0;  keep == 1: u = c ? b : u (a given iterate).
 // u is stored as TU.
 template <class TU>
-__global__ void k_select(const float* __restrict__ b, const uint8_t* __restrict__ c, size_t n,
-                         TU* __restrict__ u, int keep) {
-    const int ch = blockIdx.y;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void select_body(const float* __restrict__ b, const uint8_t* __restrict__ c, size_t n,
+                         TU* __restrict__ u, int keep, int bx, int nbx, int ch_) {
+    const int ch = ch_;
+    for (size_t i = (size_t)bx * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)nbx * blockDim.x) {
         if (c[i]) stf(u + ch * n + i, b[ch * n + i]);
         else if (!keep) stf(u + ch * n + i, 0.f);
     }
+}
+
+template <class TU>
+__global__ void k_select(const float* __restrict__ b, const uint8_t* __restrict__ c, size_t n,
+                         TU* __restrict__ u, int keep) {
+    select_body<TU>(b, c, n, u, keep, blockIdx.x, gridDim.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -695,14 +728,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // warp per word (lane = column), four words in flight per warp, persistent
 // warps; *unknown (nullable) gains the number of unknown pixels, with one
 // atomic per CTA.
-__global__ void __launch_bounds__(256)
-k_pack_mask(const uint8_t* __restrict__ c, int w, int h, uint32_t* __restrict__ bits, int wpr,
-            unsigned long long* __restrict__ unknown) {
+__device__ __forceinline__ void pack_mask_body(const uint8_t* __restrict__ c, int w, int h, uint32_t* __restrict__ bits, int wpr,
+            unsigned long long* __restrict__ unknown, int bx, int nbx) {
     const int lane = threadIdx.x & 31;
     const int total = h * wpr;
-    const int nwarps = (int)gridDim.x * (int)(blockDim.x >> 5);
+    const int nwarps = (int)nbx * (int)(blockDim.x >> 5);
     unsigned unk = 0;
-    for (int wid = (int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    for (int wid = (int)bx * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
          wid < total; wid += 4 * nwarps) {
         bool known[4];
 #pragma unroll
@@ -735,6 +767,12 @@ k_pack_mask(const uint8_t* __restrict__ c, int w, int h, uint32_t* __restrict__ 
             if (a) atomicAdd(unknown, a);
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_pack_mask(const uint8_t* __restrict__ c, int w, int h, uint32_t* __restrict__ bits, int wpr,
+            unsigned long long* __restrict__ unknown) {
+    pack_mask_body(c, w, h, bits, wpr, unknown, blockIdx.x, gridDim.x);
 }
 
 // One ORAS iteration, one warp per (block, channel) task.
@@ -2052,6 +2090,458 @@ __global__ void k_stop(unsigned* __restrict__ upd, StopState* __restrict__ st, S
     cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: the step kernels over the segments of a batch (one image's
+// level each).  A CTA finds its segment by binary search over the segments'
+// first CTAs, skips it if the image does not take part in this step, and runs
+// the single-image body on the segment's buffers.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int find_seg(const BatchSeg* __restrict__ segs, int nseg, int g) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool seg_active(int when, int img, int level, int L,
+                                           const BatchState& bs) {
+    switch (when) {
+        case kWhenTopEq: return bs.top[img] == level;
+        case kWhenCoarsestStart: return bs.leff[img] == L;
+        case kWhenBelowTop: return level < bs.top[img];
+        case kWhenCycle: return !bs.done[img] && level < bs.leff[img];
+        default: return true;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+k_batch_grid(const BatchSeg* __restrict__ segs, int nseg, BatchState bs) {
+    const BatchSeg& sg = segs[find_seg(segs, nseg, (int)blockIdx.x)];
+    if (!seg_active(sg.when, sg.img, sg.level, sg.L, bs)) return;  // uniform per CTA
+    const int local = (int)blockIdx.x - sg.first;
+    const int w = sg.w, h = sg.h;
+    const int wH = (w + 1) / 2, hH = (h + 1) / 2;
+    if (KIND == kBPack) {
+        pack_mask_body(static_cast<const uint8_t*>(sg.in0), w, h, const_cast<uint32_t*>(sg.mbits),
+                       sg.wpr, sg.counter, local, sg.gx);
+        return;
+    }
+    if (KIND == kBSelect) {
+        const int ch = local / sg.gx, bx = local - ch * sg.gx;
+        const size_t n = (size_t)w * h;
+        select_body<float>(static_cast<const float*>(sg.in1), static_cast<const uint8_t*>(sg.in2),
+                           n, static_cast<float*>(sg.out0), sg.keep, bx, sg.gx, ch);
+        if (sg.out1)
+            select_body<float>(static_cast<const float*>(sg.in1),
+                               static_cast<const uint8_t*>(sg.in2), n,
+                               static_cast<float*>(sg.out1), sg.keep, bx, sg.gx, ch);
+        return;
+    }
+    const int plane = sg.gx * sg.gy;
+    const int bz = local / plane, rem = local - bz * plane;
+    const int by = rem / sg.gx, bx = rem - by * sg.gx;
+    if (KIND == kBMaskDown)
+        mask_down_body(static_cast<const uint8_t*>(sg.in0), w, h, static_cast<uint8_t*>(sg.out0),
+                       wH, hH, bx, by);
+    else if (KIND == kBValuesDown)
+        values_down_body(static_cast<const uint8_t*>(sg.in0), static_cast<const float*>(sg.in1),
+                         w, h, sg.C, static_cast<const uint8_t*>(sg.in2),
+                         static_cast<float*>(sg.out0), wH, hH, sg.mode, bx, by);
+    else if (KIND == kBRestrict)
+        restrict_body<false, float, float, float, false>(
+            static_cast<const float*>(sg.in0), static_cast<const float*>(sg.in1), sg.rhs_zero, w,
+            h, static_cast<const uint8_t*>(sg.in2), static_cast<float*>(sg.out0), wH, hH, bx, by,
+            bz);
+    else if (KIND == kBProlong)
+        prolong_body<false, float, float>(static_cast<const float*>(sg.in0), wH, hH,
+                                          static_cast<const float*>(sg.in1),
+                                          static_cast<const uint8_t*>(sg.in2), w, h,
+                                          static_cast<float*>(sg.out0), sg.mode, sg.maxupd, bx,
+                                          by, bz);
+}
+
+// The block kernel over the block units of a batch: a unit is one 32x32
+// block of one image's level with all its channels back to back; CTAs are
+// persistent and stride over the units of every image in the launch, skipping
+// the units of images that do not take part.  Tiles by 4-byte cp.async
+// (prefetched while the previous task solves); 0/1 partition weights
+// (overlap 2: each pixel is written by the one block whose weight is 1
+// there).  Otherwise the local problem, the CG and the write are those of
+// k_oras_2w.
+__global__ void __launch_bounds__(64, 8)
+k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, float alpha,
+             BatchState bs) {
+    constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
+    constexpr int TILE = Smem2W::USTRIDE;
+    extern __shared__ float smem_raw[];
+    float* const smem = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    float* const s_u = smem;
+    float* const s_wy = smem + Smem2W::WY;
+    float* const s_b = smem + Smem2W::RHS;
+    __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
+
+    const int t = threadIdx.x;
+    const int lane = t & 31, wi = t >> 5;
+    const int col = lane;
+    const int row0 = 16 * wi;
+    const int s = B - o;
+    const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
+
+    // a task: a unit's segment and block, and a channel
+    struct Task {
+        int seg, blk, ch;
+    };
+    // the next active task after (unit g, channel ch): the next channel, else
+    // the next unit of this CTA whose image takes part
+    auto advance = [&](int& g, Task& tk) {
+        if (tk.seg >= 0 && ++tk.ch < segs[tk.seg].C) return true;
+        for (g = g < 0 ? (int)blockIdx.x : g + (int)gridDim.x; g < nunits; g += (int)gridDim.x) {
+            const int si = find_seg(segs, nseg, g);
+            const BatchSeg& sg = segs[si];
+            if (!seg_active(sg.when, sg.img, sg.level, sg.L, bs)) continue;
+            tk.seg = si;
+            tk.blk = g - sg.first;
+            tk.ch = 0;
+            return true;
+        }
+        return false;
+    };
+    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    auto prefetch = [&](const Task& tk, int bs_, bool new_blk) {
+        const BatchSeg& sg = segs[tk.seg];
+        const int w = sg.w, h = sg.h, nbx = sg.nbx;
+        const size_t n = (size_t)w * h;
+        const int px0 = (tk.blk % nbx) * s, py0 = (tk.blk / nbx) * s;
+        if (!sg.zero_in) {
+            const float* src = static_cast<const float*>(sg.in0) + tk.ch * n;
+            float* dst = s_u + bs_ * TILE;
+            const int gxa = px0 - 1 + lane, gxb = gxa + 32;
+            const bool oka = gxa >= 0 && gxa < w;
+            const bool okb = lane < TH - 32 && gxb < w;
+#pragma unroll 2
+            for (int ty = wi; ty < TH; ty += 2) {
+                const int gy = py0 - 1 + ty;
+                const bool rok = gy >= 0 && gy < h;
+                const float* row = src + (ptrdiff_t)gy * w;
+                cp_async4(dst + ty * P + lane, (rok && oka) ? row + gxa : src, rok && oka);
+                if (lane < TH - 32)
+                    cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
+            }
+        }
+        if (!sg.rhs_zero) {
+            const float* src = static_cast<const float*>(sg.in1) + tk.ch * n;
+            float* dst = s_b + bs_ * Smem2W::BSTRIDE;
+            const int gx = px0 + lane;
+#pragma unroll 4
+            for (int ly = wi; ly < B; ly += 2) {
+                const int gy = py0 + ly;
+                const bool ok = gx < w && gy < h;
+                cp_async4(dst + ly * PB + lane, ok ? src + (size_t)gy * w + gx : src, ok);
+            }
+        }
+        cp_async_commit();
+        if (new_blk && lane < 16) {
+            const int gy = py0 + row0 + lane;
+            if (gy < h) {
+                const uint32_t* row = sg.mbits + (size_t)gy * sg.wpr + (px0 >> 5);
+                nlo = __ldg(row);
+                nhi = __ldg(row + 1);
+            } else {
+                nlo = nhi = 0xffffffffu;
+            }
+        }
+    };
+
+    int g = -1;
+    Task cur{-1, 0, 0};
+    if (!advance(g, cur)) return;  // block-uniform
+    prefetch(cur, 0, true);
+    int buf = 0;
+    int cur_seg = -1, cur_blk = -1;
+    f2 ndg[NP], keep[NP];
+    f2 ml2 = 0ull, mr2 = 0ull;
+    float wx = 0.f, dh = 0.f;
+    int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
+    uint32_t rows_w = 0;
+    float vmax = 0.f;
+    unsigned* vmax_slot = nullptr;
+
+    for (;;) {
+        cp_async_wait_all();
+        __syncthreads();
+        const uint32_t mlo = nlo, mhi = nhi;
+        Task nxt = cur;
+        int g2 = g;
+        const bool more = advance(g2, nxt);
+        if (more) prefetch(nxt, buf ^ 1, nxt.seg != cur.seg || nxt.blk != cur.blk);
+
+        const BatchSeg& sg = segs[cur.seg];
+        const int w = sg.w, h = sg.h, C = sg.C, nbx = sg.nbx, nby = sg.nby;
+        const int zero_in = sg.zero_in, rhs_zero = sg.rhs_zero;
+        const size_t n = (size_t)w * h;
+        if (cur.seg != cur_seg) {
+            // the image changes: flush the previous image's largest update
+            if (vmax_slot) {
+                const float m = warp_max(vmax);
+                if (lane == 0 && m > 0.f) atomicMax(vmax_slot, __float_as_uint(m));
+            }
+            vmax = 0.f;
+            vmax_slot = sg.maxupd;
+            cur_seg = cur.seg;
+            cur_blk = -1;
+        }
+        if (cur.blk != cur_blk) {
+            cur_blk = cur.blk;
+            kx = cur.blk % nbx;
+            ky = cur.blk / nbx;
+            x0 = kx * s;
+            y0 = ky * s;
+            const int bw = min(B, w - x0);
+            bh = min(B, h - y0);
+            const uint32_t rowm = __funnelshift_r(mlo, mhi, x0 & 31);
+            uint32_t mb = 0;
+#pragma unroll
+            for (int rr = 0; rr < 16; ++rr) {
+                const uint32_t v = __shfl_sync(kFull, rowm, rr);
+                mb |= ((v >> col) & 1u) << rr;
+            }
+            const int gx = x0 + col;
+            const float hc = (col > 0 ? 1.f : (gx > 0 ? alpha : 0.f)) +
+                             (col + 1 < bw ? 1.f : (gx < w - 1 ? alpha : 0.f));
+            dh = (float)((gx > 0) + (gx < w - 1));
+            const float ml = col > 0 ? 1.f : 0.f, mr = col < B - 1 ? 1.f : 0.f;
+            ml2 = pk(ml, ml);
+            mr2 = pk(mr, mr);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                float vc[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                    vc[e] = (ly > 0 ? 1.f : (gy > 0 ? alpha : 0.f)) +
+                            (ly + 1 < bh ? 1.f : (gy < h - 1 ? alpha : 0.f));
+                }
+                ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
+                keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
+            }
+            wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
+            const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);
+            if (t < B) s_wy[t] = wyl;
+            rows_w = __ballot_sync(kFull, wyl > 0.f && lane < bh);
+        }
+        const float* tu = s_u + buf * TILE;
+        const float* tb = s_b + buf * Smem2W::BSTRIDE;
+
+        f2 x[NP], r[NP], p[NP], q[NP];
+        f2 acc0 = 0ull, acc1 = 0ull;
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            float rv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int ly = row0 + k + 8 * e, gy = y0 + ly;
+                float v = rhs_zero ? 0.f : tb[ly * PB + col];
+                if (!zero_in) {
+                    const float* c0 = tu + (ly + 1) * P + col + 1;
+                    const float dv = (float)((gy > 0) + (gy < h - 1));
+                    v = res_stencil<false>(v, dh + dv, c0[0], c0[-P], c0[P], c0[-1], c0[1]);
+                }
+                rv[e] = v;
+            }
+            r[k] = mul2(pk(rv[0], rv[1]), keep[k]);
+            p[k] = r[k];
+            x[k] = 0ull;
+            if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+            else acc0 = fma2(r[k], r[k], acc0);
+        }
+        acc0 = add2(acc0, acc1);
+        s_seam[wi][lane] = wi == 0 ? hi2(r[NP - 1]) : lo2(r[0]);
+        float part = warp_sum(lo2(acc0) + hi2(acc0));
+        if (lane == 0) s_red2[wi] = part;
+        __syncthreads();
+        float rr = s_red2[0] + s_red2[1];
+        float pb = s_seam[wi ^ 1][lane];
+        const float rtol2 = sg.rtol2;
+        const float rr_stop = rtol2 >= 0.f ? fmaxf(rtol2, 1e-14f) * rr
+                                           : fmaxf(1e-14f * rr, -rtol2);
+        const int iters = sg.iters;
+        for (int it = 0; it < iters; ++it) {
+            if (!(rr > rr_stop)) break;  // rr is identical in both warps
+            const f2 pu = wi == 0 ? pk(0.f, lo2(p[NP - 1])) : pk(pb, lo2(p[NP - 1]));
+            const f2 pd = wi == 0 ? pk(hi2(p[0]), pb) : pk(hi2(p[0]), 0.f);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                const f2 left = __shfl_up_sync(kFull, p[k], 1);
+                const f2 right = __shfl_down_sync(kFull, p[k], 1);
+                const f2 up = k > 0 ? p[k - 1] : pu;
+                const f2 dn = k < NP - 1 ? p[k + 1] : pd;
+                f2 nbs = add2(up, dn);
+                nbs = fma2(ml2, left, nbs);
+                nbs = fma2(mr2, right, nbs);
+                const f2 qk = mul2(fma2(ndg[k], p[k], nbs), keep[k]);
+                q[k] = qk;
+                if (k & 1) acc1 = fma2(p[k], qk, acc1);
+                else acc0 = fma2(p[k], qk, acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red1[wi] = part;
+            __syncthreads();
+            const float pq = -(s_red1[0] + s_red1[1]);
+            if (!(pq > 0.f) || pq == INFINITY) break;
+            const float a = __fdividef(rr, pq);
+            const f2 a2 = pk(a, a);
+            acc0 = 0ull;
+            acc1 = 0ull;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                x[k] = fma2(a2, p[k], x[k]);
+                r[k] = fma2(a2, q[k], r[k]);
+                if (k & 1) acc1 = fma2(r[k], r[k], acc1);
+                else acc0 = fma2(r[k], r[k], acc0);
+            }
+            acc0 = add2(acc0, acc1);
+            s_seam[wi][lane] = wi == 0 ? hi2(r[NP - 1]) : lo2(r[0]);
+            part = warp_sum(lo2(acc0) + hi2(acc0));
+            if (lane == 0) s_red2[wi] = part;
+            __syncthreads();
+            const float rrn = s_red2[0] + s_red2[1];
+            const float beta = __fdividef(rrn, rr);
+            rr = rrn;
+            const f2 b2 = pk(beta, beta);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) p[k] = fma2(b2, p[k], r[k]);
+            pb = fmaf(beta, pb, s_seam[wi ^ 1][lane]);
+        }
+
+        // 0/1 weights: each pixel is written by the one block whose weight is
+        // 1 there, with u_in added
+        float* uo = static_cast<float*>(sg.out0) + cur.ch * n;
+        if (x0 + col < w && wx > 0.f) {
+            float* uol = uo + (size_t)(y0 + row0) * w + x0 + col;
+            const float* tol = tu + (row0 + 1) * P + col + 1;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const int j = k + 8 * e;
+                    if (!((rows_w >> (row0 + j)) & 1u)) continue;
+                    const float v = e ? hi2(x[k]) : lo2(x[k]);
+                    uol[(size_t)j * w] = (zero_in ? 0.f : tol[j * P]) + v;
+                    vmax = fmaxf(vmax, fabsf(v));
+                }
+            }
+        }
+        if (!more) break;
+        g = g2;
+        cur = nxt;
+        buf ^= 1;
+    }
+    if (vmax_slot) {
+        vmax = warp_max(vmax);
+        if (lane == 0 && vmax > 0.f) atomicMax(vmax_slot, __float_as_uint(vmax));
+    }
+}
+
+// Plan of every image of a batch: levels in use, the cascade's start level
+// and the initial stop state (as k_plan for one image).
+__global__ void k_batch_plan(int n, const int* __restrict__ Ls,
+                             const unsigned long long* __restrict__ n0s, BatchState bs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int L = Ls[i];
+    const unsigned long long* counts = bs.counts + (size_t)i * (kMaxLevels + 1);
+    const unsigned long long unk0 = counts[1];
+    int Leff = L;
+    for (int l = 1; l < L; ++l)
+        if (counts[1 + l] == 0) { Leff = l; break; }
+    if (unk0 == 0) Leff = 0;
+    StopState* st = bs.st + i;
+    st->cycles = 0;
+    st->converged = 0;
+    st->levels_used = Leff;
+    st->est = 0.f;
+    st->prevU = -1.f;
+    st->prevQ = -1.f;
+    st->unknowns = unk0;
+    for (int k = 0; k < kMaxChannels; ++k) st->rel[k] = -1.f;
+    const bool empty = unk0 == n0s[i];
+    st->status = empty ? DI_ERR_EMPTY_MASK : DI_OK;
+    bs.leff[i] = empty ? 0 : Leff;
+    bs.top[i] = empty ? -1 : (Leff == 0 ? 0 : (Leff == L ? L - 1 : Leff));
+    bs.done[i] = (empty || Leff == 0) ? 1 : 0;
+    if (!empty && Leff == 0) st->converged = 1;
+    unsigned* upd = bs.upd + (size_t)i * (kMaxUpdSlots + 1);
+    for (int k = 0; k <= kMaxUpdSlots; ++k) upd[k] = 0u;
+}
+
+// The stop test of every image still running (k_stop's rule per image); the
+// loop continues while any image runs.
+__global__ void k_batch_stop(int n, StopParams p, BatchState bs, cudaGraphConditionalHandle h) {
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    int running = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (bs.done[i]) continue;
+        StopState* st = bs.st + i;
+        unsigned* upd = bs.upd + (size_t)i * (kMaxUpdSlots + 1);
+        const int cycles = st->cycles + 1;
+        st->cycles = cycles;
+        bool stop = false;
+        if (upd[kMaxUpdSlots]) {
+            st->status = DI_ERR_TIMEOUT;
+            stop = true;
+        } else if (p.rule == DI_STOP_ERROR_ESTIMATE) {
+            float U = 0.f;
+            for (int k = 0; k < p.nslots; ++k) U += __uint_as_float(upd[k]);
+            float prevU = st->prevU, prevQ = st->prevQ, est;
+            if (!isfinite(U)) {
+                est = INFINITY;
+                prevU = -1.f;
+                prevQ = -1.f;
+            } else if (prevU > 0.f) {
+                const float qk = __fdiv_rn(U, prevU);
+                const float q = prevQ > qk ? prevQ : qk;
+                prevQ = qk;
+                est = q < 1.f ? __fdiv_rn(__fmul_rn(U, q), __fsub_rn(1.f, q)) : INFINITY;
+            } else {
+                est = U;
+            }
+            prevU = U;
+            if (U == 0.f) est = 0.f;
+            st->prevU = prevU;
+            st->prevQ = prevQ;
+            st->est = est;
+            if (cycles >= p.min_cycles && est <= 0.5f * bs.tol[i]) {
+                st->converged = 1;
+                stop = true;
+            }
+        } else if (cycles >= p.max_cycles) {  // fixed number of cycles
+            st->converged = 1;
+            stop = true;
+        }
+        if (!stop && cycles >= p.max_cycles) {
+            st->status = DI_ERR_NOT_CONVERGED;
+            stop = true;
+        }
+        for (int k = 0; k < p.nslots; ++k) upd[k] = 0u;
+        if (stop) bs.done[i] = 1;
+        else running = 1;
+    }
+    if (running) atomicOr(&s_any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, s_any ? 1u : 0u);
+}
+
 // Timing event on s; inside a stream capture it becomes an event record node
 // of the graph (recorded by every replay).
 void record_event(cudaEvent_t e, cudaStream_t s) {
@@ -2671,6 +3161,73 @@ cudaError_t launch_plan(const unsigned long long* counts, StopState* st, const P
 cudaError_t launch_stop(unsigned* upd, StopState* st, const StopParams& p,
                         unsigned long long h_loop, cudaStream_t s) {
     k_stop<<<1, 32, 0, s>>>(upd, st, p, (cudaGraphConditionalHandle)h_loop);
+    count();
+    return cudaGetLastError();
+}
+
+void batch_grid_dims(int kind, int w, int h, int* gx, int* gy) {
+    if (kind == kBPack) {  // persistent warps over the packed words
+        const long long words = (long long)h * mask_words_per_row(w);
+        long long b = (words + 31) / 32;
+        if (b > 152) b = 152;
+        *gx = (int)(b < 1 ? 1 : b);
+        *gy = 1;
+    } else if (kind == kBSelect) {
+        size_t b = ((size_t)w * h + 255) / 256;
+        if (b > 1024) b = 1024;
+        *gx = (int)(b < 1 ? 1 : b);
+        *gy = 1;
+    } else if (kind == kBRestrict || kind == kBProlong || kind == kBMaskDown ||
+               kind == kBValuesDown) {  // one thread per coarse cell, 32 x 8 per CTA
+        const int wH = (w + 1) / 2, hH = (h + 1) / 2;
+        *gx = (wH + 31) / 32;
+        *gy = (hH + 7) / 8;
+    } else {
+        *gx = *gy = 1;
+    }
+}
+
+cudaError_t launch_batch_grid(int kind, const BatchSeg* segs, int nseg, int nctas,
+                              const BatchState& bs, cudaStream_t s) {
+    if (nctas < 1 || nseg < 1) return cudaSuccess;
+    const dim3 blk2(32, 8), blk1(256);
+    switch (kind) {
+        case kBMaskDown: k_batch_grid<kBMaskDown><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
+        case kBValuesDown: k_batch_grid<kBValuesDown><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
+        case kBPack: k_batch_grid<kBPack><<<nctas, blk1, 0, s>>>(segs, nseg, bs); break;
+        case kBSelect: k_batch_grid<kBSelect><<<nctas, blk1, 0, s>>>(segs, nseg, bs); break;
+        case kBRestrict: k_batch_grid<kBRestrict><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
+        case kBProlong: k_batch_grid<kBProlong><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_oras(const BatchSeg* segs, int nseg, int nunits, int o, float alpha,
+                              const BatchState& bs, cudaStream_t s) {
+    if (nunits < 1 || nseg < 1) return cudaSuccess;
+    if (shared_per_seam(o) != 0) return cudaErrorInvalidValue;  // 0/1 weights only
+    int nsm = 0;
+    const size_t smem = Smem2W::bytes(true);
+    const int oc = cached_occupancy((const void*)k_batch_oras, 64, smem, smem, &nsm);
+    int grid = nsm * oc;
+    if (grid > nunits) grid = nunits;
+    k_batch_oras<<<grid, 64, smem, s>>>(segs, nseg, nunits, o, alpha, bs);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_plan(int n, const int* L, const unsigned long long* n0,
+                              const BatchState& bs, cudaStream_t s) {
+    k_batch_plan<<<(n + 127) / 128, 128, 0, s>>>(n, L, n0, bs);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stop(int n, const StopParams& p, const BatchState& bs,
+                              unsigned long long h_loop, cudaStream_t s) {
+    k_batch_stop<<<1, 256, 0, s>>>(n, p, bs, (cudaGraphConditionalHandle)h_loop);
     count();
     return cudaGetLastError();
 }

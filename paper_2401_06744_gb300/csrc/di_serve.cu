@@ -150,6 +150,14 @@ extern "C" di_status di_inpaint_batch(const di_config* cfg, int device, di_image
                                       int concurrency, void* stream) {
     if (!imgs || n < 0 || concurrency < 0) return DI_ERR_INVALID_ARG;
     if (n == 0) return DI_OK;
+    // the batched form: one graph, one launch per step over every image
+    di_batch* bt = nullptr;
+    if (di_batch_create(cfg, device, imgs, n, &bt) == DI_OK) {
+        cudaStream_t caller = static_cast<cudaStream_t>(stream);
+        di_status st = di_batch_run(bt, imgs, n, caller);
+        di_batch_destroy(bt);
+        return st;
+    }
     int P = concurrency > 0 ? concurrency : 4;
     if (P > n) P = n;
     di_pool* pool = nullptr;

@@ -211,3 +211,60 @@ def test_autotune_over_local_steps_cycle_type_and_schedule(di):
     cfg = {k: best[k] for k in ("block", "overlap", "local_iters", "pre", "post", "schedule")}
     for f, c in sample_cases:
         _check_oracle(_solo(di, f, c, **cfg), f, c)
+
+
+def test_batched_form_one_graph_matches_solo_and_oracle(di):
+    # the batched form: a batch of uneven sizes and channel counts decoded as
+    # one graph with one launch per step over every image; every image equals
+    # its single-image decode bit for bit (the same arithmetic in the same
+    # order) and, checked on the oracle, is within the bar
+    g = np.random.default_rng(44)
+    sizes = [(96, 64), (160, 90), (257, 129), (320, 180), (512, 512), (640, 360)]
+    cases = []
+    for i in range(10):
+        w, h = sizes[i % len(sizes)]
+        d = float(g.uniform(0.005, 0.10))
+        cases.append(_case(w, h, int(g.integers(1, 4)), d, "edge" if i % 2 else "uniform",
+                           600 + i))
+    # one fully known image and one with a single known pixel ride along
+    f1, c1 = _case(128, 96, 2, 0.05, "uniform", 650)
+    cases.append((f1, np.ones_like(c1)))
+    f2, c2 = _case(200, 120, 1, 0.05, "uniform", 651)
+    one = np.zeros_like(c2)
+    one[60, 100] = 1
+    cases.append((f2, one))
+    cfg = dict(block=32, overlap=2, local_iters=10, local_iters_coarse=8, max_cycles=64)
+    items = [(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), TOL) for f, c in cases]
+    with di.Batch(items, **cfg) as bt:
+        for rep in range(2):  # the graph replays on the same buffers
+            outs, sts, cyc = bt.run()
+            torch.cuda.synchronize()
+            assert all(s == di.OK for s in sts), sts
+            for k, ((f, c), u) in enumerate(zip(cases, outs)):
+                u = u.cpu().numpy()
+                if rep == 0:
+                    assert np.array_equal(u, _solo(di, f, c, **cfg)), k
+                    if k < 6 or k >= 10:
+                        _check_oracle(u, f, c)
+
+
+def test_batched_form_config3_images_against_solo(di):
+    # the 32-image mix of the batched workload (512x512 ... 3840x2160, 1-3
+    # channels, 1-10 %) as one graph: bit-identical to the single-image
+    # decodes of a sample and within the bar for one image of every size
+    specs = _config3_images()
+    cases = [_case(*s) for s in specs]
+    cfg = dict(block=32, overlap=2, local_iters=10, local_iters_coarse=8)
+    items = [(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), TOL) for f, c in cases]
+    with di.Batch(items, **cfg) as bt:
+        outs, sts, cyc = bt.run()
+        torch.cuda.synchronize()
+    assert all(s == di.OK for s in sts), sts
+    seen = set()
+    for k, ((f, c), u, sp) in enumerate(zip(cases, outs, specs)):
+        u = u.cpu().numpy()
+        if k % 8 == 0:
+            assert np.array_equal(u, _solo(di, f, c, **cfg)), k
+        if sp[:2] not in seen:
+            seen.add(sp[:2])
+            _check_oracle(u, f, c)
