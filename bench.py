@@ -954,27 +954,52 @@ def _compare_configs(args, di, dev, s):
     cases = [synth.make_case(*sp) for sp in specs]
     items = [(torch.from_numpy(f).to(dev), torch.from_numpy(c).to(dev), TOL) for f, c in cases]
     small = [it for it, sp in zip(items, specs) if sp[0] == 512][:2] or items[:1]
-    best, tune_ms = di.autotune(small, blocks=(8, 16, 32), overlaps=(1, 2, 4), reps=1)
+    # autotuner over block x overlap x local CG steps x V(k,k) x schedule on
+    # two of the batch's images
+    best, tune_ms = di.autotune(small, blocks=(8, 16, 32), overlaps=(1, 2, 4),
+                                local_iters=(6, 8, 10), smoothing=(1, 2),
+                                schedules=(di.SCHED_REDUCED_FMG, di.SCHED_FULL_FMG), reps=1,
+                                local_iters_coarse=args.local_iters_coarse)
+    tuned = {k: best[k] for k in ("block", "overlap", "local_iters", "pre", "post", "schedule")}
     pxch = sum(sp[0] * sp[1] * sp[2] for sp in specs)
-    with di.Pool(concurrency=4, block=best["block"], overlap=best["overlap"]) as pool:
+    # the pool of concurrent single-image decoders with the tuned setting
+    with di.Pool(concurrency=4, local_iters_coarse=args.local_iters_coarse, **tuned) as pool:
         outs, sts, cyc = pool.inpaint(items)  # warm-up: workspaces, graphs
         ms = _median_ms(lambda: pool.inpaint(items), s, 3)
         outs, sts, cyc = pool.inpaint(items)
     torch.cuda.synchronize()
-    errs = []
-    for (f, c), u, sp in zip(cases, outs, specs):
-        if sp[0] == 512:
-            errs.append(err_of(u.cpu().numpy(), oracle.cg_inpaint(f, c)))
+    # the batched form: one graph, one launch per step over all 32 images
+    bcfg = dict(block=32, overlap=2, local_iters=args.local_iters,
+                local_iters_coarse=args.local_iters_coarse)
+    with di.Batch(items, **bcfg) as bt:
+        bt.run()
+        ms_b = _median_ms(lambda: bt.run(s), s, 5)
+        outs_b, sts_b, cyc_b = bt.run()
+    torch.cuda.synchronize()
+    errs, errs_b, seen = [], [], set()
+    for (f, c), u, ub, sp in zip(cases, outs, outs_b, specs):
+        if sp[:2] in seen:
+            continue
+        seen.add(sp[:2])
+        ref = oracle.cg_inpaint(f, c)
+        errs.append(err_of(u.cpu().numpy(), ref))
+        errs_b.append(err_of(ub.cpu().numpy(), ref))
     print(json.dumps({"config": 3, "workload": "32 images, sizes 512^2..4K, 1-3 channels, 1-10 %",
-                      "autotuned": {"block": best["block"], "overlap": best["overlap"],
-                                    "ms_per_sample_pass": round(tune_ms, 3)},
-                      "ms_per_batch": round(ms, 3), "images_per_s": round(32e3 / ms, 1),
-                      "gpix_ch_per_s": round(pxch / ms / 1e6, 3),
-                      "statuses_ok": all(x == di.OK for x in sts),
-                      "cycles_mean": round(float(np.mean(cyc)), 3),
-                      "max_abs_512": max(e[0] for e in errs) if errs else None,
-                      "rms_512": max(e[1] for e in errs) if errs else None}), flush=True)
-    del items, outs
+                      "autotuned": {**tuned, "ms_per_sample_pass": round(tune_ms, 3)},
+                      "pool": {"ms_per_batch": round(ms, 3), "images_per_s": round(32e3 / ms, 1),
+                               "gpix_ch_per_s": round(pxch / ms / 1e6, 3),
+                               "statuses_ok": all(x == di.OK for x in sts),
+                               "cycles_mean": round(float(np.mean(cyc)), 3),
+                               "max_abs": max(e[0] for e in errs), "rms": max(e[1] for e in errs)},
+                      "batched_graph": {"ms_per_batch": round(ms_b, 3),
+                                        "images_per_s": round(32e3 / ms_b, 1),
+                                        "gpix_ch_per_s": round(pxch / ms_b / 1e6, 3),
+                                        "statuses_ok": all(x == di.OK for x in sts_b),
+                                        "cycles_mean": round(float(np.mean(cyc_b)), 3),
+                                        "max_abs": max(e[0] for e in errs_b),
+                                        "rms": max(e[1] for e in errs_b), "setting": bcfg},
+                      "oracle_checked": "one image of every size"}), flush=True)
+    del items, outs, outs_b
 
     # --- config 4 ---------------------------------------------------------------
     f, c = synth.make_case(W4K, H4K, C4K, 0.005, "edge", BASE_SEED + 4)
