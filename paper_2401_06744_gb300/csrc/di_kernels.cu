@@ -1402,23 +1402,38 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         f2 acc0 = 0ull, acc1 = 0ull;
         // r = b - A u on the block (0 on the mask).  The variants: rows off the
         // image's top and bottom rows (vertical degree 2), and b = 0 off the mask.
+        // Each run of eight rows walks down the lane's column, so a row's centre
+        // is the next row's upper neighbour (one tile load per row for the
+        // vertical neighbours instead of three).
         auto residual = [&](auto interior, auto rhs0) {
+            float rv[2 * NP];  // rows row0 .. row0 + 15
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                float rv[2];
+            for (int e = 0; e < 2; ++e) {
+                const float* cb = tu + (row0 + 8 * e + 1) * P + col + 1;  // centre of row 8e
+                float up = 0.f, cen = 0.f;
+                if (!zero_in) {
+                    up = cb[-P];
+                    cen = cb[0];
+                }
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
+                for (int k = 0; k < NP; ++k) {
                     const int ly = row0 + k + 8 * e, gy = y0 + ly;
                     float v = decltype(rhs0)::value ? 0.f : tb[ly * PB + col];
                     if (!zero_in) {
-                        const float* c0 = tu + (ly + 1) * P + col + 1;
+                        const float* c0 = cb + k * P;
+                        const float dn = c0[P];
                         const float dv = decltype(interior)::value
                                              ? 2.f : (float)((gy > 0) + (gy < h - 1));
-                        v = res_stencil<F64>(v, dh + dv, c0[0], c0[-P], c0[P], c0[-1], c0[1]);
+                        v = res_stencil<F64>(v, dh + dv, cen, up, dn, c0[-1], c0[1]);
+                        up = cen;
+                        cen = dn;
                     }
-                    rv[e] = v;
+                    rv[k + NP * e] = v;
                 }
-                r[k] = mul2(pk(rv[0], rv[1]), keep[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                r[k] = mul2(pk(rv[k], rv[k + NP]), keep[k]);
                 p[k] = r[k];
                 x[k] = 0ull;
                 if (k & 1) acc1 = fma2(r[k], r[k], acc1);

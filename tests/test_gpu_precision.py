@@ -142,4 +142,5 @@ def test_fp64_restriction_matches_oracle_more_closely(di):
         torch.cuda.synchronize()
         out[refine] = float(np.abs(rH.cpu().numpy() - ref).max())
     assert out[1] <= out[0] + 1e-7
-    assert out[1] <= 1e-5
+    # FP64 arithmetic, one rounding to FP32 at the end: within one FP32 ulp
+    assert out[1] <= float(np.abs(ref).max()) * 2.0 ** -23
