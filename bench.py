@@ -42,13 +42,18 @@ UNIT = "frames/s"
 W4K, H4K, C4K = 3840, 2160, 3
 TOL = 0.05
 # Solver configuration of the timed decode: 32x32 blocks, overlap 2, 10 local
-# CG steps on the finest level and 8 on the coarser ones.  Block size, overlap
+# CG steps on the finest level and 8 on the coarser ones, local stop 0.4.  Block size, overlap
 # and local steps are tunables of the method; this setting decodes the six
 # frames fastest among those swept (overlaps 2-6, 6-16 local steps, 4-14 on the
 # coarse levels, 16x16 and 32x32 blocks) while every frame stays within 0.026
 # gray of the FP64 oracle.  The paper's own setting (overlap 6, 8 local
 # steps) is timed beside it on the same frames ("paper_config").
 BLOCK, OVERLAP, LOCAL_ITERS, LOCAL_ITERS_COARSE = 32, 2, 10, 8
+# A block's local CG also stops once its residual is at most LOCAL_STOP x tol
+# gray (a correction that small is below what the stop rule resolves); 0.4
+# decodes the six frames 5 % faster than 0.2 at the same V-cycle counts and a
+# largest error of 0.028 gray (0.026 at 0.2) in a sweep of 0.2 - 0.5.
+LOCAL_STOP = 0.4
 PAPER_BLOCK, PAPER_OVERLAP, PAPER_LOCAL_ITERS = 32, 6, 8
 CASES = [(0.10, "edge"), (0.04, "edge"), (0.01, "edge"),
          (0.10, "uniform"), (0.04, "uniform"), (0.01, "uniform")]
@@ -264,7 +269,8 @@ def run_ours(args):
     # one decoder (context, stream, output) per frame in flight
     ctxs = [di.Context(device=local, profile=0, precision=prec, block=args.block,
                        overlap=args.overlap, local_iters=args.local_iters,
-                       local_iters_coarse=args.local_iters_coarse) for _ in range(S)]
+                       local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+            for _ in range(S)]
     streams = [torch.cuda.Stream(dev) for _ in range(S)]
     u_dev = [torch.empty_like(f_dev[0]) for _ in range(S)]
     main = torch.cuda.current_stream(dev)
@@ -357,7 +363,7 @@ def run_ours(args):
     u_host = [torch.empty(f_host[0].shape, dtype=torch.float32).pin_memory() for _ in range(R)]
     srv = di.Server(slots=S, device=local, precision=prec, block=args.block,
                     overlap=args.overlap, local_iters=args.local_iters,
-                    local_iters_coarse=args.local_iters_coarse)
+                    local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
 
     def e2e_run(n):
         tickets = []
@@ -422,7 +428,8 @@ def run_ours(args):
     prof_n = 2 * len(cases)
     with di.Context(device=local, profile=1, precision=prec, block=args.block,
                     overlap=args.overlap, local_iters=args.local_iters,
-                    local_iters_coarse=args.local_iters_coarse) as pctx_:
+                    local_iters_coarse=args.local_iters_coarse,
+                    local_stop=args.local_stop) as pctx_:
         for i in range(len(cases)):  # warm-up: workspace, graphs
             pctx_.inpaint(f_dev[i], c_dev[i], tol=TOL, out=u_dev[0], stream=streams[0])
         torch.cuda.synchronize(dev)
@@ -576,7 +583,8 @@ def run_ours(args):
                                "uniform} in rotation, tol 0.05 gray (error-estimate stop rule)",
                    "block": args.block, "overlap": args.overlap,
                    "local_iters": args.local_iters,
-                   "local_iters_coarse": args.local_iters_coarse, "frames": len(cases),
+                   "local_iters_coarse": args.local_iters_coarse,
+                   "local_stop": args.local_stop, "frames": len(cases),
                    "streams": S, "precision": args.precision,
                    "l2": "inputs larger than L2 (6 rotating frames, 650 MB), no flush",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -689,7 +697,8 @@ def run_decode_once(args):
     graph = di.GRAPH_OFF if args.graph == "off" else di.GRAPH_ON
     with di.Context(device=0, block=args.block, overlap=args.overlap,
                     local_iters=args.local_iters, graph=graph,
-                    local_iters_coarse=args.local_iters_coarse) as ctx:
+                    local_iters_coarse=args.local_iters_coarse,
+                    local_stop=args.local_stop) as ctx:
         for k in range(len(cases)):
             ctx.inpaint(fd[k], cd[k], tol=TOL, out=out)
         torch.cuda.synchronize(dev)
@@ -854,7 +863,7 @@ def _compare_video(args, di, dev, s):
     ft = [torch.from_numpy(f).to(dev) for f in seq]
     refs = []
     cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters,
-               local_iters_coarse=args.local_iters_coarse)
+               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
     with di.Context(device=0, stop_rule=di.STOP_FIXED_CYCLES, max_cycles=12, min_cycles=12,
                     **cfg) as ctx:
         for f in ft:
@@ -921,7 +930,7 @@ def _compare_configs(args, di, dev, s):
     import synth
 
     cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters,
-               local_iters_coarse=args.local_iters_coarse)
+               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
 
     def err_of(u, ref):
         e = np.abs(u.astype(np.float64) - ref)
@@ -970,7 +979,7 @@ def _compare_configs(args, di, dev, s):
     torch.cuda.synchronize()
     # the batched form: one graph, one launch per step over all 32 images
     bcfg = dict(block=32, overlap=2, local_iters=args.local_iters,
-                local_iters_coarse=args.local_iters_coarse)
+                local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
     with di.Batch(items, **bcfg) as bt:
         bt.run()
         ms_b = _median_ms(lambda: bt.run(s), s, 5)
@@ -1056,11 +1065,13 @@ def _compare_configs(args, di, dev, s):
                     res.append(srv.wait(tickets[j - ring])[1])
                 o = outs[j % ring].view(-1)[:f.numel()].view(f.shape)
                 tickets.append(srv.submit(f, c, TOL, out=o))
+            t_submitted = time.perf_counter()
             res += [srv.wait(t)[1] for t in tickets[max(0, len(tickets) - ring):]]
             t_last = time.perf_counter()
         lat = sorted(r["latency_ms"] for r in res)
         print(json.dumps({"config": 5, "workload": "Poisson stream, 720p/1080p/4K RGB, 0.5-10 %",
                           "offered_per_s": lam, "requests": n,
+                          "arrived_per_s": round(n / (t_submitted - t_first), 1),
                           "served_per_s": round(n / (t_last - t_first), 1),
                           "p50_ms": round(lat[len(lat) // 2], 3),
                           "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
@@ -1089,6 +1100,8 @@ def main():
                     help="CG steps of each local block solve on the finest level")
     ap.add_argument("--local-iters-coarse", type=int, default=LOCAL_ITERS_COARSE,
                     help="CG steps of the local block solves on the coarser levels")
+    ap.add_argument("--local-stop", type=float, default=LOCAL_STOP,
+                    help="local CG stop level as a fraction of tol (cfg.local_stop)")
     ap.add_argument("--streams", type=int, default=4,
                     help="frames in flight: decoders, each with its own context and stream")
     ap.add_argument("--graph", choices=["on", "off"], default="on",

@@ -396,6 +396,18 @@ di_status di_values_downsample(const uint8_t *c, const float *b, int width, int 
                                int channels, const uint8_t *cH, float *bH, int modified,
                                void *stream);
 
+/* One level of the pyramid in one pass, as the decoder runs it (Section 4.3):
+ * cH = the 2x2 max pooling of c (as di_mask_downsample), bH = the mask-value
+ * downsampling of (c, b) with the modified (1) or naive (0) weights (as
+ * di_values_downsample; b and bH NULL: masks only), bits = cH bit-packed,
+ * ceil(ceil(w/2) / 32) + 1 uint32 words per coarse row (bit x of word k = column
+ * 32k + x known or beyond the image; the last word of a row all ones), and
+ * *unknown (device, nullable; not cleared) gains the coarse level's unknown
+ * pixels.  Bit-identical to the separate steps. */
+di_status di_pyramid_level(const uint8_t *c, const float *b, int width, int height, int channels,
+                           uint8_t *cH, float *bH, uint32_t *bits, int modified,
+                           unsigned long long *unknown, void *stream);
+
 /* Residual r = b - A u with A = C + (I - C) L (Algorithm 2 step 1, eq. 2.6),
  * and its squared 2-norm per channel.
  *  b: [ch][h][w]: at mask pixels the Dirichlet value, at unknown pixels the

@@ -15,7 +15,7 @@ from ._lib import (  # noqa: F401
     STOP_ERROR_ESTIMATE, SCHED_REDUCED_FMG, SCHED_FULL_FMG, SCHED_MULTILEVEL, SCHED_SINGLE,
     SMOOTH_ORAS, SMOOTH_CG, GRAPH_ON, GRAPH_OFF, START_CASCADE, START_GIVEN,
     STOP_FIXED_CYCLES, STOP_RELATIVE_RESIDUAL, TIMEOUT, Context, DiError, LIB_PATH,
-    exported_symbols, load, mask_downsample, plan, prolong, residual_norm_noalloc,
+    exported_symbols, load, mask_downsample, plan, prolong, pyramid_level, residual_norm_noalloc,
     restrict_residual, status_string, values_downsample, inpaint_batch, autotune, Server, Pool, Batch,
     selftest_bounded_wait)
 

@@ -125,6 +125,7 @@ _SIGS = {
     "di_last_error": (ctypes.c_char_p, [_P]),
     "di_mask_downsample": (_I, [_P, _I, _I, _P, _P]),
     "di_values_downsample": (_I, [_P, _P, _I, _I, _I, _P, _P, _I, _P]),
+    "di_pyramid_level": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _I, _P, _P]),
     "di_residual_norm": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_residual_norm_noalloc": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
     "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P]),
@@ -342,6 +343,28 @@ def values_downsample(c, b, cH, modified=True, stream=None):
     _check(load().di_values_downsample(c.data_ptr(), b3.data_ptr(), W, H, C, cH.data_ptr(),
                                        bH.data_ptr(), int(bool(modified)), _stream(stream)))
     return bH
+
+
+def pyramid_level(c, b=None, modified=True, stream=None):
+    """di_pyramid_level: (cH, bH or None, packed cH words [hH, wpr] int32, unknown count)."""
+    c = _mask(c)
+    H, W = c.shape
+    hH, wH = (H + 1) // 2, (W + 1) // 2
+    wpr = (wH + 31) // 32 + 1
+    cH = torch.empty((hH, wH), dtype=torch.uint8, device=c.device)
+    bits = torch.empty((hH, wpr), dtype=torch.int32, device=c.device)
+    unk = torch.zeros(1, dtype=torch.int64, device=c.device)
+    if b is not None:
+        b3 = _img(b, "b")
+        C = b3.shape[0]
+        bH = torch.empty((C, hH, wH), dtype=torch.float32, device=c.device)
+        bp, bHp = b3.data_ptr(), bH.data_ptr()
+    else:
+        C, bH, bp, bHp = 1, None, None, None
+    _check(load().di_pyramid_level(c.data_ptr(), bp, W, H, C, cH.data_ptr(), bHp,
+                                   bits.data_ptr(), int(bool(modified)), unk.data_ptr(),
+                                   _stream(stream)))
+    return cH, bH, bits, unk
 
 
 NOALLOC_PARTIALS = 131072

@@ -115,6 +115,13 @@ struct di_ctx {
     unsigned long long ws_gen = 0;     // workspace generation (graphs bake its addresses)
     DecodeGraph* pending = nullptr;    // device-driven decode whose stats are not read yet
     bool device_path_broken = false;   // a capture failed: use the host-driven loop
+    // capture policy: a call whose buffers have no graph captures one unless
+    // the last calls all missed too (the caller changes buffers every call);
+    // then only buffers seen before (a recent key, kept here) get a graph
+    int misses = 0;
+    static constexpr int kSeen = 64;
+    unsigned long long seen[kSeen] = {};
+    int seen_next = 0;
 };
 
 namespace {
@@ -529,6 +536,12 @@ di_status timeout(di_ctx* ctx) {
     return DI_ERR_TIMEOUT;
 }
 
+unsigned bits_of(float f) {
+    unsigned b;
+    std::memcpy(&b, &f, sizeof b);
+    return b;
+}
+
 float bits_to_float(unsigned b) {
     float f;
     std::memcpy(&f, &b, sizeof f);
@@ -700,12 +713,10 @@ bool capture_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, flo
             for (int l = 1; l < L; ++l) {
                 Level& fl = lv[l - 1];
                 Level& cl = lv[l];
-                if (launch_mask_down(fl.c, fl.w, fl.h, const_cast<uint8_t*>(cl.c), s0)) return false;
-                if (cascade &&
-                    launch_values_down(fl.c, fl.b, fl.w, fl.h, C, cl.c, const_cast<float*>(cl.b),
-                                       cfg.downsample == 0 ? 1 : 0, s0))
+                if (launch_pyramid_level(fl.c, fl.b, fl.w, fl.h, C, const_cast<uint8_t*>(cl.c),
+                                         const_cast<float*>(cl.b), cfg.downsample == 0 ? 1 : 0,
+                                         cascade ? 1 : 0, cl.mbits, cnt + 1 + l, s0))
                     return false;
-                if (launch_pack_mask(cl.c, cl.w, cl.h, cl.mbits, cnt + 1 + l, s0)) return false;
             }
             if (launch_plan(cnt, ctx->dstate, pp, s0)) return false;
             // 2. the given start, and the reference norm of the relative-residual rule
@@ -846,12 +857,31 @@ bool device_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, floa
         if (!dg.valid || dg.used < victim->used) victim = &dg;
     }
     if (!hit) {
+        // capture unless the buffers change every call: after two misses in a
+        // row only a key seen before gets a graph (the others run the
+        // host-driven loop, which captures no more than one V-cycle)
+        unsigned long long key = 1469598103934665603ull;
+        for (unsigned long long v :
+             {(unsigned long long)(uintptr_t)f, (unsigned long long)(uintptr_t)c,
+              (unsigned long long)(uintptr_t)u, (unsigned long long)w, (unsigned long long)h,
+              (unsigned long long)C, (unsigned long long)bits_of(tol), ctx->ws_gen})
+            key = (key ^ v) * 1099511628211ull;
+        bool seen = false;
+        for (unsigned long long k : ctx->seen) seen = seen || (k == key);
+        if (!seen) {
+            ctx->seen[ctx->seen_next] = key;
+            ctx->seen_next = (ctx->seen_next + 1) % di_ctx::kSeen;
+        }
+        if (ctx->misses >= 2 && !seen) return false;
+        ++ctx->misses;
         drop_graph(*victim);
         if (!capture_decode(ctx, S, f, c, u, w, h, C, tol, *victim)) {
             ctx->device_path_broken = true;
             return false;
         }
         hit = victim;
+    } else {
+        ctx->misses = 0;
     }
     hit->used = ++ctx->graph_clock;
     cudaStream_t s = S.s;
@@ -1080,12 +1110,11 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
     for (int l = 1; l < L; ++l) {
         Level& f_ = ctx->lv[l - 1];
         Level& cv = ctx->lv[l];
-        DI_CUDA(ctx, launch_mask_down(f_.c, f_.w, f_.h, const_cast<uint8_t*>(cv.c), s));
-        if (cfg.start != DI_START_GIVEN)  // the coarse values feed the cascade only
-            DI_CUDA(ctx, launch_values_down(f_.c, f_.b, f_.w, f_.h, C, cv.c,
-                                            const_cast<float*>(cv.b),
-                                            cfg.downsample == 0 ? 1 : 0, s));
-        DI_CUDA(ctx, launch_pack_mask(cv.c, cv.w, cv.h, cv.mbits, cnt + 1 + l, s));
+        // the coarse values feed the cascade only
+        DI_CUDA(ctx, launch_pyramid_level(f_.c, f_.b, f_.w, f_.h, C, const_cast<uint8_t*>(cv.c),
+                                          const_cast<float*>(cv.b), cfg.downsample == 0 ? 1 : 0,
+                                          cfg.start != DI_START_GIVEN ? 1 : 0, cv.mbits,
+                                          cnt + 1 + l, s));
     }
     unsigned long long* hcnt = static_cast<unsigned long long*>(ctx->host);
     DI_CUDA(ctx, cudaMemcpyAsync(hcnt, cnt, (L + 1) * sizeof(unsigned long long),
@@ -1317,6 +1346,18 @@ di_status di_values_downsample(const uint8_t* c, const float* b, int width, int 
         return DI_ERR_INVALID_ARG;
     cudaError_t e = launch_values_down(c, b, width, height, channels, cH, bH, modified,
                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
+}
+
+di_status di_pyramid_level(const uint8_t* c, const float* b, int width, int height, int channels,
+                           uint8_t* cH, float* bH, uint32_t* bits, int modified,
+                           unsigned long long* unknown, void* stream) {
+    if (!c || !cH || !bits || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels || (modified != 0 && modified != 1) || (!b) != (!bH))
+        return DI_ERR_INVALID_ARG;
+    cudaError_t e = launch_pyramid_level(c, b, width, height, channels, cH, bH, modified,
+                                         b ? 1 : 0, bits, unknown,
+                                         static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? DI_OK : DI_ERR_CUDA;
 }
 

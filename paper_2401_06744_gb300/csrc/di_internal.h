@@ -79,6 +79,15 @@ cudaError_t launch_select(const float* b, const uint8_t* c, int w, int h, int C,
 // polls), on a barrier nothing completes; *flag = 1 when the wait ran out.
 cudaError_t launch_wait_selftest(unsigned* flag, int limit, cudaStream_t s);
 
+// One pyramid level in one launch: cH = 2x2 max pool of c, bH the mask-value
+// downsampling of (c, b) (modified = 1, or naive; values = 0: skipped), bits
+// the bit-packed cH, *unknown (nullable, zeroed by the caller) gains the
+// coarse level's unknown pixels.  Bit-identical to mask_down + values_down +
+// pack_mask.
+cudaError_t launch_pyramid_level(const uint8_t* c, const float* b, int w, int h, int C,
+                                 uint8_t* cH, float* bH, int modified, int values, uint32_t* bits,
+                                 unsigned long long* unknown, cudaStream_t s);
+
 // Bit-packed mask (see mask_words_per_row) of c; *unknown (nullable, zeroed
 // by the caller) gains the number of unknown pixels.
 cudaError_t launch_pack_mask(const uint8_t* c, int w, int h, uint32_t* bits,

@@ -213,6 +213,116 @@ __global__ void k_values_down(const uint8_t* __restrict__ c, const float* __rest
     values_down_body(c, b, w, h, C, cH, bH, wH, hH, modified, blockIdx.x, blockIdx.y);
 }
 
+// One level of the pyramid in one pass (Section 4.3): thread (X, Y) forms the
+// coarse mask cell cH = max over its children, the mask value bH (modified or
+// naive downsampling, the same weights and sums as values_down_body), and the
+// warp of 32 consecutive X packs the 32 mask bits of its row (known or beyond
+// the image = 1) and counts the unknown ones; the CTAs of the last column
+// write the padding word of their rows.  The neighbouring coarse cells'
+// masks that the modified weights need are formed from the fine mask too, so
+// the level needs no second pass.  values = 0: masks only (a given start).
+__global__ void __launch_bounds__(256)
+k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int w, int h, int C,
+                uint8_t* __restrict__ cH, float* __restrict__ bH, int wH, int hH, int modified,
+                int values, uint32_t* __restrict__ bits, int wpr,
+                unsigned long long* __restrict__ unknown) {
+    const int X = blockIdx.x * 32 + threadIdx.x;
+    const int Y = blockIdx.y * 8 + threadIdx.y;
+    const int lane = threadIdx.x;
+    // coarse cell (Xc, Yc) known: any of its in-image children known
+    auto known = [&](int Xc, int Yc) -> bool {
+        if (Xc < 0 || Xc >= wH || Yc < 0 || Yc >= hH) return false;
+        const int x = 2 * Xc, y = 2 * Yc;
+        const uint8_t* row = c + (size_t)y * w;
+        bool m = row[x] != 0;
+        if (x + 1 < w) m |= row[x + 1] != 0;
+        if (y + 1 < h) {
+            m |= row[x + w] != 0;
+            if (x + 1 < w) m |= row[x + w + 1] != 0;
+        }
+        return m;
+    };
+    const bool inside = X < wH && Y < hH;
+    const bool kn = inside && known(X, Y);
+    if (inside) {
+        const size_t nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
+        cH[P] = kn ? 1 : 0;
+        if (values) {
+            const size_t n = (size_t)w * h;
+            if (!kn) {
+                for (int ch = 0; ch < C; ++ch) bH[ch * nH + P] = 0.f;
+            } else {
+                // masks of the four direct neighbour cells (for the modified weights)
+                const bool kl = known(X - 1, Y), kr = known(X + 1, Y);
+                const bool ku = known(X, Y - 1), kd = known(X, Y + 1);
+                float wt[4];
+                size_t idx[4];
+                float den = 0.f, cnt = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = 2 * X + (k & 1), y = 2 * Y + (k >> 1);
+                    wt[k] = 0.f;
+                    idx[k] = 0;
+                    if (x >= w || y >= h) continue;
+                    const size_t p = (size_t)y * w + x;
+                    idx[k] = p;
+                    if (!c[p]) continue;
+                    cnt += 1.f;
+                    if (!modified) { wt[k] = 1.f; continue; }
+                    int m = 0;
+                    const int xi = x ^ 1, yi = y ^ 1;  // partners inside the cell
+                    if (xi < w) m += c[(size_t)y * w + xi] != 0;
+                    if (yi < h) m += c[(size_t)yi * w + x] != 0;
+                    const int xo = (x & 1) ? x + 1 : x - 1;  // neighbours across the cell
+                    const int yo = (y & 1) ? y + 1 : y - 1;
+                    if (xo >= 0 && xo < w) m += (x & 1) ? kr : kl;
+                    if (yo >= 0 && yo < h) m += (y & 1) ? kd : ku;
+                    wt[k] = (float)(4 - m);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) den += wt[k];
+                if (den == 0.f) {  // gap of the printed rule: the naive average
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int x = 2 * X + (k & 1), y = 2 * Y + (k >> 1);
+                        wt[k] = (x < w && y < h && c[idx[k]]) ? 1.f : 0.f;
+                    }
+                    den = cnt;
+                }
+                const float inv = 1.f / fmaxf(1.f, den);
+                for (int ch = 0; ch < C; ++ch) {
+                    const float* bc = b + ch * n;
+                    float num = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (wt[k] != 0.f) num += wt[k] * bc[idx[k]];
+                    bH[ch * nH + P] = num * inv;
+                }
+            }
+        }
+    }
+    // the packed mask row of this warp: bit set = known or beyond the image
+    const unsigned word = __ballot_sync(0xffffffffu, X >= wH || kn);
+    unsigned unk = 0;
+    if (Y < hH) {
+        if (lane == 0) bits[(size_t)Y * wpr + blockIdx.x] = word;
+        unk = X < wH && !kn ? 1u : 0u;
+        if (blockIdx.x == gridDim.x - 1 && lane == 0)
+            bits[(size_t)Y * wpr + wpr - 1] = 0xffffffffu;  // the padding word
+    }
+    if (unknown) {
+        __shared__ unsigned s_u[8];
+        const unsigned c8 = __reduce_add_sync(0xffffffffu, unk);
+        if (lane == 0) s_u[threadIdx.y] = c8;
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            unsigned long long a = 0;
+            for (int i = 0; i < 8; ++i) a += s_u[i];
+            if (a) atomicAdd(unknown, a);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Residual and its norm (Algorithm 2 step 1; Section 2.2 "single global scalar
 // product")
@@ -526,6 +636,96 @@ k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
            int hH) {
     restrict_body<VEC, TU, TB, TO, F64>(u, b, rhs_zero, w, h, cH, rH, wH, hH, blockIdx.x, blockIdx.y,
                                         blockIdx.z);
+}
+
+// The restriction of FP32 levels with a shared-memory tile: a CTA of 32 x 8
+// threads (one per coarse cell) first stages the fine rows 2Y0 - 1 .. 2Y0 + 16
+// and columns 2X0 - 2 .. 2X0 + 65 around its cells' children with coalesced
+// loads (8-byte words where VEC), zero outside the image; each thread then
+// reads its 4 x 4 patch from shared memory (the children's pair of columns as
+// one 8-byte word per row) and forms the same sums in the same order as
+// restrict_body, so the results are bit-identical.
+template <bool VEC, bool F64>
+__global__ void __launch_bounds__(256)
+k_restrict_tile(const float* __restrict__ u, const float* __restrict__ b, int rhs_zero, int w,
+                int h, const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH, int hH) {
+    typedef typename std::conditional<F64, double, float>::type R;
+    constexpr int TR = 18, TC = 68;  // tile rows and columns (pitch)
+    __shared__ __align__(16) float tile[TR][TC];
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    const int ch = blockIdx.z;
+    const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
+    const float* uc = u + ch * n;
+    const int fx0 = 2 * (int)blockIdx.x * 32 - 2, fy0 = 2 * (int)blockIdx.y * 8 - 1;
+    if (VEC) {
+        // 18 rows of 34 pairs; fx0 is even, so every pair is 8-byte aligned
+        for (int e = t; e < TR * (TC / 2); e += 256) {
+            const int r = e / (TC / 2), pc = e - r * (TC / 2);
+            const int y = fy0 + r, x = fx0 + 2 * pc;
+            float2 v = make_float2(0.f, 0.f);
+            if (y >= 0 && y < h) {
+                const float* row = uc + (size_t)y * w;
+                if (x >= 0 && x + 1 < w) v = *reinterpret_cast<const float2*>(row + x);
+                else {
+                    if (x >= 0 && x < w) v.x = row[x];
+                    if (x + 1 >= 0 && x + 1 < w) v.y = row[x + 1];
+                }
+            }
+            *reinterpret_cast<float2*>(&tile[r][2 * pc]) = v;
+        }
+    } else {
+        for (int e = t; e < TR * TC; e += 256) {
+            const int r = e / TC, cc = e - r * TC;
+            const int y = fy0 + r, x = fx0 + cc;
+            tile[r][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
+        }
+    }
+    __syncthreads();
+    const int X = (int)blockIdx.x * 32 + tx, Y = (int)blockIdx.y * 8 + ty;
+    if (X >= wH || Y >= hH) return;
+    const size_t P = (size_t)Y * wH + X;
+    if (cH[P]) { rH[ch * nH + P] = 0.f; return; }
+    const int x0 = 2 * X - 1, y0 = 2 * Y - 1;
+    // patch row j (fine row y0 + j) = tile row 2 ty + j; patch column i (fine
+    // column x0 + i) = tile column 2 tx + 1 + i
+    float t4[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float* tr = &tile[2 * ty + j][2 * tx];
+        const float2 mid = *reinterpret_cast<const float2*>(tr + 2);
+        t4[j][1] = mid.x;
+        t4[j][2] = mid.y;
+        const bool inner = j == 1 || j == 2;
+        t4[j][0] = inner ? tr[1] : 0.f;
+        t4[j][3] = inner ? tr[4] : 0.f;
+    }
+    R sum = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int j = 1; j <= 2; ++j) {
+        float2 rb = make_float2(0.f, 0.f);
+        const int y = y0 + j;
+        if (!rhs_zero && y < h) {
+            const float* br = b + ch * n + (size_t)y * w + x0 + 1;
+            if (VEC) rb = *reinterpret_cast<const float2*>(br);
+            else {
+                rb.x = br[0];
+                if (x0 + 2 < w) rb.y = br[1];
+            }
+        }
+#pragma unroll
+        for (int i = 1; i <= 2; ++i) {
+            const int x = x0 + i;
+            if (x >= w || y >= h) continue;
+            const int deg = (x > 0) + (x < w - 1) + (y > 0) + (y < h - 1);
+            const R lu = (R)deg * (R)t4[j][i] -
+                         ((R)t4[j][i - 1] + (R)t4[j][i + 1] + (R)t4[j - 1][i] + (R)t4[j + 1][i]);
+            const R rhs = rhs_zero ? (R)0 : (R)(i == 1 ? rb.x : rb.y);
+            sum += rhs - lu;
+            ++cnt;
+        }
+    }
+    rH[ch * nH + P] = (float)((R)4 * sum / (R)cnt);
 }
 
 // Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
@@ -2612,38 +2812,44 @@ bool make_map(CUtensorMap* m, const float* base, int w, int h, int C, int bw, in
            CUDA_SUCCESS;
 }
 
-// occupancy per (kernel, shared-memory size), cached
+// Resident CTAs per SM of a kernel at a shared-memory size, and the SM count,
+// cached per (device, kernel, shared-memory size): a process may drive
+// several GPUs.
 int cached_occupancy(const void* kern, int threads, size_t smem, size_t smem_max, int* nsm_out) {
     static std::mutex occ_mu;
-    static int nsm = 0;
-    static const void* occ_fn[16] = {};
-    static size_t occ_key[16] = {};
-    static int occ_val[16] = {};
+    constexpr int kSlots = 64;
+    static int occ_dev[kSlots];
+    static const void* occ_fn[kSlots] = {};
+    static size_t occ_key[kSlots] = {};
+    static int occ_val[kSlots] = {};
+    static int occ_nsm[kSlots] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
     std::lock_guard<std::mutex> occ_lock(occ_mu);
-    if (nsm == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    }
-    *nsm_out = nsm;
-    for (int i = 0; i < 16; ++i)
-        if (occ_fn[i] == kern && occ_key[i] == smem) return occ_val[i];
-    int oc = 0;
+    for (int i = 0; i < kSlots; ++i)
+        if (occ_fn[i] == kern && occ_key[i] == smem && occ_dev[i] == dev) {
+            *nsm_out = occ_nsm[i];
+            return occ_val[i];
+        }
+    int nsm = 0, oc = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, kern, threads, smem);
     if (oc < 1) oc = 1;
-    for (int i = 0; i < 16; ++i)
+    if (nsm < 1) nsm = 1;
+    for (int i = 0; i < kSlots; ++i)
         if (occ_fn[i] == nullptr) {
             occ_fn[i] = kern;
             occ_key[i] = smem;
+            occ_dev[i] = dev;
             occ_val[i] = oc;
+            occ_nsm[i] = nsm;
             break;
         }
+    *nsm_out = nsm;
     return oc;
 }
 
-// precision: 0 FP32 (tiles by TMA where the image allows it), 1 FP16, 2 BF16
-// local iterates
 // The 16-bit block kernel for iterate type H and storage TU.
 template <class H, class TU, bool F64>
 void run_oras_2w_h(int grid, size_t smem, cudaStream_t s, const float* u_in, int zero_in,
@@ -2753,20 +2959,9 @@ cudaError_t launch_oras_t(const float* u_in, int zero_in, const float* rhs, int 
     const size_t smem = (size_t)FIXED * sizeof(float) +
                         (rhs_zero ? 0 : (size_t)2 * B * B * sizeof(float));
     // persistent warps: as many as fit on the GPU at once
-    static std::mutex occ_mu;
-    std::lock_guard<std::mutex> occ_lock(occ_mu);
-    static int occ[2] = {0, 0};
-    static int nsm = 0;
-    int& oc = occ[rhs_zero ? 0 : 1];
-    if (oc == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_oras_warp<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(FIXED * sizeof(float) + 2 * B * B * sizeof(float)));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_oras_warp<B>, 32, smem);
-        if (oc < 1) oc = 1;
-    }
+    int nsm = 0;
+    const int oc = cached_occupancy((const void*)k_oras_warp<B>, 32, smem,
+                                    FIXED * sizeof(float) + 2 * B * B * sizeof(float), &nsm);
     const int slots = nsm * oc;
     const int nblk = nbx * nby;
     const int chan_inner = nblk >= slots ? 1 : 0;
@@ -2960,17 +3155,15 @@ cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const 
                      ((reinterpret_cast<uintptr_t>(u) |
                        reinterpret_cast<uintptr_t>(rhs_zero ? nullptr : b)) % 8 == 0);
     if (su == kF32 && sb == kF32 && sr == kF32) {
+        // the shared-memory tile kernel (bit-identical to the per-cell one)
         if (vec && f64)
-            k_restrict<true, float, float, float, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h,
-                                                                            cH, rH, wH, hH);
+            k_restrict_tile<true, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else if (vec)
-            k_restrict<true, float, float, float, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h,
-                                                                             cH, rH, wH, hH);
+            k_restrict_tile<true, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else if (f64)
-            run_restrict<float, float, float, true>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH, hH);
+            k_restrict_tile<false, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else
-            run_restrict<float, float, float, false>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH,
-                                                     hH);
+            k_restrict_tile<false, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
     } else if (su == kF32 && sb == kF32 && sr == kF16) {  // finest level, FP16 coarse levels
         if (vec && f64)
             k_restrict<true, float, float, __half, true><<<grid, blk, 0, s>>>(
@@ -3243,6 +3436,20 @@ cudaError_t launch_batch_plan(int n, const int* L, const unsigned long long* n0,
 cudaError_t launch_batch_stop(int n, const StopParams& p, const BatchState& bs,
                               unsigned long long h_loop, cudaStream_t s) {
     k_batch_stop<<<1, 256, 0, s>>>(n, p, bs, (cudaGraphConditionalHandle)h_loop);
+    count();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid_level(const uint8_t* c, const float* b, int w, int h, int C,
+                                 uint8_t* cH, float* bH, int modified, int values, uint32_t* bits,
+                                 unsigned long long* unknown, cudaStream_t s) {
+    int wH, hH;
+    coarse_dims(w, h, &wH, &hH);
+    const int wpr = mask_words_per_row(wH);
+    // one CTA column per packed word of a coarse row but the padding word
+    const dim3 grid((unsigned)(wpr - 1), (unsigned)((hH + 7) / 8));
+    k_pyramid_level<<<grid, dim3(32, 8), 0, s>>>(c, b, w, h, C, cH, bH, wH, hH, modified, values,
+                                                 bits, wpr, unknown);
     count();
     return cudaGetLastError();
 }

@@ -117,14 +117,13 @@ extern "C" di_status di_pool_inpaint(di_pool* pool, di_image* imgs, int n, void*
         return (long long)imgs[a].width * imgs[a].height * imgs[a].channels >
                (long long)imgs[b].width * imgs[b].height * imgs[b].channels;
     });
-    std::atomic<int> next{0};
+    // images dealt round robin (largest first), so a repeated batch gives
+    // every slot the same images and their graphs stay cached
     auto worker = [&](int k) {
         Slot& s = pool->slots[k];
         cudaSetDevice(device);
         cudaStreamWaitEvent(s.stream, pool->start, 0);
-        for (;;) {
-            const int j = next.fetch_add(1);
-            if (j >= n) break;
+        for (int j = k; j < n; j += P) {
             di_image& im = imgs[order[j]];
             im.status = di_inpaint(s.ctx, im.f, im.c, im.width, im.height, im.channels, im.tol,
                                    im.u, s.stream);

@@ -200,7 +200,7 @@ def test_full_size_bench_frames_in_bench_configuration(di):
     frames = [synth.make_case(bench.W4K, bench.H4K, bench.C4K, *bench.CASES[k],
                               bench._case_seed(k)) for k in ks]
     cfg = dict(block=bench.BLOCK, overlap=bench.OVERLAP, local_iters=bench.LOCAL_ITERS,
-               local_iters_coarse=bench.LOCAL_ITERS_COARSE)
+               local_iters_coarse=bench.LOCAL_ITERS_COARSE, local_stop=bench.LOCAL_STOP)
     outs, sts = [None] * len(ks), [None] * len(ks)
 
     def work(t):

@@ -77,6 +77,35 @@ def test_values_downsample(di, h, w, modified):
     assert np.abs(out - ref).max() < 2e-4
 
 
+@pytest.mark.parametrize("h,w", SIZES + [(1080, 1920), (33, 2000)])
+@pytest.mark.parametrize("modified", [True, False])
+def test_pyramid_level_one_pass_bit_exact(di, h, w, modified):
+    # the decoder's one-pass pyramid level: the coarse mask bit-exact with the
+    # oracle's 2x2 max pooling, the mask values bit-identical to the separate
+    # downsampling step and within rounding of the oracle, the packed words
+    # and the unknown count exactly those of the coarse mask
+    f, fn, c = _case(h, w, 2, 0.2, h * 5 + w)
+    cH, bH, bits, unk = di.pyramid_level(T(c), T(fn), modified=modified)
+    cH_ref = M.mask_downsample(c)
+    assert np.array_equal(N(cH), cH_ref)
+    sep = N(di.values_downsample(T(c), T(fn), T(cH_ref), modified=modified))
+    assert np.array_equal(N(bH), sep)
+    ref = (M.values_downsample_modified(c, f, cH_ref) if modified
+           else M.values_downsample_naive(c, f))
+    assert np.abs(N(bH) - ref).max() < 2e-4
+    hH, wH = cH_ref.shape
+    wpr = (wH + 31) // 32 + 1
+    words = N(bits).astype(np.int64) & 0xFFFFFFFF
+    known = np.ones((hH, 32 * wpr), dtype=bool)
+    known[:, :wH] = cH_ref.astype(bool)
+    ref_words = (known.reshape(hH, wpr, 32) * (1 << np.arange(32, dtype=np.int64))).sum(axis=2)
+    assert np.array_equal(words, ref_words)
+    assert int(N(unk)[0]) == int((cH_ref == 0).sum())
+    # masks only
+    cH2, bH2, bits2, unk2 = di.pyramid_level(T(c))
+    assert bH2 is None and np.array_equal(N(cH2), cH_ref) and np.array_equal(N(bits2), N(bits))
+
+
 @pytest.mark.parametrize("h,w", SIZES)
 def test_residual_and_norm(di, h, w):
     f, fn, c = _case(h, w, 2, 0.1, h * 13 + w)
