@@ -115,10 +115,10 @@ struct di_ctx {
     unsigned long long ws_gen = 0;     // workspace generation (graphs bake its addresses)
     DecodeGraph* pending = nullptr;    // device-driven decode whose stats are not read yet
     bool device_path_broken = false;   // a capture failed: use the host-driven loop
-    // capture policy: a call whose buffers have no graph captures one unless
-    // the last calls all missed too (the caller changes buffers every call);
-    // then only buffers seen before (a recent key, kept here) get a graph
-    int misses = 0;
+    // capture policy: a call whose buffers have no graph captures one while
+    // the cache has room; once it is full, only buffers seen before (a recent
+    // key, kept here) get a graph, so a caller that changes buffers every call
+    // runs the host-driven loop instead of capturing every time
     static constexpr int kSeen = 64;
     unsigned long long seen[kSeen] = {};
     int seen_next = 0;
@@ -857,9 +857,9 @@ bool device_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, floa
         if (!dg.valid || dg.used < victim->used) victim = &dg;
     }
     if (!hit) {
-        // capture unless the buffers change every call: after two misses in a
-        // row only a key seen before gets a graph (the others run the
-        // host-driven loop, which captures no more than one V-cycle)
+        // capture while the cache has room; then only for buffers seen before
+        // (the others run the host-driven loop, which captures no more than
+        // one V-cycle per call)
         unsigned long long key = 1469598103934665603ull;
         for (unsigned long long v :
              {(unsigned long long)(uintptr_t)f, (unsigned long long)(uintptr_t)c,
@@ -872,16 +872,13 @@ bool device_decode(di_ctx* ctx, Sched& S, const float* f, const uint8_t* c, floa
             ctx->seen[ctx->seen_next] = key;
             ctx->seen_next = (ctx->seen_next + 1) % di_ctx::kSeen;
         }
-        if (ctx->misses >= 2 && !seen) return false;
-        ++ctx->misses;
+        if (victim->valid && !seen) return false;  // the cache is full
         drop_graph(*victim);
         if (!capture_decode(ctx, S, f, c, u, w, h, C, tol, *victim)) {
             ctx->device_path_broken = true;
             return false;
         }
         hit = victim;
-    } else {
-        ctx->misses = 0;
     }
     hit->used = ++ctx->graph_clock;
     cudaStream_t s = S.s;

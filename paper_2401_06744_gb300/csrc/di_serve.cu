@@ -347,6 +347,9 @@ constexpr int kSets = 3;
 struct ServerSlot {
     Slot s;  // context and decode stream
     cudaStream_t in_stream = nullptr, out_stream = nullptr;
+    // the copy stages wait on these (blocking, not spinning: a slot's three
+    // threads and the decoders' own waits would otherwise spin on the cores)
+    cudaEvent_t in_done = nullptr, out_done = nullptr;
     BufSet sets[kSets];
     Chan<int> free_sets;
     Chan<Request*> to_decode, to_output;
@@ -441,7 +444,8 @@ void input_stage(di_server* srv, ServerSlot* sl) {
                                    sl->in_stream) != cudaSuccess ||
                    cudaMemcpyAsync(b.c, r->c, px, cudaMemcpyHostToDevice, sl->in_stream) !=
                        cudaSuccess ||
-                   cudaStreamSynchronize(sl->in_stream) != cudaSuccess) {
+                   cudaEventRecord(sl->in_done, sl->in_stream) != cudaSuccess ||
+                   cudaEventSynchronize(sl->in_done) != cudaSuccess) {
             cudaGetLastError();
             r->status = DI_ERR_CUDA;
         }
@@ -480,7 +484,8 @@ void output_stage(di_server* srv, ServerSlot* sl) {
             const size_t pxch = (size_t)r->w * r->h * r->ch;
             if (cudaMemcpyAsync(r->u, b.u, pxch * sizeof(float), cudaMemcpyDeviceToHost,
                                 sl->out_stream) != cudaSuccess ||
-                cudaStreamSynchronize(sl->out_stream) != cudaSuccess) {
+                cudaEventRecord(sl->out_done, sl->out_stream) != cudaSuccess ||
+                cudaEventSynchronize(sl->out_done) != cudaSuccess) {
                 cudaGetLastError();
                 r->status = DI_ERR_CUDA;
             }
@@ -496,6 +501,8 @@ void free_server_slot(ServerSlot* sl) {
         if (b.u) cudaFree(b.u);
         if (b.c) cudaFree(b.c);
     }
+    if (sl->in_done) cudaEventDestroy(sl->in_done);
+    if (sl->out_done) cudaEventDestroy(sl->out_done);
     if (sl->in_stream) cudaStreamDestroy(sl->in_stream);
     if (sl->out_stream) cudaStreamDestroy(sl->out_stream);
     free_slot(&sl->s);
@@ -520,9 +527,12 @@ extern "C" di_status di_server_create(const di_config* cfg, int device, int slot
         if (!sl) { st = DI_ERR_OOM; break; }
         srv->slots.push_back(sl);
         st = make_slot(&srv->cfg, device, &sl->s);
+        const unsigned evf = cudaEventDisableTiming | cudaEventBlockingSync;
         if (st == DI_OK &&
             (cudaStreamCreateWithFlags(&sl->in_stream, cudaStreamNonBlocking) != cudaSuccess ||
-             cudaStreamCreateWithFlags(&sl->out_stream, cudaStreamNonBlocking) != cudaSuccess))
+             cudaStreamCreateWithFlags(&sl->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&sl->in_done, evf) != cudaSuccess ||
+             cudaEventCreateWithFlags(&sl->out_done, evf) != cudaSuccess))
             st = DI_ERR_CUDA;
         for (int b = 0; b < kSets; ++b) sl->free_sets.push(b);
     }
