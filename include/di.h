@@ -485,6 +485,22 @@ di_status di_oras_iteration(di_ctx *ctx, const float *u_in, const float *b, int 
                             const uint8_t *c, int width, int height, int channels,
                             int local_iters, float *u_out, void *stream);
 
+/* The V-cycle's correction step fused with the first post-smoothing
+ * iteration (Algorithm 1 with the prolongation of Section 4.4 and the ORAS
+ * iteration of Algorithm 2): u_out = ORAS(u_in + P uH), where P uH is added at
+ * the unknown pixels only, as di_prolong does in mode 1.  u_in is not
+ * modified.  The result equals di_prolong (mode 1) on a copy of u_in followed
+ * by di_oras_iteration, bit for bit; the decoder takes this form whenever it
+ * applies.
+ *  uH: [ch][ceil(h/2)][ceil(w/2)] coarse correction (FP32).
+ *  Other arguments as for di_oras_iteration.
+ * Requires the context's block size 32, FP32 precision and an even block
+ * stride (32 - overlap); DI_ERR_INVALID_ARG otherwise. */
+di_status di_prolong_oras_iteration(di_ctx *ctx, const float *uH, const float *u_in,
+                                    const float *b, int rhs_zero, const uint8_t *c, int width,
+                                    int height, int channels, int local_iters, float *u_out,
+                                    void *stream);
+
 /* Fault-path self test (no counterpart in the paper): launches one CTA that
  * waits, with the same bounded mbarrier wait as the 32x32 block kernel
  * (`limit` polls), on a barrier that nothing completes, and reports what the

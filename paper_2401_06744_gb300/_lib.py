@@ -131,6 +131,7 @@ _SIGS = {
     "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P]),
     "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
     "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
+    "di_prolong_oras_iteration": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     "di_selftest_bounded_wait": (_I, [_I, _I, _P]),
 }
 
@@ -322,6 +323,19 @@ class Context:
         st = load().di_oras_iteration(self._h, u3.data_ptr(), b3.data_ptr(), int(bool(rhs_zero)),
                                       c.data_ptr(), W, H, C, int(local_iters), uo.data_ptr(),
                                       _stream(stream))
+        _check(st, self)
+        return uo
+
+    def prolong_oras_iteration(self, uH, u_in, b, c, local_iters, rhs_zero=False, out=None,
+                               stream=None):
+        """One ORAS iteration from u_in + P uH (P uH added off the mask; u_in unchanged)."""
+        uH3, u3, b3, c = _img(uH, "uH"), _img(u_in, "u_in"), _img(b, "b"), _mask(c)
+        C, H, W = u3.shape
+        uo = torch.empty_like(u3) if out is None else _img(out, "out")
+        st = load().di_prolong_oras_iteration(self._h, uH3.data_ptr(), u3.data_ptr(),
+                                              b3.data_ptr(), int(bool(rhs_zero)), c.data_ptr(),
+                                              W, H, C, int(local_iters), uo.data_ptr(),
+                                              _stream(stream))
         _check(st, self)
         return uo
 

@@ -359,7 +359,8 @@ struct Sched {
     }
 
     di_status run_oras(int l, const float* in, int zero_in, float* out, int iters,
-                       unsigned* maxupd, float rtol2 = 0.f) {
+                       unsigned* maxupd, float rtol2 = 0.f, const float* pro_e = nullptr,
+                       unsigned* pro_max = nullptr) {
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);
@@ -392,21 +393,31 @@ struct Sched {
                                  ctx->planes, maxupd, s, ev, ctx->cfg.precision,
                                  ctx->upd + kMaxUpdSlots,
                                  l == 0 && ctx->cfg.profile ? ctx->dsteps : nullptr, stor(l),
-                                 f64(l)));
+                                 f64(l), pro_e, pro_max));
         return DI_OK;
+    }
+
+    // Whether level l's correction step (prolongation of level l + 1's
+    // correction) runs inside its first post-smoothing ORAS iteration.
+    bool fuse_prolong(int l) const {
+        const di_config& cfg = ctx->cfg;
+        return cfg.smoother == DI_SMOOTH_ORAS && cfg.block == 32 && cfg.post >= 1 &&
+               stor(l + 1) == kF32 && prolong_fusable(cfg.precision, cfg.overlap, 0);
     }
 
     // One smoothing call on level l (in -> out): an ORAS iteration, or
     // local_iters steps of global CG (restart = false continues the previous
     // CG call on the same level).
+    // pro_e, pro_max: the correction prolonged into the start (fuse_prolong).
     di_status smooth(int l, const float* in, int zero_in, float* out, unsigned* maxupd,
-                     bool restart = true) {
+                     bool restart = true, const float* pro_e = nullptr,
+                     unsigned* pro_max = nullptr) {
         const di_config& cfg = ctx->cfg;
         if (cfg.smoother == DI_SMOOTH_ORAS)
             return run_oras(l, in, zero_in, out,
                             l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
                                                                 : cfg.local_iters,
-                            maxupd, abs2 > 0.f ? -abs2 : 0.f);
+                            maxupd, abs2 > 0.f ? -abs2 : 0.f, pro_e, pro_max);
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);
@@ -446,6 +457,8 @@ struct Sched {
             DI_CUDA(ctx, cudaMemsetAsync(v.u[cur], 0, v.n * C * storage_bytes(stor(l)), s));
             zero = false;
         }
+        const float* pro_e = nullptr;  // correction prolonged inside the first post-smoothing
+        unsigned* pro_max = nullptr;
         if (l + 1 < Leff) {
             Level& cv = ctx->lv[l + 1];
             int rz;
@@ -455,12 +468,18 @@ struct Sched {
             int cw = 0;
             st = vcycle(l + 1, true, &cw, nullptr);
             if (st) return st;
-            DI_CUDA(ctx, launch_prolong(cv.u[cw], nullptr, v.c, v.w, v.h, C, v.u[cur], 1,
-                                        upd ? &upd[slot] : nullptr, s, stor(l + 1), stor(l)));
+            if (fuse_prolong(l)) {
+                pro_e = cv.u[cw];
+                pro_max = upd ? &upd[slot] : nullptr;
+            } else {
+                DI_CUDA(ctx, launch_prolong(cv.u[cw], nullptr, v.c, v.w, v.h, C, v.u[cur], 1,
+                                            upd ? &upd[slot] : nullptr, s, stor(l + 1), stor(l)));
+            }
         }
         ++slot;
         for (int k = 0; k < cfg.post; ++k) {
-            st = smooth(l, v.u[cur], 0, v.u[cur ^ 1], upd ? &upd[slot] : nullptr);
+            st = smooth(l, v.u[cur], 0, v.u[cur ^ 1], upd ? &upd[slot] : nullptr, true,
+                        k == 0 ? pro_e : nullptr, k == 0 ? pro_max : nullptr);
             if (st) return st;
             ++slot;
             cur ^= 1;
@@ -1431,6 +1450,35 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
                              u_out, ctx->planes, nullptr, s, nullptr, ctx->cfg.precision,
                              ctx->upd + kMaxUpdSlots, nullptr, kF32,
                              ctx->cfg.refine_fp64 != 0));
+    return DI_OK;
+}
+
+di_status di_prolong_oras_iteration(di_ctx* ctx, const float* uH, const float* u_in,
+                                    const float* b, int rhs_zero, const uint8_t* c, int width,
+                                    int height, int channels, int local_iters, float* u_out,
+                                    void* stream) {
+    if (!ctx || !uH || !u_in || !b || !c || !u_out || width < 1 || height < 1 || channels < 1 ||
+        channels > kMaxChannels || local_iters < 0 || ctx->cfg.block != 32 ||
+        !prolong_fusable(ctx->cfg.precision, ctx->cfg.overlap, 0))
+        return DI_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)width * height * channels * sizeof(float);
+    int wH, hH;
+    coarse_dims(width, height, &wH, &hH);
+    const size_t bytesH = (size_t)wH * hH * channels * sizeof(float);
+    if (overlaps(u_in, bytes, u_out, bytes) || overlaps(uH, bytesH, u_out, bytes))
+        return DI_ERR_INVALID_ARG;
+    DI_CUDA(ctx, cudaSetDevice(ctx->device));
+    di_status st = ensure_workspace(ctx, width, height, channels);
+    if (st) return st;
+    bind_levels(ctx, b, c, u_out, width, height, channels);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* bits = ctx->lv[0].mbits;
+    DI_CUDA(ctx, launch_pack_mask(c, width, height, bits, nullptr, s));
+    DI_CUDA(ctx, launch_oras(u_in, 0, b, rhs_zero ? 1 : 0, bits, width, height, channels, 32,
+                             ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f, u_out,
+                             ctx->planes, nullptr, s, nullptr, ctx->cfg.precision,
+                             ctx->upd + kMaxUpdSlots, nullptr, kF32, ctx->cfg.refine_fp64 != 0,
+                             uH, nullptr));
     return DI_OK;
 }
 

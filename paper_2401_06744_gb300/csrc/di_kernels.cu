@@ -626,7 +626,9 @@ __device__ __forceinline__ void restrict_body(const TU* __restrict__ u, const TB
             ++cnt;
         }
     }
-    stf(rH + ch * nH + P, (float)((R)4 * sum / (R)cnt));
+    // 4 sum / cnt with cnt in {1, 2, 4} (children inside the image): an exact
+    // power-of-two scaling, so a multiplication gives the quotient bit for bit
+    stf(rH + ch * nH + P, (float)(sum * (R)(4 >> (cnt >> 1))));
 }
 
 template <bool VEC, class TU, class TB, class TO, bool F64>
@@ -636,96 +638,6 @@ k_restrict(const TU* __restrict__ u, const TB* __restrict__ b, int rhs_zero,
            int hH) {
     restrict_body<VEC, TU, TB, TO, F64>(u, b, rhs_zero, w, h, cH, rH, wH, hH, blockIdx.x, blockIdx.y,
                                         blockIdx.z);
-}
-
-// The restriction of FP32 levels with a shared-memory tile: a CTA of 32 x 8
-// threads (one per coarse cell) first stages the fine rows 2Y0 - 1 .. 2Y0 + 16
-// and columns 2X0 - 2 .. 2X0 + 65 around its cells' children with coalesced
-// loads (8-byte words where VEC), zero outside the image; each thread then
-// reads its 4 x 4 patch from shared memory (the children's pair of columns as
-// one 8-byte word per row) and forms the same sums in the same order as
-// restrict_body, so the results are bit-identical.
-template <bool VEC, bool F64>
-__global__ void __launch_bounds__(256)
-k_restrict_tile(const float* __restrict__ u, const float* __restrict__ b, int rhs_zero, int w,
-                int h, const uint8_t* __restrict__ cH, float* __restrict__ rH, int wH, int hH) {
-    typedef typename std::conditional<F64, double, float>::type R;
-    constexpr int TR = 18, TC = 68;  // tile rows and columns (pitch)
-    __shared__ __align__(16) float tile[TR][TC];
-    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
-    const int ch = blockIdx.z;
-    const size_t n = (size_t)w * h, nH = (size_t)wH * hH;
-    const float* uc = u + ch * n;
-    const int fx0 = 2 * (int)blockIdx.x * 32 - 2, fy0 = 2 * (int)blockIdx.y * 8 - 1;
-    if (VEC) {
-        // 18 rows of 34 pairs; fx0 is even, so every pair is 8-byte aligned
-        for (int e = t; e < TR * (TC / 2); e += 256) {
-            const int r = e / (TC / 2), pc = e - r * (TC / 2);
-            const int y = fy0 + r, x = fx0 + 2 * pc;
-            float2 v = make_float2(0.f, 0.f);
-            if (y >= 0 && y < h) {
-                const float* row = uc + (size_t)y * w;
-                if (x >= 0 && x + 1 < w) v = *reinterpret_cast<const float2*>(row + x);
-                else {
-                    if (x >= 0 && x < w) v.x = row[x];
-                    if (x + 1 >= 0 && x + 1 < w) v.y = row[x + 1];
-                }
-            }
-            *reinterpret_cast<float2*>(&tile[r][2 * pc]) = v;
-        }
-    } else {
-        for (int e = t; e < TR * TC; e += 256) {
-            const int r = e / TC, cc = e - r * TC;
-            const int y = fy0 + r, x = fx0 + cc;
-            tile[r][cc] = (y >= 0 && y < h && x >= 0 && x < w) ? uc[(size_t)y * w + x] : 0.f;
-        }
-    }
-    __syncthreads();
-    const int X = (int)blockIdx.x * 32 + tx, Y = (int)blockIdx.y * 8 + ty;
-    if (X >= wH || Y >= hH) return;
-    const size_t P = (size_t)Y * wH + X;
-    if (cH[P]) { rH[ch * nH + P] = 0.f; return; }
-    const int x0 = 2 * X - 1, y0 = 2 * Y - 1;
-    // patch row j (fine row y0 + j) = tile row 2 ty + j; patch column i (fine
-    // column x0 + i) = tile column 2 tx + 1 + i
-    float t4[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float* tr = &tile[2 * ty + j][2 * tx];
-        const float2 mid = *reinterpret_cast<const float2*>(tr + 2);
-        t4[j][1] = mid.x;
-        t4[j][2] = mid.y;
-        const bool inner = j == 1 || j == 2;
-        t4[j][0] = inner ? tr[1] : 0.f;
-        t4[j][3] = inner ? tr[4] : 0.f;
-    }
-    R sum = 0;
-    int cnt = 0;
-#pragma unroll
-    for (int j = 1; j <= 2; ++j) {
-        float2 rb = make_float2(0.f, 0.f);
-        const int y = y0 + j;
-        if (!rhs_zero && y < h) {
-            const float* br = b + ch * n + (size_t)y * w + x0 + 1;
-            if (VEC) rb = *reinterpret_cast<const float2*>(br);
-            else {
-                rb.x = br[0];
-                if (x0 + 2 < w) rb.y = br[1];
-            }
-        }
-#pragma unroll
-        for (int i = 1; i <= 2; ++i) {
-            const int x = x0 + i;
-            if (x >= w || y >= h) continue;
-            const int deg = (x > 0) + (x < w - 1) + (y > 0) + (y < h - 1);
-            const R lu = (R)deg * (R)t4[j][i] -
-                         ((R)t4[j][i - 1] + (R)t4[j][i + 1] + (R)t4[j - 1][i] + (R)t4[j + 1][i]);
-            const R rhs = rhs_zero ? (R)0 : (R)(i == 1 ? rb.x : rb.y);
-            sum += rhs - lu;
-            ++cnt;
-        }
-    }
-    rH[ch * nH + P] = (float)((R)4 * sum / (R)cnt);
 }
 
 // Cell-centred bilinear prolongation.  A fine pixel takes 9/16 of its parent
@@ -740,6 +652,16 @@ k_restrict_tile(const float* __restrict__ u, const float* __restrict__ b, int rh
 // of u and b and one 2-byte word of c (w even, aligned base pointers; FP32 u).
 // uH is stored as TC and u as TF (FP16/BF16 on the coarse levels in the
 // 16-bit precision modes); b is FP32.
+// The bilinear weights of one fine pixel: cc its parent coarse cell, cn the
+// parent's vertical neighbour on the child's side, cs the horizontal one and
+// csn the diagonal one; (3 (3 cc + cn) + (3 cs + csn)) / 16 with every
+// rounding explicit, so that each kernel that prolongs gets the same bits.
+__device__ __forceinline__ float prolong_blend(float cc, float cn, float cs, float csn) {
+    const float vc = __fmaf_rn(3.f, cc, cn);
+    const float vs = __fmaf_rn(3.f, cs, csn);
+    return __fmul_rn(__fmaf_rn(3.f, vc, vs), 0.0625f);
+}
+
 template <bool VEC, class TC, class TF>
 __device__ __forceinline__ void prolong_body(const TC* __restrict__ uH, int wH, int hH, const float* __restrict__ b,
           const uint8_t* __restrict__ c, int w, int h, TF* __restrict__ u, int mode,
@@ -764,11 +686,8 @@ __device__ __forceinline__ void prolong_body(const TC* __restrict__ uH, int wH, 
         for (int dy = 0; dy < 2; ++dy) {
             const int y = 2 * Y + dy;
             if (y >= h) break;
-            const float v_l = 3.f * cl + (dy ? dl : ul);
-            const float v_c = 3.f * cc + (dy ? dc : uc);
-            const float v_r = 3.f * cr + (dy ? dr : ur);
-            const float a0 = (3.f * v_c + v_l) * (1.f / 16.f);
-            const float a1 = (3.f * v_c + v_r) * (1.f / 16.f);
+            const float a0 = prolong_blend(cc, dy ? dc : uc, cl, dy ? dl : ul);
+            const float a1 = prolong_blend(cc, dy ? dc : uc, cr, dy ? dr : ur);
             const size_t p = (size_t)y * w + x;
             if (VEC) {
                 const uchar2 cm = *reinterpret_cast<const uchar2*>(c + p);
@@ -779,8 +698,8 @@ __device__ __forceinline__ void prolong_body(const TC* __restrict__ uH, int wH, 
                     *up = make_float2(cm.x ? bv.x : a0, cm.y ? bv.y : a1);
                 } else {
                     float2 uv = *up;
-                    if (!cm.x) { uv.x += a0; amax = fmaxf(amax, fabsf(a0)); }
-                    if (!cm.y) { uv.y += a1; amax = fmaxf(amax, fabsf(a1)); }
+                    if (!cm.x) { uv.x = __fadd_rn(uv.x, a0); amax = fmaxf(amax, fabsf(a0)); }
+                    if (!cm.y) { uv.y = __fadd_rn(uv.y, a1); amax = fmaxf(amax, fabsf(a1)); }
                     *up = uv;
                 }
             } else {
@@ -793,7 +712,7 @@ __device__ __forceinline__ void prolong_body(const TC* __restrict__ uH, int wH, 
                     } else if (mode == 0) {
                         stf(ucn + p + dx, v);
                     } else {
-                        stf(ucn + p + dx, ldf(ucn + p + dx) + v);
+                        stf(ucn + p + dx, __fadd_rn(ldf(ucn + p + dx), v));
                         amax = fmaxf(amax, fabsf(v));
                     }
                 }
@@ -1384,7 +1303,15 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 // use_tma: the tiles come by TMA (tm_u over u_in, tm_b over rhs, both FP32
 // [C][h][w] with w a multiple of 4); otherwise by 4-byte cp.async.  errflag:
 // set to 1 if a TMA wait ran out (the CTA then stops).
-template <bool F64>
+// PRO: the iteration starts from u_in + P eH instead of u_in, the coarse
+// correction eH [C][hH][wH] prolonged as prolong_body does in mode 1 (added
+// at unknown pixels only), so that the V-cycle's correction step needs no
+// launch and no pass over the fine iterate of its own.  Each block adds the
+// prolongation to its tile (block pixels and halo) before the residual; the
+// largest |P eH| over the unknown pixels goes to *maxpro.  Needs u_in (not
+// zero_in) and an even block stride, so that the parity of a block pixel is
+// that of its tile index.
+template <bool F64, bool PRO>
 __global__ void __launch_bounds__(64, 8)
 k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
           int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
@@ -1392,7 +1319,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
           float* __restrict__ planes, unsigned* __restrict__ maxupd, int chan_inner,
           const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
           int use_tma, unsigned* __restrict__ errflag,
-          unsigned long long* __restrict__ step_count) {
+          unsigned long long* __restrict__ step_count, const float* __restrict__ eH, int wH,
+          int hH, unsigned* __restrict__ maxpro) {
     constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
     constexpr int TILE = Smem2W::USTRIDE;
     extern __shared__ float smem_raw[];
@@ -1515,7 +1443,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
     uint32_t rows_w = 0;  // bit ly: row ly of the block is in the image with weight > 0
-    float vmax = 0.f;
+    uint32_t mbk = 0;     // bit k: pixel (row0 + k, col) of the block is known or off the image
+    float vmax = 0.f, pmax = 0.f;
     unsigned nsteps = 0;  // completed local CG steps of this thread's tasks
 
     for (;;) {
@@ -1585,6 +1514,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
 #pragma unroll
             for (int k = 0; k < NP; ++k)
                 keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
+            mbk = mb;
             wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
             const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);  // row lane
             if (t < B) s_wy[t] = wyl;
@@ -1597,6 +1527,58 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         const int db = use_tma ? (x0 & 3) : 0;
         const float* tu = s_u + buf * TILE + du;
         const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
+        if constexpr (PRO) {
+            float* tw = s_u + buf * TILE + du;
+            const float* e = eH + (size_t)ch * wH * hH;
+            // the block pixels of this thread's column: x0 and y0 + row0 are
+            // even, so row row0 + k has parent row Yb + k / 2 and takes the
+            // coarse row above it (k even) or below it (k odd); the ten coarse
+            // rows Yb - 1 .. Yb + 8 (clamped) of the parent column X and of its
+            // neighbour Xn on the pixel's side come first
+            const int gx = x0 + col;
+            if (gx < w && (mbk & 0xffffu) != 0xffffu) {
+                const int X = gx >> 1;
+                const int Xn = (gx & 1) ? min(X + 1, wH - 1) : max(X - 1, 0);
+                const int Yb = (y0 + row0) >> 1;
+                float ec[10], es[10];
+#pragma unroll
+                for (int j = 0; j < 10; ++j) {
+                    const size_t rw = (size_t)min(max(Yb - 1 + j, 0), hH - 1) * wH;
+                    ec[j] = __ldg(e + rw + X);
+                    es[j] = __ldg(e + rw + Xn);
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    if ((mbk >> k) & 1u) continue;
+                    const int jc = (k >> 1) + 1, jn = (k & 1) ? jc + 1 : jc - 1;
+                    const float a = prolong_blend(ec[jc], ec[jn], es[jc], es[jn]);
+                    float* tp = tw + (row0 + k + 1) * P + col + 1;
+                    *tp = __fadd_rn(*tp, a);
+                    pmax = fmaxf(pmax, fabsf(a));
+                }
+            }
+            // the halo the residual reads: warp 0 the row above the block and
+            // the column left of it, warp 1 the row below and the column right
+            // of it, one pixel of each per lane (block pixels of a neighbouring
+            // block, which counts them in the maximum)
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int hy = side == 0 ? (wi == 0 ? y0 - 1 : y0 + B) : y0 + lane;
+                const int hx = side == 0 ? x0 + lane : (wi == 0 ? x0 - 1 : x0 + B);
+                if (hx < 0 || hx >= w || hy < 0 || hy >= h) continue;
+                if ((__ldg(mbits + (size_t)hy * wpr + (hx >> 5)) >> (hx & 31)) & 1u) continue;
+                const int X = hx >> 1, Y = hy >> 1;
+                const int Xn = (hx & 1) ? min(X + 1, wH - 1) : max(X - 1, 0);
+                const int Yn = (hy & 1) ? min(Y + 1, hH - 1) : max(Y - 1, 0);
+                const float* ry = e + (size_t)Y * wH;
+                const float* rn = e + (size_t)Yn * wH;
+                const float a = prolong_blend(__ldg(ry + X), __ldg(rn + X), __ldg(ry + Xn),
+                                              __ldg(rn + Xn));
+                float* tp = tw + (hy - y0 + 1) * P + (hx - x0 + 1);
+                *tp = __fadd_rn(*tp, a);
+            }
+            __syncthreads();  // the residual reads the other threads' columns
+        }
 
         f2 x[NP], r[NP], p[NP], q[NP];
         f2 acc0 = 0ull, acc1 = 0ull;
@@ -1787,6 +1769,10 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
     if (maxupd) {
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
+    }
+    if (PRO && maxpro) {
+        pmax = warp_max(pmax);
+        if (lane == 0 && pmax > 0.f) atomicMax(maxpro, __float_as_uint(pmax));
     }
 }
 
@@ -2871,13 +2857,19 @@ const void* oras_2w_h_fn() {
 // precision: 0 FP32 iterates (tiles by TMA where the image allows it), 1 FP16,
 // 2 BF16 iterates; stor: storage of u_in, rhs, u_out (kF32, or the iterate
 // type on the coarse levels of the 16-bit modes); f64: FP64 block residual.
+// pro_e: coarse correction prolonged into the iteration's start (FP32 only;
+// see k_oras_2w), largest |P e| into *pro_max.
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                            cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
-                           unsigned long long* step_count, int stor, bool f64) {
+                           unsigned long long* step_count, int stor, bool f64,
+                           const float* pro_e, unsigned* pro_max) {
     constexpr int B = 32;
     if (stor != kF32 && stor != precision) return cudaErrorInvalidValue;
+    if (pro_e && !prolong_fusable(precision, o, zero_in)) return cudaErrorInvalidValue;
+    int wH = 0, hH = 0;
+    coarse_dims(w, h, &wH, &hH);
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
     const int ntasks = nbx * nby * C;
     const int nblk = nbx * nby;
@@ -2893,7 +2885,9 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
                   (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
                   (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
         smem = Smem2W::bytes(!rhs_zero);
-        kern = f64 ? (const void*)k_oras_2w<true> : (const void*)k_oras_2w<false>;
+        kern = pro_e ? (f64 ? (const void*)k_oras_2w<true, true> : (const void*)k_oras_2w<false, true>)
+                     : (f64 ? (const void*)k_oras_2w<true, false>
+                            : (const void*)k_oras_2w<false, false>);
         oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true), &nsm);
     } else {
         smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) * sizeof(float);
@@ -2914,16 +2908,19 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     if (grid < 1) grid = 1;
     if (ev) record_event(ev[0], s);
     if (precision == 0) {
-        if (f64)
-            k_oras_2w<true><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h,
-                                                   C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                   planes, maxupd, chan_inner, tm_u, tm_b,
-                                                   use_tma, errflag, step_count);
-        else
-            k_oras_2w<false><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w,
-                                                    h, C, o, nbx, nby, alpha, iters, rtol2, u_out,
-                                                    planes, maxupd, chan_inner, tm_u, tm_b,
-                                                    use_tma, errflag, step_count);
+#define DI_ORAS_F(F, PR)                                                                         \
+    k_oras_2w<F, PR><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, \
+                                            nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd, \
+                                            chan_inner, tm_u, tm_b, use_tma, errflag, step_count, \
+                                            pro_e, wH, hH, pro_max)
+        if (pro_e) {
+            if (f64) DI_ORAS_F(true, true);
+            else DI_ORAS_F(false, true);
+        } else {
+            if (f64) DI_ORAS_F(true, false);
+            else DI_ORAS_F(false, false);
+        }
+#undef DI_ORAS_F
     } else {
 #define DI_ORAS_H(H, TU, F)                                                                     \
     run_oras_2w_h<H, TU, F>(grid, smem, s, u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, \
@@ -3155,15 +3152,17 @@ cudaError_t launch_restrict(const float* u, const float* b, int rhs_zero, const 
                      ((reinterpret_cast<uintptr_t>(u) |
                        reinterpret_cast<uintptr_t>(rhs_zero ? nullptr : b)) % 8 == 0);
     if (su == kF32 && sb == kF32 && sr == kF32) {
-        // the shared-memory tile kernel (bit-identical to the per-cell one)
         if (vec && f64)
-            k_restrict_tile<true, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
+            k_restrict<true, float, float, float, true><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else if (vec)
-            k_restrict_tile<true, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
+            k_restrict<true, float, float, float, false><<<grid, blk, 0, s>>>(
+                u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else if (f64)
-            k_restrict_tile<false, true><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
+            run_restrict<float, float, float, true>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH, hH);
         else
-            k_restrict_tile<false, false><<<grid, blk, 0, s>>>(u, b, rhs_zero, w, h, cH, rH, wH, hH);
+            run_restrict<float, float, float, false>(grid, blk, s, u, b, rhs_zero, w, h, cH, rH, wH,
+                                                     hH);
     } else if (su == kF32 && sb == kF32 && sr == kF16) {  // finest level, FP16 coarse levels
         if (vec && f64)
             k_restrict<true, float, float, __half, true><<<grid, blk, 0, s>>>(
@@ -3340,14 +3339,15 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
-                        unsigned long long* step_count, int stor, bool f64) {
+                        unsigned long long* step_count, int stor, bool f64, const float* pro_e,
+                        unsigned* pro_max) {
     const int wpr = mask_words_per_row(w);
-    if (B != 32 && (stor != kF32 || f64)) return cudaErrorInvalidValue;
+    if (B != 32 && (stor != kF32 || f64 || pro_e)) return cudaErrorInvalidValue;
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                   iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag,
-                                  step_count, stor, f64);
+                                  step_count, stor, f64, pro_e, pro_max);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev, step_count);

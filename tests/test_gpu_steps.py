@@ -267,3 +267,73 @@ def test_transfers_vector_and_scalar_paths_agree(di, h, w):
     pa = N(di.prolong(T(e), T(c), 0, b=T(fn)))
     pb = N(di.prolong(T(e), T(c), 0, b=_unaligned(fn)))
     assert np.array_equal(pa, pb)
+
+
+PRO_CASES = [  # (h, w, overlap, rhs_zero, aligned)
+    (70, 96, 2, True, True), (70, 96, 2, False, False), (70, 96, 6, False, True),
+    (33, 35, 2, False, True), (130, 100, 2, True, False), (61, 250, 6, True, True),
+    (1, 9, 2, False, True), (7, 1, 2, True, True), (3, 5, 6, False, False),
+    (17, 33, 2, False, True), (95, 64, 4, False, True),
+]
+
+
+@pytest.mark.parametrize("h,w,o,rhs_zero,aligned", PRO_CASES)
+def test_prolong_oras_iteration_bit_identical_to_two_steps(di, h, w, o, rhs_zero, aligned):
+    # the decoder's correction step inside the first post-smoothing iteration:
+    # the same bits as the prolongation (mode 1) on a copy followed by the
+    # plain iteration, through both tile paths (TMA where aligned) and the
+    # ragged right and bottom blocks
+    C = 3
+    f, fn, c = _case(h, w, C, 0.08, 31 * h + w + o)
+    g = np.random.default_rng(h + 7 * w)
+    H, W = M.coarse_shape(h, w)
+    if rhs_zero:
+        u = np.where(c.astype(bool), f, g.uniform(0, 255, f.shape)).astype(np.float32)
+        b = fn
+    else:
+        u = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+        b = np.where(c.astype(bool), 0.0, g.normal(size=f.shape)).astype(np.float32)
+    uH = g.normal(scale=4.0, size=(C, H, W)).astype(np.float32)
+    put = T if aligned else _unaligned
+    with di.Context(block=32, overlap=o) as ctx:
+        ut = put(u)
+        fused = N(ctx.prolong_oras_iteration(T(uH), ut, put(b), T(c), 8, rhs_zero=rhs_zero))
+        assert np.array_equal(N(ut), u)  # u_in is not modified
+        up = put(u)
+        di.prolong(T(uH), T(c), 1, u=up)
+        two = N(ctx.oras_iteration(up, put(b), T(c), 8, rhs_zero=rhs_zero))
+    assert np.array_equal(fused, two)
+    # and against the oracle's two steps
+    ref = M.oras_iteration(M.prolong_correct(u.astype(np.float64), uH, c),
+                           M.rhs(f, c) if rhs_zero else b, c, 32, o, 0.5, ("cg", 8))
+    start = M.prolong_correct(u.astype(np.float64), uH, c)
+    scale = np.abs(ref - start).max() + np.abs(start).max() * 1e-5
+    assert np.abs(fused - ref).max() < 1e-3 * scale + 2e-4
+
+
+def test_prolong_oras_iteration_4k_rgb(di):
+    # the finest level of the bench frames' size (3840 x 2160 x 3): bit-identical
+    # to the two steps
+    h, w, C = 2160, 3840, 3
+    g = torch.Generator(device=DEV).manual_seed(5)
+    c = (torch.rand((h, w), generator=g, device=DEV) < 0.04).to(torch.uint8)
+    f = torch.rand((C, h, w), generator=g, device=DEV) * 255
+    u = torch.where(c.bool(), f, torch.full_like(f, 128.0))
+    uH = torch.randn((C, (h + 1) // 2, (w + 1) // 2), generator=g, device=DEV) * 4
+    with di.Context(block=32, overlap=2) as ctx:
+        fused = ctx.prolong_oras_iteration(uH, u, f, c, 10, rhs_zero=True)
+        up = u.clone()
+        di.prolong(uH, c, 1, u=up)
+        two = ctx.oras_iteration(up, f, c, 10, rhs_zero=True)
+    torch.cuda.synchronize()
+    assert torch.equal(fused, two)
+
+
+@pytest.mark.parametrize("kw", [dict(block=32, overlap=3), dict(block=16, overlap=2),
+                                dict(block=32, overlap=2, precision=1)])
+def test_prolong_oras_iteration_rejects_other_configurations(di, kw):
+    f, fn, c = _case(40, 40, 1, 0.1, 3)
+    uH = np.zeros((1, 20, 20), np.float32)
+    with di.Context(**kw) as ctx:
+        with pytest.raises(di.DiError):
+            ctx.prolong_oras_iteration(T(uH), T(f), T(fn), T(c), 4, rhs_zero=True)
