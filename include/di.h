@@ -485,18 +485,23 @@ di_status di_oras_iteration(di_ctx *ctx, const float *u_in, const float *b, int 
                             const uint8_t *c, int width, int height, int channels,
                             int local_iters, float *u_out, void *stream);
 
-/* The V-cycle's correction step fused with the first post-smoothing
- * iteration (Algorithm 1 with the prolongation of Section 4.4 and the ORAS
- * iteration of Algorithm 2): u_out = ORAS(u_in + P uH), where P uH is added at
- * the unknown pixels only, as di_prolong does in mode 1.  u_in is not
- * modified.  The result equals di_prolong (mode 1) on a copy of u_in followed
- * by di_oras_iteration, bit for bit; the decoder takes this form whenever it
- * applies.
- *  uH: [ch][ceil(h/2)][ceil(w/2)] coarse correction (FP32).
+/* A prolongation (Section 4.4) fused with the ORAS iteration (Algorithm 2)
+ * that follows it in the method: u_out = ORAS(s) with the start s formed from
+ * u_in and P uH inside the block kernel, which the decoder does whenever this
+ * form applies.
+ *  mode 1 (the V-cycle's correction step before the first post-smoothing):
+ *         s = u_in + P uH at unknown pixels, u_in at mask pixels; equals
+ *         di_prolong (mode 1) on a copy of u_in followed by
+ *         di_oras_iteration, bit for bit.
+ *  mode 0 (the cascade's interpolation before its smoothing step, u_in = b):
+ *         s = u_in at mask pixels, P uH elsewhere (u_in not read there);
+ *         equals di_prolong (mode 0, b = u_in) followed by
+ *         di_oras_iteration, bit for bit.
+ *  uH: [ch][ceil(h/2)][ceil(w/2)] coarse field (FP32).  u_in is not modified.
  *  Other arguments as for di_oras_iteration.
  * Requires the context's block size 32, FP32 precision and an even block
  * stride (32 - overlap); DI_ERR_INVALID_ARG otherwise. */
-di_status di_prolong_oras_iteration(di_ctx *ctx, const float *uH, const float *u_in,
+di_status di_prolong_oras_iteration(di_ctx *ctx, const float *uH, int mode, const float *u_in,
                                     const float *b, int rhs_zero, const uint8_t *c, int width,
                                     int height, int channels, int local_iters, float *u_out,
                                     void *stream);

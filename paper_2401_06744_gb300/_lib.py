@@ -131,7 +131,7 @@ _SIGS = {
     "di_restrict_residual": (_I, [_P, _P, _I, _P, _I, _I, _I, _P, _P, _I, _P]),
     "di_prolong": (_I, [_P, _P, _P, _I, _I, _I, _P, _I, _P]),
     "di_oras_iteration": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
-    "di_prolong_oras_iteration": (_I, [_P, _P, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
+    "di_prolong_oras_iteration": (_I, [_P, _P, _I, _P, _P, _I, _P, _I, _I, _I, _I, _P, _P]),
     "di_selftest_bounded_wait": (_I, [_I, _I, _P]),
 }
 
@@ -327,12 +327,13 @@ class Context:
         return uo
 
     def prolong_oras_iteration(self, uH, u_in, b, c, local_iters, rhs_zero=False, out=None,
-                               stream=None):
-        """One ORAS iteration from u_in + P uH (P uH added off the mask; u_in unchanged)."""
+                               stream=None, mode=1):
+        """One ORAS iteration from a prolonged start (u_in unchanged): mode 1
+        u_in + P uH off the mask, mode 0 u_in on the mask and P uH off it."""
         uH3, u3, b3, c = _img(uH, "uH"), _img(u_in, "u_in"), _img(b, "b"), _mask(c)
         C, H, W = u3.shape
         uo = torch.empty_like(u3) if out is None else _img(out, "out")
-        st = load().di_prolong_oras_iteration(self._h, uH3.data_ptr(), u3.data_ptr(),
+        st = load().di_prolong_oras_iteration(self._h, uH3.data_ptr(), int(mode), u3.data_ptr(),
                                               b3.data_ptr(), int(bool(rhs_zero)), c.data_ptr(),
                                               W, H, C, int(local_iters), uo.data_ptr(),
                                               _stream(stream))

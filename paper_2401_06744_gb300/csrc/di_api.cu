@@ -360,7 +360,7 @@ struct Sched {
 
     di_status run_oras(int l, const float* in, int zero_in, float* out, int iters,
                        unsigned* maxupd, float rtol2 = 0.f, const float* pro_e = nullptr,
-                       unsigned* pro_max = nullptr) {
+                       unsigned* pro_max = nullptr, int pro_mode = 1) {
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);
@@ -393,31 +393,35 @@ struct Sched {
                                  ctx->planes, maxupd, s, ev, ctx->cfg.precision,
                                  ctx->upd + kMaxUpdSlots,
                                  l == 0 && ctx->cfg.profile ? ctx->dsteps : nullptr, stor(l),
-                                 f64(l), pro_e, pro_max));
+                                 f64(l), pro_e, pro_max, pro_mode));
         return DI_OK;
     }
 
-    // Whether level l's correction step (prolongation of level l + 1's
-    // correction) runs inside its first post-smoothing ORAS iteration.
+    // Whether a prolongation from level l + 1 to level l can run inside the
+    // ORAS iteration that follows it on level l (the V-cycle's correction
+    // step before the first post-smoothing, the cascade's interpolation
+    // before its smoothing step).
     bool fuse_prolong(int l) const {
         const di_config& cfg = ctx->cfg;
-        return cfg.smoother == DI_SMOOTH_ORAS && cfg.block == 32 && cfg.post >= 1 &&
-               stor(l + 1) == kF32 && prolong_fusable(cfg.precision, cfg.overlap, 0);
+        return cfg.smoother == DI_SMOOTH_ORAS && cfg.block == 32 && stor(l + 1) == kF32 &&
+               prolong_fusable(cfg.precision, cfg.overlap, 0);
     }
 
     // One smoothing call on level l (in -> out): an ORAS iteration, or
     // local_iters steps of global CG (restart = false continues the previous
     // CG call on the same level).
-    // pro_e, pro_max: the correction prolonged into the start (fuse_prolong).
+    // pro_e, pro_max, pro_mode: a coarser field prolonged into the start
+    // (fuse_prolong; mode 1 adds a correction, mode 0 interpolates a solution
+    // with in = b).
     di_status smooth(int l, const float* in, int zero_in, float* out, unsigned* maxupd,
                      bool restart = true, const float* pro_e = nullptr,
-                     unsigned* pro_max = nullptr) {
+                     unsigned* pro_max = nullptr, int pro_mode = 1) {
         const di_config& cfg = ctx->cfg;
         if (cfg.smoother == DI_SMOOTH_ORAS)
             return run_oras(l, in, zero_in, out,
                             l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
                                                                 : cfg.local_iters,
-                            maxupd, abs2 > 0.f ? -abs2 : 0.f, pro_e, pro_max);
+                            maxupd, abs2 > 0.f ? -abs2 : 0.f, pro_e, pro_max, pro_mode);
         const Level& v = ctx->lv[l];
         int rhs_zero;
         const float* rhs = rhs_of(l, &rhs_zero);
@@ -468,7 +472,7 @@ struct Sched {
             int cw = 0;
             st = vcycle(l + 1, true, &cw, nullptr);
             if (st) return st;
-            if (fuse_prolong(l)) {
+            if (cfg.post >= 1 && fuse_prolong(l)) {
                 pro_e = cv.u[cw];
                 pro_max = upd ? &upd[slot] : nullptr;
             } else {
@@ -664,6 +668,10 @@ bool capture_cascade(di_ctx* ctx, Sched& S, int Leff) {
         Level& v = lv[l];
         Level& cv = lv[l + 1];
         S.root = l;
+        if (S.fuse_prolong(l)) {
+            if (S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0)) return false;
+            continue;
+        }
         if (launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, S.s, S.stor(l + 1),
                            S.stor(l)))
             return false;
@@ -1194,8 +1202,12 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
                 st = S.vcycle(l, false, &which, nullptr);
                 if (st) return st;
                 if (which != 0) std::swap(v.u[0], v.u[1]);
+            } else if (S.fuse_prolong(l)) {
+                // reduced FMG and multilevel: one smoothing step per level,
+                // from b on the mask and the interpolated coarser solution
+                st = S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0);
+                if (st) return st;
             } else {
-                // reduced FMG and multilevel: one smoothing step per level
                 DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s,
                                             S.stor(l + 1), S.stor(l)));
                 st = S.smooth(l, v.u[1], 0, v.u[0], nullptr);
@@ -1453,12 +1465,13 @@ di_status di_oras_iteration(di_ctx* ctx, const float* u_in, const float* b, int 
     return DI_OK;
 }
 
-di_status di_prolong_oras_iteration(di_ctx* ctx, const float* uH, const float* u_in,
+di_status di_prolong_oras_iteration(di_ctx* ctx, const float* uH, int mode, const float* u_in,
                                     const float* b, int rhs_zero, const uint8_t* c, int width,
                                     int height, int channels, int local_iters, float* u_out,
                                     void* stream) {
     if (!ctx || !uH || !u_in || !b || !c || !u_out || width < 1 || height < 1 || channels < 1 ||
-        channels > kMaxChannels || local_iters < 0 || ctx->cfg.block != 32 ||
+        channels > kMaxChannels || local_iters < 0 || (mode != 0 && mode != 1) ||
+        ctx->cfg.block != 32 ||
         !prolong_fusable(ctx->cfg.precision, ctx->cfg.overlap, 0))
         return DI_ERR_INVALID_ARG;
     const size_t bytes = (size_t)width * height * channels * sizeof(float);
@@ -1478,7 +1491,7 @@ di_status di_prolong_oras_iteration(di_ctx* ctx, const float* uH, const float* u
                              ctx->cfg.overlap, ctx->cfg.alpha, local_iters, 0.f, u_out,
                              ctx->planes, nullptr, s, nullptr, ctx->cfg.precision,
                              ctx->upd + kMaxUpdSlots, nullptr, kF32, ctx->cfg.refine_fp64 != 0,
-                             uH, nullptr));
+                             uH, nullptr, mode));
     return DI_OK;
 }
 

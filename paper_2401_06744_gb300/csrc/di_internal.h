@@ -115,18 +115,19 @@ inline size_t oras_scratch_floats(int w, int h, int C, int B, int o) {
 // (nullable): gains the local CG steps completed, summed over the tasks.
 // stor: storage of u_in, rhs and u_out (kF32, or on the coarse levels of the
 // 16-bit modes the precision's type; 32x32 blocks only); f64: the block
-// residual in FP64.  pro_e (nullable): the next coarser level's FP32
-// correction, prolonged and added to u_in at the unknown pixels before the
-// iteration (the V-cycle's correction step, bit-identical to launch_prolong
-// in mode 1 followed by the plain iteration), with the largest |P e| into
-// *pro_max (nullable); only where prolong_fusable() holds.
+// residual in FP64.  pro_e (nullable): the next coarser level's FP32 field,
+// prolonged into the iteration's start, bit-identical to launch_prolong
+// followed by the plain iteration: pro_mode 1 adds P e to u_in at the unknown
+// pixels (the V-cycle's correction step; the largest |P e| into *pro_max,
+// nullable), pro_mode 0 takes u_in at the known pixels and P e at the others
+// (the cascade's interpolation, u_in = b); only where prolong_fusable() holds.
 cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                         const uint32_t* mbits, int w, int h, int C, int B, int o, float alpha,
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev = nullptr, int precision = 0,
                         unsigned* errflag = nullptr, unsigned long long* step_count = nullptr,
                         int stor = kF32, bool f64 = false, const float* pro_e = nullptr,
-                        unsigned* pro_max = nullptr);
+                        unsigned* pro_max = nullptr, int pro_mode = 1);
 
 // Whether the 32x32 block kernel can take the correction's prolongation:
 // FP32 iterates, an even block stride 32 - o (the pixel parities of every

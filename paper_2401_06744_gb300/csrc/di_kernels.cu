@@ -1240,18 +1240,24 @@ struct Tile2W {
 
 // Shared-memory layout of the FP32 kernel (floats, from a 128-byte aligned
 // base): two u tiles of TH rows with pitch PU (a 40-wide TMA box, or the
-// 34-wide cp.async copy at column 0), the row weights, then two right-hand
-// side tiles of B rows with pitch PB (36-wide TMA box).  Tile strides are
-// multiples of 128 bytes, the alignment of a TMA destination.
+// 34-wide cp.async copy at column 0), the row weights, with a prolongation
+// two patches of 18 x 18 coarse cells, then two right-hand side tiles of B
+// rows with pitch PB (36-wide TMA box).  Tile strides are multiples of 128
+// bytes, the alignment of a TMA destination.
 struct Smem2W {
     static constexpr int B = 32, TH = 34, PU = 40, PB = 36;
     static constexpr int USTRIDE = 1376;            // >= TH * PU, 128-byte multiple
     static constexpr int BSTRIDE = B * PB;          // 1152 floats = 4608 bytes
     static constexpr int WY = 2 * USTRIDE;          // row weights (32 floats)
     static constexpr int RHS = WY + 32;             // 128-byte aligned
+    static constexpr int EP = WY + 32;              // coarse patches (prolongation only)
+    static constexpr int EW = 18, ES = EW * EW;     // patch pitch and size
+    static constexpr int RHS_PRO = (EP + 2 * ES + 31) / 32 * 32;
     static constexpr int TMA_U_BYTES = TH * PU * 4; // 5440
     static constexpr int TMA_B_BYTES = B * PB * 4;  // 4608
-    static size_t bytes(bool rhs) { return 128 + 4 * (size_t)(RHS + (rhs ? 2 * BSTRIDE : 0)); }
+    static size_t bytes(bool rhs, bool pro = false) {
+        return 128 + 4 * (size_t)((pro ? RHS_PRO : RHS) + (rhs ? 2 * BSTRIDE : 0));
+    }
 };
 
 // Bounded wait for phase `parity` of the mbarrier at shared address `bar`;
@@ -1303,15 +1309,17 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 // use_tma: the tiles come by TMA (tm_u over u_in, tm_b over rhs, both FP32
 // [C][h][w] with w a multiple of 4); otherwise by 4-byte cp.async.  errflag:
 // set to 1 if a TMA wait ran out (the CTA then stops).
-// PRO: the iteration starts from u_in + P eH instead of u_in, the coarse
+// PRO = 1: the iteration starts from u_in + P eH instead of u_in, the coarse
 // correction eH [C][hH][wH] prolonged as prolong_body does in mode 1 (added
 // at unknown pixels only), so that the V-cycle's correction step needs no
-// launch and no pass over the fine iterate of its own.  Each block adds the
-// prolongation to its tile (block pixels and halo) before the residual; the
-// largest |P eH| over the unknown pixels goes to *maxpro.  Needs u_in (not
-// zero_in) and an even block stride, so that the parity of a block pixel is
-// that of its tile index.
-template <bool F64, bool PRO>
+// launch and no pass over the fine iterate of its own; the largest |P eH|
+// over the unknown pixels goes to *maxpro.  PRO = 2: the start is u_in at
+// the known pixels and P eH at the unknown ones (prolong_body's mode 0 with
+// u_in as b: the cascade's interpolation of the coarser level's solution).
+// Each block forms the start in its tile (block pixels and halo) before the
+// residual.  Needs u_in (not zero_in) and an even block stride, so that the
+// parity of a block pixel is that of its tile index.
+template <bool F64, int PRO>
 __global__ void __launch_bounds__(64, 8)
 k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__ rhs,
           int rhs_zero, const uint32_t* __restrict__ mbits, int wpr, int w, int h, int C, int o,
@@ -1328,7 +1336,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     float* const s_u = smem;                     // [2][USTRIDE]
     float* const s_wy = smem + Smem2W::WY;       // [B]
-    float* const s_b = smem + Smem2W::RHS;       // [2][BSTRIDE] if rhs_zero == 0
+    float* const s_e = smem + Smem2W::EP;        // [2][ES] if PRO
+    float* const s_b = smem + (PRO ? Smem2W::RHS_PRO : Smem2W::RHS);  // [2][BSTRIDE] if rhs_zero == 0
     __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
     __shared__ __align__(8) unsigned long long s_bar[2];
 
@@ -1358,8 +1367,35 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         return blk < nblk;
     };
     uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    uint32_t nhk = 3u;  // PRO: bit i = halo pixel i of this thread (next block) is known or off the image
     auto prefetch = [&](int blk, int ch, int bs, int have_blk) {
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
+        if constexpr (PRO != 0) {
+            // the coarse cells the task's prolongation reads: rows
+            // (py0 >> 1) - 1 + r and columns (px0 >> 1) - 1 + q, r, q < 18,
+            // each clamped to the level as the prolongation clamps its indices
+            const int Ys = (py0 >> 1) - 1, Xs = (px0 >> 1) - 1;
+            const float* e = eH + (size_t)ch * wH * hH;
+            float* dst = s_e + bs * Smem2W::ES;
+            for (int i = t; i < Smem2W::ES; i += 64) {
+                const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
+                const int Y = min(max(Ys + r, 0), hH - 1), X = min(max(Xs + q, 0), wH - 1);
+                cp_async4(dst + i, e + (size_t)Y * wH + X, true);
+            }
+            cp_async_commit();
+            if (blk != have_blk) {
+                // this thread's two halo pixels (see the prolongation below)
+                const int hy0 = wi == 0 ? py0 - 1 : py0 + B, hx0 = px0 + lane;
+                const int hy1 = py0 + lane, hx1 = wi == 0 ? px0 - 1 : px0 + B;
+                nhk = 3u;
+                if (hx0 >= 0 && hx0 < w && hy0 >= 0 && hy0 < h &&
+                    !((__ldg(mbits + (size_t)hy0 * wpr + (hx0 >> 5)) >> (hx0 & 31)) & 1u))
+                    nhk &= ~1u;
+                if (hx1 >= 0 && hx1 < w && hy1 >= 0 && hy1 < h &&
+                    !((__ldg(mbits + (size_t)hy1 * wpr + (hx1 >> 5)) >> (hx1 & 31)) & 1u))
+                    nhk &= ~2u;
+            }
+        }
         if (use_tma) {
             if (t == 0) {
                 const unsigned bar =
@@ -1452,6 +1488,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[buf]);
             bool ok = mbar_wait(bar, (phase >> buf) & 1u);
             phase ^= 1u << buf;
+            if constexpr (PRO != 0) cp_async_wait_all();  // the coarse patch
             if (__syncthreads_or(!ok)) {
                 // give the copy one more bounded wait before the CTA leaves
                 if (!ok) mbar_wait(bar, ((phase >> buf) & 1u) ^ 1u);
@@ -1462,7 +1499,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             cp_async_wait_all();
             __syncthreads();
         }
-        const uint32_t mlo = nlo, mhi = nhi;
+        const uint32_t mlo = nlo, mhi = nhi, hk = nhk;
         int nb2 = blk, nc2 = ch;
         const bool more = next_task(nb2, nc2);
         if (more) prefetch(nb2, nc2, buf ^ 1, blk);
@@ -1527,55 +1564,47 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         const int db = use_tma ? (x0 & 3) : 0;
         const float* tu = s_u + buf * TILE + du;
         const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
-        if constexpr (PRO) {
+        if constexpr (PRO != 0) {
+            // the start of the iteration in the tile: block pixels of this
+            // thread's column (x0 and y0 + row0 are even, so row row0 + k has
+            // parent patch row 1 + row0 / 2 + k / 2 and takes the coarse row
+            // above it for even k, below it for odd k; the column likewise),
+            // then the halo pixels the residual reads: warp 0 the row above
+            // the block and the column left of it, warp 1 the row below and
+            // the column right of it, one pixel of each per lane (block
+            // pixels of a neighbouring block, which counts them in the maximum)
+            constexpr int EW = Smem2W::EW;
             float* tw = s_u + buf * TILE + du;
-            const float* e = eH + (size_t)ch * wH * hH;
-            // the block pixels of this thread's column: x0 and y0 + row0 are
-            // even, so row row0 + k has parent row Yb + k / 2 and takes the
-            // coarse row above it (k even) or below it (k odd); the ten coarse
-            // rows Yb - 1 .. Yb + 8 (clamped) of the parent column X and of its
-            // neighbour Xn on the pixel's side come first
-            const int gx = x0 + col;
-            if (gx < w && (mbk & 0xffffu) != 0xffffu) {
-                const int X = gx >> 1;
-                const int Xn = (gx & 1) ? min(X + 1, wH - 1) : max(X - 1, 0);
-                const int Yb = (y0 + row0) >> 1;
-                float ec[10], es[10];
-#pragma unroll
-                for (int j = 0; j < 10; ++j) {
-                    const size_t rw = (size_t)min(max(Yb - 1 + j, 0), hH - 1) * wH;
-                    ec[j] = __ldg(e + rw + X);
-                    es[j] = __ldg(e + rw + Xn);
-                }
+            const float* pe = s_e + buf * Smem2W::ES;
+            // Branch-free (every patch index below stays inside the patch, and a
+            // pixel that is known or off the image keeps its tile value), so
+            // the loads of all pixels can be in flight together.
+            {
+                const int q = 1 + (col >> 1), qn = (col & 1) ? q + 1 : q - 1;
+                const float* pr = pe + (1 + (row0 >> 1)) * EW;
+                float* tc = tw + (row0 + 1) * P + col + 1;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    if ((mbk >> k) & 1u) continue;
-                    const int jc = (k >> 1) + 1, jn = (k & 1) ? jc + 1 : jc - 1;
-                    const float a = prolong_blend(ec[jc], ec[jn], es[jc], es[jn]);
-                    float* tp = tw + (row0 + k + 1) * P + col + 1;
-                    *tp = __fadd_rn(*tp, a);
-                    pmax = fmaxf(pmax, fabsf(a));
+                    const int r = (k >> 1) * EW, rn = (k & 1) ? r + EW : r - EW;
+                    const float a = prolong_blend(pr[r + q], pr[rn + q], pr[r + qn], pr[rn + qn]);
+                    const bool kn = (mbk >> k) & 1u;
+                    const float old = tc[k * P];
+                    tc[k * P] = kn ? old : (PRO == 1 ? __fadd_rn(old, a) : a);
+                    pmax = fmaxf(pmax, kn ? 0.f : fabsf(a));
                 }
             }
-            // the halo the residual reads: warp 0 the row above the block and
-            // the column left of it, warp 1 the row below and the column right
-            // of it, one pixel of each per lane (block pixels of a neighbouring
-            // block, which counts them in the maximum)
 #pragma unroll
             for (int side = 0; side < 2; ++side) {
                 const int hy = side == 0 ? (wi == 0 ? y0 - 1 : y0 + B) : y0 + lane;
                 const int hx = side == 0 ? x0 + lane : (wi == 0 ? x0 - 1 : x0 + B);
-                if (hx < 0 || hx >= w || hy < 0 || hy >= h) continue;
-                if ((__ldg(mbits + (size_t)hy * wpr + (hx >> 5)) >> (hx & 31)) & 1u) continue;
-                const int X = hx >> 1, Y = hy >> 1;
-                const int Xn = (hx & 1) ? min(X + 1, wH - 1) : max(X - 1, 0);
-                const int Yn = (hy & 1) ? min(Y + 1, hH - 1) : max(Y - 1, 0);
-                const float* ry = e + (size_t)Y * wH;
-                const float* rn = e + (size_t)Yn * wH;
-                const float a = prolong_blend(__ldg(ry + X), __ldg(rn + X), __ldg(ry + Xn),
-                                              __ldg(rn + Xn));
+                const int r = (hy >> 1) - (y0 >> 1) + 1, q = (hx >> 1) - (x0 >> 1) + 1;
+                const int rn = (hy & 1) ? r + 1 : r - 1, qn = (hx & 1) ? q + 1 : q - 1;
+                const float a = prolong_blend(pe[r * EW + q], pe[rn * EW + q], pe[r * EW + qn],
+                                              pe[rn * EW + qn]);
                 float* tp = tw + (hy - y0 + 1) * P + (hx - x0 + 1);
-                *tp = __fadd_rn(*tp, a);
+                const bool kn = (hk >> side) & 1u;  // known or off the image
+                const float old = *tp;
+                *tp = kn ? old : (PRO == 1 ? __fadd_rn(old, a) : a);
             }
             __syncthreads();  // the residual reads the other threads' columns
         }
@@ -1770,7 +1799,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(maxupd, __float_as_uint(vmax));
     }
-    if (PRO && maxpro) {
+    if (PRO == 1 && maxpro) {
         pmax = warp_max(pmax);
         if (lane == 0 && pmax > 0.f) atomicMax(maxpro, __float_as_uint(pmax));
     }
@@ -2857,17 +2886,20 @@ const void* oras_2w_h_fn() {
 // precision: 0 FP32 iterates (tiles by TMA where the image allows it), 1 FP16,
 // 2 BF16 iterates; stor: storage of u_in, rhs, u_out (kF32, or the iterate
 // type on the coarse levels of the 16-bit modes); f64: FP64 block residual.
-// pro_e: coarse correction prolonged into the iteration's start (FP32 only;
-// see k_oras_2w), largest |P e| into *pro_max.
+// pro_e: coarser level's correction (pro_mode 1) or solution (pro_mode 0)
+// prolonged into the iteration's start (FP32 only; see k_oras_2w), largest
+// |P e| of mode 1 into *pro_max.
 cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int rhs_zero,
                            const uint32_t* mbits, int wpr, int w, int h, int C, int o, float alpha,
                            int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                            cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
                            unsigned long long* step_count, int stor, bool f64,
-                           const float* pro_e, unsigned* pro_max) {
+                           const float* pro_e, unsigned* pro_max, int pro_mode) {
     constexpr int B = 32;
     if (stor != kF32 && stor != precision) return cudaErrorInvalidValue;
-    if (pro_e && !prolong_fusable(precision, o, zero_in)) return cudaErrorInvalidValue;
+    if (pro_e && (!prolong_fusable(precision, o, zero_in) || (pro_mode != 0 && pro_mode != 1)))
+        return cudaErrorInvalidValue;
+    const int pm = pro_e ? (pro_mode == 1 ? 1 : 2) : 0;  // the kernel's PRO
     int wH = 0, hH = 0;
     coarse_dims(w, h, &wH, &hH);
     const int nbx = axis_blocks(w, B, o), nby = axis_blocks(h, B, o);
@@ -2884,11 +2916,11 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
         use_tma = (!zero_in || !rhs_zero) &&
                   (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
                   (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
-        smem = Smem2W::bytes(!rhs_zero);
-        kern = pro_e ? (f64 ? (const void*)k_oras_2w<true, true> : (const void*)k_oras_2w<false, true>)
-                     : (f64 ? (const void*)k_oras_2w<true, false>
-                            : (const void*)k_oras_2w<false, false>);
-        oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true), &nsm);
+        smem = Smem2W::bytes(!rhs_zero, pm != 0);
+        kern = pm == 1 ? (f64 ? (const void*)k_oras_2w<true, 1> : (const void*)k_oras_2w<false, 1>)
+               : pm == 2 ? (f64 ? (const void*)k_oras_2w<true, 2> : (const void*)k_oras_2w<false, 2>)
+                         : (f64 ? (const void*)k_oras_2w<true, 0> : (const void*)k_oras_2w<false, 0>);
+        oc = cached_occupancy(kern, 64, smem, Smem2W::bytes(true, pm != 0), &nsm);
     } else {
         smem = ((size_t)Tile2W::FIXED + (rhs_zero ? 0 : (size_t)2 * B * B)) * sizeof(float);
         if (precision == 1)
@@ -2913,12 +2945,15 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
                                             nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd, \
                                             chan_inner, tm_u, tm_b, use_tma, errflag, step_count, \
                                             pro_e, wH, hH, pro_max)
-        if (pro_e) {
-            if (f64) DI_ORAS_F(true, true);
-            else DI_ORAS_F(false, true);
+        if (pm == 1) {
+            if (f64) DI_ORAS_F(true, 1);
+            else DI_ORAS_F(false, 1);
+        } else if (pm == 2) {
+            if (f64) DI_ORAS_F(true, 2);
+            else DI_ORAS_F(false, 2);
         } else {
-            if (f64) DI_ORAS_F(true, false);
-            else DI_ORAS_F(false, false);
+            if (f64) DI_ORAS_F(true, 0);
+            else DI_ORAS_F(false, 0);
         }
 #undef DI_ORAS_F
     } else {
@@ -3340,14 +3375,14 @@ cudaError_t launch_oras(const float* u_in, int zero_in, const float* rhs, int rh
                         int iters, float rtol2, float* u_out, float* planes, unsigned* maxupd,
                         cudaStream_t s, cudaEvent_t* ev, int precision, unsigned* errflag,
                         unsigned long long* step_count, int stor, bool f64, const float* pro_e,
-                        unsigned* pro_max) {
+                        unsigned* pro_max, int pro_mode) {
     const int wpr = mask_words_per_row(w);
     if (B != 32 && (stor != kF32 || f64 || pro_e)) return cudaErrorInvalidValue;
     switch (B) {
         case 32:
             return launch_oras_2w(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                   iters, rtol2, u_out, planes, maxupd, s, ev, precision, errflag,
-                                  step_count, stor, f64, pro_e, pro_max);
+                                  step_count, stor, f64, pro_e, pro_max, pro_mode);
         case 16:
             return launch_oras_t<16>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, alpha,
                                      iters, rtol2, u_out, planes, maxupd, s, ev, step_count);

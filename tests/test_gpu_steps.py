@@ -279,8 +279,8 @@ PRO_CASES = [  # (h, w, overlap, rhs_zero, aligned)
 
 @pytest.mark.parametrize("h,w,o,rhs_zero,aligned", PRO_CASES)
 def test_prolong_oras_iteration_bit_identical_to_two_steps(di, h, w, o, rhs_zero, aligned):
-    # the decoder's correction step inside the first post-smoothing iteration:
-    # the same bits as the prolongation (mode 1) on a copy followed by the
+    # the decoder's correction step inside the first post-smoothing iteration
+    # (mode 1): the same bits as the prolongation on a copy followed by the
     # plain iteration, through both tile paths (TMA where aligned) and the
     # ragged right and bottom blocks
     C = 3
@@ -304,11 +304,34 @@ def test_prolong_oras_iteration_bit_identical_to_two_steps(di, h, w, o, rhs_zero
         two = N(ctx.oras_iteration(up, put(b), T(c), 8, rhs_zero=rhs_zero))
     assert np.array_equal(fused, two)
     # and against the oracle's two steps
-    ref = M.oras_iteration(M.prolong_correct(u.astype(np.float64), uH, c),
-                           M.rhs(f, c) if rhs_zero else b, c, 32, o, 0.5, ("cg", 8))
     start = M.prolong_correct(u.astype(np.float64), uH, c)
+    ref = M.oras_iteration(start, M.rhs(f, c) if rhs_zero else b, c, 32, o, 0.5, ("cg", 8))
     scale = np.abs(ref - start).max() + np.abs(start).max() * 1e-5
     assert np.abs(fused - ref).max() < 1e-3 * scale + 2e-4
+
+
+@pytest.mark.parametrize("h,w,o,aligned", [(70, 96, 2, True), (70, 96, 6, False),
+                                           (33, 35, 2, True), (1, 9, 2, True),
+                                           (130, 100, 2, False), (61, 250, 4, True)])
+def test_prolong_oras_iteration_interpolation_bit_identical(di, h, w, o, aligned):
+    # the cascade's step (mode 0): u_in = b (not finite off the mask, where it
+    # must not be read), the start is b on the mask and P uH elsewhere
+    C = 3
+    f, fn, c = _case(h, w, C, 0.08, 17 * h + w + o)
+    g = np.random.default_rng(2 * h + w)
+    H, W = M.coarse_shape(h, w)
+    uH = g.uniform(0, 255, size=(C, H, W)).astype(np.float32)
+    put = T if aligned else _unaligned
+    with di.Context(block=32, overlap=o) as ctx:
+        fused = N(ctx.prolong_oras_iteration(T(uH), put(fn), put(fn), T(c), 8, rhs_zero=True,
+                                             mode=0))
+        start = di.prolong(T(uH), T(c), 0, b=put(fn))
+        two = N(ctx.oras_iteration(start, put(fn), T(c), 8, rhs_zero=True))
+    assert np.isfinite(fused).all()
+    assert np.array_equal(fused, two)
+    s0 = M.prolong_solution(uH, f, c)
+    ref = M.oras_iteration(s0, M.rhs(f, c), c, 32, o, 0.5, ("cg", 8))
+    assert np.abs(fused - ref).max() < 1e-3 * np.abs(ref - s0).max() + 2e-4
 
 
 def test_prolong_oras_iteration_4k_rgb(di):
