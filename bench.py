@@ -72,6 +72,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (8 bytes): its residual is formed from the staged tile and b = 0 off the mask.
 ORAS_MODEL_BYTES = 20
 ORAS_FUSED_BYTES = 8
+# A launch that also forms its start by prolongation (the V-cycle's correction
+# step, the cascade's interpolation) does the model's prolongation pass too:
+# 13 B per pixel-channel in the model; the kernel itself reads the coarse
+# field besides (1 B per pixel-channel: a quarter of the pixels, 4 B each).
+PROLONG_MODEL_BYTES = 13
+PROLONG_FUSED_BYTES = 1
 # DRAM traffic measured by ncu for the decode of the bench frames, with the
 # kernel sources it was taken on (read from the committed profile summary;
 # reported as null once the sources differ).
@@ -79,6 +85,30 @@ DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_4k_rgb_decode.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2401_06744_gb300", "csrc", n)
                   for n in ("di_kernels.cu", "di_internal.h")]
 LATENCY_FRAMES = 240
+
+
+def _link_gbs(dev) -> dict:
+    """Page-locked host <-> device copy rates (GB/s, 256 MB, CUDA events)."""
+    import torch
+
+    n = 256 << 20
+    h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d = torch.empty(n, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            fn()
+        z.record()
+        torch.cuda.synchronize(dev)
+        out[name] = round(5 * n / (a.elapsed_time(z) / 1e3) / 1e9, 1)
+    return out
 
 
 def _kernel_sha() -> str:
@@ -380,6 +410,7 @@ def run_ours(args):
                 raise RuntimeError(di.status_string(info["status"]))
 
     e2e_run(6 * S)  # warm-up: every slot's buffer sets and graphs
+    link = _link_gbs(dev)  # the host link's copy rate, which bounds this leg
     barrier()
     t0 = time.perf_counter()
     e2e_run(e2e_steps)
@@ -490,8 +521,9 @@ def run_ours(args):
     hbm_peak, hbm_src = _hbm_peak()
     # HBM view (the path's bound): the bytes model's 20 B per pixel-channel of
     # one ORAS iteration, and the 8 B the fused kernel itself must move
-    model_b = ORAS_MODEL_BYTES * pxch
-    fused_b = ORAS_FUSED_BYTES * pxch
+    pro_share = prof.get("oras_l0_prolong", 0) / n_l  # launches that also prolong
+    model_b = (ORAS_MODEL_BYTES + PROLONG_MODEL_BYTES * pro_share) * pxch
+    fused_b = (ORAS_FUSED_BYTES + PROLONG_FUSED_BYTES * pro_share) * pxch
     achieved = model_b / (avg_ms / 1e3) / 1e9
     # ALU view: local CG steps the local problems completed (blocks stop early
     # at the local_stop level), per local problem
@@ -508,11 +540,16 @@ def run_ours(args):
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(model_b),
                 "bytes_basis": f"{ORAS_MODEL_BYTES} B per pixel-channel per ORAS iteration "
-                               "(residual pass 8 + block pass 12, the whole-frame bytes model)",
+                               "(residual pass 8 + block pass 12, the whole-frame bytes model)"
+                               f" + {PROLONG_MODEL_BYTES} B of the model's prolongation pass "
+                               "on the launches that form their start by prolongation",
+                "prolong_launch_share": round(pro_share, 4),
                 "fused": {"bytes_per_launch": int(fused_b),
                           "gbs": round(fused_b / (avg_ms / 1e3) / 1e9, 1),
                           "frac": round(fused_b / (avg_ms / 1e3) / 1e9 / hbm_peak, 4),
-                          "basis": f"{ORAS_FUSED_BYTES} B per pixel-channel (read u, write u)"},
+                          "basis": f"{ORAS_FUSED_BYTES} B per pixel-channel (read u, write u)"
+                                   f" + {PROLONG_FUSED_BYTES} B (the coarse field) on the "
+                                   "prolonging launches"},
                 "alu": {"achieved_tflops": round(tflops, 3),
                         "peak_tflops": round(FP32_PEAK_TFLOPS, 1),
                         "frac": round(tflops / FP32_PEAK_TFLOPS, 4),
@@ -610,7 +647,12 @@ def run_ours(args):
                 "frames": e2e_steps,
                 "path": f"C ABI di_server_submit / di_server_wait, {S} slots, page-locked "
                         "host buffers, host wall clock from the first submit to the last "
-                        "result"},
+                        "result",
+                "link_gbs": link,
+                "link_bound": round(1e9 / (h2d / link["h2d"] + d2h / link["d2h"]), 1),
+                "link_note": "page-locked copies of 256 MB each way measured before the "
+                             "leg; link_bound = frames/s if copies in and out shared the "
+                             "link one after the other"},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -239,7 +239,9 @@ typedef struct {
     long long oras_l0_cg_steps;  /* local CG steps completed, summed over the local problems */
     long long oras_l0_tasks;     /* local problems (blocks x channels) of those launches */
     long long device_decodes;    /* decodes run as one device-driven graph (see di_inpaint) */
-    long long reserved[2];
+    long long oras_l0_prolong;   /* of the oras_l0 launches, those that also formed the
+                                    prolonged start (see di_prolong_oras_iteration) */
+    long long reserved[1];
 } di_profile;
 
 di_status di_get_profile(const di_ctx *ctx, di_profile *out);

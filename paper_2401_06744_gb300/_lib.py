@@ -56,7 +56,8 @@ class di_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("oras_l0_launches", ctypes.c_longlong),
                 ("oras_l0_ms", ctypes.c_double), ("oras_l0_pixel_channels", ctypes.c_longlong),
                 ("oras_l0_cg_steps", ctypes.c_longlong), ("oras_l0_tasks", ctypes.c_longlong),
-                ("device_decodes", ctypes.c_longlong), ("reserved", ctypes.c_longlong * 2)]
+                ("device_decodes", ctypes.c_longlong), ("oras_l0_prolong", ctypes.c_longlong),
+                ("reserved", ctypes.c_longlong * 1)]
 
 
 class di_image(ctypes.Structure):
@@ -299,7 +300,7 @@ class Context:
         return {"launches": pr.launches, "oras_l0_launches": pr.oras_l0_launches,
                 "oras_l0_ms": pr.oras_l0_ms, "oras_l0_pixel_channels": pr.oras_l0_pixel_channels,
                 "oras_l0_cg_steps": pr.oras_l0_cg_steps, "oras_l0_tasks": pr.oras_l0_tasks,
-                "device_decodes": pr.device_decodes}
+                "device_decodes": pr.device_decodes, "oras_l0_prolong": pr.oras_l0_prolong}
 
     def reset_profile(self):
         _check(load().di_reset_profile(self._h), self)

@@ -100,7 +100,7 @@ struct di_ctx {
     cudaEvent_t gev[kGPairs][2] = {};
     int g_pairs = 0;            // event pairs recorded by one replay
     long long g_kernels = 0;    // kernels launched by one replay
-    long long g_oras = 0, g_pxch = 0, g_tasks = 0;  // profile counters of one replay
+    long long g_oras = 0, g_pxch = 0, g_tasks = 0, g_pro = 0;  // profile counters of one replay
     unsigned long long* dsteps = nullptr;  // device: completed finest-level local CG steps
     // device-driven decode (see DecodeGraph): stop-test state on the device,
     // its pinned host copy, the capture streams of the graph and its bodies,
@@ -384,6 +384,7 @@ struct Sched {
                 ev = ctx->ev[ctx->ev_used++];
             }
             ctx->prof.oras_l0_launches += 1;
+            if (pro_e) ctx->prof.oras_l0_prolong += 1;
             ctx->prof.oras_l0_pixel_channels += (long long)v.n * C;
             ctx->prof.oras_l0_tasks += (long long)axis_blocks(v.w, ctx->cfg.block, ctx->cfg.overlap) *
                                        axis_blocks(v.h, ctx->cfg.block, ctx->cfg.overlap) * C;
@@ -528,6 +529,7 @@ bool capture_vcycle(di_ctx* ctx, Sched& S) {
     ctx->g_oras = ctx->prof.oras_l0_launches - p0.oras_l0_launches;
     ctx->g_pxch = ctx->prof.oras_l0_pixel_channels - p0.oras_l0_pixel_channels;
     ctx->g_tasks = ctx->prof.oras_l0_tasks - p0.oras_l0_tasks;
+    ctx->g_pro = ctx->prof.oras_l0_prolong - p0.oras_l0_prolong;
     ctx->prof = p0;
     if (st != DI_OK || e != cudaSuccess || g == nullptr || which != 0) {
         if (g) cudaGraphDestroy(g);
@@ -1253,6 +1255,7 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
             ctx->prof.oras_l0_launches += ctx->g_oras;
             ctx->prof.oras_l0_pixel_channels += ctx->g_pxch;
             ctx->prof.oras_l0_tasks += ctx->g_tasks;
+            ctx->prof.oras_l0_prolong += ctx->g_pro;
             if (cfg.profile && cfg.stop_rule == DI_STOP_FIXED_CYCLES) {
                 // the replay's event pairs are re-recorded by the next one
                 DI_CUDA(ctx, cudaStreamSynchronize(s));

@@ -1251,8 +1251,11 @@ struct Smem2W {
     static constexpr int WY = 2 * USTRIDE;          // row weights (32 floats)
     static constexpr int RHS = WY + 32;             // 128-byte aligned
     static constexpr int EP = WY + 32;              // coarse patches (prolongation only)
-    static constexpr int EW = 18, ES = EW * EW;     // patch pitch and size
-    static constexpr int RHS_PRO = (EP + 2 * ES + 31) / 32 * 32;
+    static constexpr int EW = 18, ES = EW * EW;     // patch side and cells
+    static constexpr int EPW = 24, EH = 18;         // patch pitch (a 24-wide TMA box) and rows
+    static constexpr int ESTRIDE = 448;             // >= EH * EPW, 128-byte multiple
+    static constexpr int RHS_PRO = EP + 2 * ESTRIDE;
+    static constexpr int TMA_E_BYTES = EH * EPW * 4;  // 1728
     static constexpr int TMA_U_BYTES = TH * PU * 4; // 5440
     static constexpr int TMA_B_BYTES = B * PB * 4;  // 4608
     static size_t bytes(bool rhs, bool pro = false) {
@@ -1308,7 +1311,8 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
 
 // use_tma: the tiles come by TMA (tm_u over u_in, tm_b over rhs, both FP32
 // [C][h][w] with w a multiple of 4); otherwise by 4-byte cp.async.  errflag:
-// set to 1 if a TMA wait ran out (the CTA then stops).
+// set to 1 if a TMA wait ran out (the CTA then stops).  use_tma_e (only with
+// use_tma): the coarse patches of PRO come by TMA too (tm_e over eH).
 // PRO = 1: the iteration starts from u_in + P eH instead of u_in, the coarse
 // correction eH [C][hH][wH] prolonged as prolong_body does in mode 1 (added
 // at unknown pixels only), so that the V-cycle's correction step needs no
@@ -1328,7 +1332,8 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
           const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_b,
           int use_tma, unsigned* __restrict__ errflag,
           unsigned long long* __restrict__ step_count, const float* __restrict__ eH, int wH,
-          int hH, unsigned* __restrict__ maxpro) {
+          int hH, unsigned* __restrict__ maxpro, const __grid_constant__ CUtensorMap tm_e,
+          int use_tma_e) {
     constexpr int B = 32, NP = 8, TH = Smem2W::TH, P = Smem2W::PU, PB = Smem2W::PB;
     constexpr int TILE = Smem2W::USTRIDE;
     extern __shared__ float smem_raw[];
@@ -1372,17 +1377,20 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         const int px0 = (blk % nbx) * s, py0 = (blk / nbx) * s;
         if constexpr (PRO != 0) {
             // the coarse cells the task's prolongation reads: rows
-            // (py0 >> 1) - 1 + r and columns (px0 >> 1) - 1 + q, r, q < 18,
-            // each clamped to the level as the prolongation clamps its indices
-            const int Ys = (py0 >> 1) - 1, Xs = (px0 >> 1) - 1;
-            const float* e = eH + (size_t)ch * wH * hH;
-            float* dst = s_e + bs * Smem2W::ES;
-            for (int i = t; i < Smem2W::ES; i += 64) {
-                const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
-                const int Y = min(max(Ys + r, 0), hH - 1), X = min(max(Xs + q, 0), wH - 1);
-                cp_async4(dst + i, e + (size_t)Y * wH + X, true);
+            // (py0 >> 1) - 1 + r and columns (px0 >> 1) - 1 + q, r, q < 18
+            // (with TMA, the box issued below; here each cell is clamped to
+            // the level as the prolongation clamps its indices)
+            if (!use_tma_e) {
+                const int Ys = (py0 >> 1) - 1, Xs = (px0 >> 1) - 1;
+                const float* e = eH + (size_t)ch * wH * hH;
+                float* dst = s_e + bs * Smem2W::ESTRIDE;
+                for (int i = t; i < Smem2W::ES; i += 64) {
+                    const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
+                    const int Y = min(max(Ys + r, 0), hH - 1), X = min(max(Xs + q, 0), wH - 1);
+                    cp_async4(dst + r * Smem2W::EPW + q, e + (size_t)Y * wH + X, true);
+                }
+                cp_async_commit();
             }
-            cp_async_commit();
             if (blk != have_blk) {
                 // this thread's two halo pixels (see the prolongation below)
                 const int hy0 = wi == 0 ? py0 - 1 : py0 + B, hx0 = px0 + lane;
@@ -1401,7 +1409,9 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 const unsigned bar =
                     (unsigned)__cvta_generic_to_shared(&s_bar[bs]);
                 const unsigned bytes = (zero_in ? 0u : (unsigned)Smem2W::TMA_U_BYTES) +
-                                       (rhs_zero ? 0u : (unsigned)Smem2W::TMA_B_BYTES);
+                                       (rhs_zero ? 0u : (unsigned)Smem2W::TMA_B_BYTES) +
+                                       (PRO != 0 && use_tma_e ? (unsigned)Smem2W::TMA_E_BYTES
+                                                              : 0u);
                 // the buffer's previous contents were read before the loop-top barrier
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
@@ -1414,6 +1424,12 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 if (!rhs_zero)
                     tma_load_3d((unsigned)__cvta_generic_to_shared(s_b + bs * Smem2W::BSTRIDE),
                                 &tm_b, px0 & ~3, py0, ch, bar);
+                // the coarse patch from the 4-aligned column at or below its
+                // first one (cells off the level read 0 and are fixed up
+                // where the task starts)
+                if (PRO != 0 && use_tma_e)
+                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_e + bs * Smem2W::ESTRIDE),
+                                &tm_e, ((px0 >> 1) - 1) & ~3, (py0 >> 1) - 1, ch, bar);
             }
         } else if (!zero_in) {
             // thread t copies tile column lane of the rows ty = wi, wi + 2, ...
@@ -1573,9 +1589,24 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             // the block and the column left of it, warp 1 the row below and
             // the column right of it, one pixel of each per lane (block
             // pixels of a neighbouring block, which counts them in the maximum)
-            constexpr int EW = Smem2W::EW;
+            constexpr int EW = Smem2W::EPW;  // patch pitch
             float* tw = s_u + buf * TILE + du;
-            const float* pe = s_e + buf * Smem2W::ES;
+            const int Ys = (y0 >> 1) - 1, Xs = (x0 >> 1) - 1;
+            // TMA patches start at the 4-aligned column at or below Xs
+            const int dqe = use_tma_e ? Xs - (Xs & ~3) : 0;
+            float* const pw = s_e + buf * Smem2W::ESTRIDE + dqe;
+            if (use_tma_e && (Ys < 0 || Xs < 0 || Ys + Smem2W::EW > hH || Xs + Smem2W::EW > wH)) {
+                // a block at the level's border: the cells off the level
+                // (read as 0) take the value of their clamped cell, which is
+                // on the level and not itself rewritten
+                for (int i = t; i < Smem2W::ES; i += 64) {
+                    const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
+                    const int Yc = min(max(Ys + r, 0), hH - 1), Xc = min(max(Xs + q, 0), wH - 1);
+                    if (Yc != Ys + r || Xc != Xs + q) pw[r * EW + q] = pw[(Yc - Ys) * EW + (Xc - Xs)];
+                }
+                __syncthreads();  // block-uniform branch
+            }
+            const float* pe = pw;
             // Branch-free (every patch index below stays inside the patch, and a
             // pixel that is known or off the image keeps its tile value), so
             // the loads of all pixels can be in flight together.
@@ -2908,14 +2939,17 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     int nsm = 0, oc = 0;
     size_t smem = 0;
     const void* kern = nullptr;
-    CUtensorMap tm_u, tm_b;
+    CUtensorMap tm_u, tm_b, tm_e;
     std::memset(&tm_u, 0, sizeof tm_u);
     std::memset(&tm_b, 0, sizeof tm_b);
-    int use_tma = 0;
+    std::memset(&tm_e, 0, sizeof tm_e);
+    int use_tma = 0, use_tma_e = 0;
     if (precision == 0) {
         use_tma = (!zero_in || !rhs_zero) &&
                   (zero_in || make_map(&tm_u, u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
                   (rhs_zero || make_map(&tm_b, rhs, w, h, C, Smem2W::PB, B));
+        use_tma_e = use_tma && pm != 0 &&
+                    make_map(&tm_e, pro_e, wH, hH, C, Smem2W::EPW, Smem2W::EH);
         smem = Smem2W::bytes(!rhs_zero, pm != 0);
         kern = pm == 1 ? (f64 ? (const void*)k_oras_2w<true, 1> : (const void*)k_oras_2w<false, 1>)
                : pm == 2 ? (f64 ? (const void*)k_oras_2w<true, 2> : (const void*)k_oras_2w<false, 2>)
@@ -2944,7 +2978,7 @@ cudaError_t launch_oras_2w(const float* u_in, int zero_in, const float* rhs, int
     k_oras_2w<F, PR><<<grid, 64, smem, s>>>(u_in, zero_in, rhs, rhs_zero, mbits, wpr, w, h, C, o, \
                                             nbx, nby, alpha, iters, rtol2, u_out, planes, maxupd, \
                                             chan_inner, tm_u, tm_b, use_tma, errflag, step_count, \
-                                            pro_e, wH, hH, pro_max)
+                                            pro_e, wH, hH, pro_max, tm_e, use_tma_e)
         if (pm == 1) {
             if (f64) DI_ORAS_F(true, 1);
             else DI_ORAS_F(false, 1);

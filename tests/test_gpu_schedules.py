@@ -174,6 +174,7 @@ def test_graph_replay_matches_direct_launches(di, case, stop):
     assert p0["launches"] == p1["launches"] and p0["launches"] > 0
     assert p0["oras_l0_launches"] == p1["oras_l0_launches"]
     assert p0["oras_l0_cg_steps"] == p1["oras_l0_cg_steps"]
+    assert p0["oras_l0_prolong"] == p1["oras_l0_prolong"]
     assert p0["oras_l0_ms"] > 0 and p1["oras_l0_ms"] > 0
 
 
@@ -214,7 +215,13 @@ def test_profile_counts_completed_local_steps(di, case):
             ctx.inpaint(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), tol=TOL)
             torch.cuda.synchronize()
             pr = ctx.profile()
+            st = ctx.stats()
         assert pr["oras_l0_tasks"] > 0
         assert 0 < pr["oras_l0_cg_steps"] <= 8 * pr["oras_l0_tasks"]  # default local_iters 8
+        # the finest level's prolongations run inside its block kernel (32x32
+        # blocks, even stride): the cascade's interpolation once, and one
+        # correction per V-cycle where a coarser level carries unknowns
+        assert st["levels"] >= 2
+        assert pr["oras_l0_prolong"] == 1 + (st["cycles"] if st["levels_used"] >= 2 else 0)
         per_task[ls] = pr["oras_l0_cg_steps"] / pr["oras_l0_tasks"]
     assert per_task[0.2] <= per_task[-1.0]

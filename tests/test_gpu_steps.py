@@ -273,7 +273,8 @@ PRO_CASES = [  # (h, w, overlap, rhs_zero, aligned)
     (70, 96, 2, True, True), (70, 96, 2, False, False), (70, 96, 6, False, True),
     (33, 35, 2, False, True), (130, 100, 2, True, False), (61, 250, 6, True, True),
     (1, 9, 2, False, True), (7, 1, 2, True, True), (3, 5, 6, False, False),
-    (17, 33, 2, False, True), (95, 64, 4, False, True),
+    (17, 33, 2, False, True), (95, 64, 4, False, True), (71, 96, 2, False, True),
+    (129, 160, 6, True, True),
 ]
 
 
