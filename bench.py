@@ -781,9 +781,21 @@ def run_kernel(args):
         if args.kernel == "oras":
             u1 = ctx.oras_iteration(u0, ft, ct, args.local_iters, rhs_zero=True)
             out["max_update"] = float((u1 - u0).abs().max())
+        elif args.kernel == "oras_prolong":
+            # the V-cycle's correction step: a smooth coarse correction
+            # prolonged inside the first post-smoothing iteration
+            hH, wH = (H4K + 1) // 2, (W4K + 1) // 2
+            yy = torch.arange(hH, device=dev, dtype=torch.float32)[:, None]
+            xx = torch.arange(wH, device=dev, dtype=torch.float32)[None, :]
+            e = torch.sin(yy / 37.0) * torch.cos(xx / 53.0)
+            e = e.expand(C4K, hH, wH).contiguous()
+            u1 = ctx.prolong_oras_iteration(e, u0, ft, ct, args.local_iters, rhs_zero=True)
+            out["max_update"] = float((u1 - u0).abs().max())
         elif args.kernel == "prolong":
             e = torch.ones(C4K, (H4K + 1) // 2, (W4K + 1) // 2, device=dev)
             di.prolong(e, ct, 1, u=u0)
+        elif args.kernel == "pyramid":
+            di.pyramid_level(ct, ft)
         elif args.kernel == "restrict":
             cH = di.mask_downsample(ct)
             di.restrict_residual(u0, ft, ct, cH, rhs_zero=True)
@@ -1134,7 +1146,8 @@ def main():
                     help="omit the decode with the paper's solver setting (after the timed region)")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
                     help="storage of the block-local CG iterates (default fp32)")
-    ap.add_argument("--kernel", choices=["oras", "prolong", "restrict", "residual"],
+    ap.add_argument("--kernel", choices=["oras", "oras_prolong", "prolong", "restrict",
+                                         "residual", "pyramid"],
                     help="run one launch of this step on one 4K RGB frame (for ncu) and exit")
     ap.add_argument("--block", type=int, default=BLOCK, help="ORAS block side")
     ap.add_argument("--overlap", type=int, default=OVERLAP, help="ORAS block overlap")

@@ -1608,19 +1608,28 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             }
             const float* pe = pw;
             // Branch-free (every patch index below stays inside the patch, and a
-            // pixel that is known or off the image keeps its tile value), so
-            // the loads of all pixels can be in flight together.
+            // pixel that is known or off the image keeps its tile value).  The
+            // ten patch rows of both columns and the sixteen tile values are
+            // read before anything is stored (the stores could alias them
+            // otherwise), so the loads are in flight together.
             {
                 const int q = 1 + (col >> 1), qn = (col & 1) ? q + 1 : q - 1;
-                const float* pr = pe + (1 + (row0 >> 1)) * EW;
+                const float* pr = pe + (row0 >> 1) * EW;  // patch row of coarse row Yb - 1
                 float* tc = tw + (row0 + 1) * P + col + 1;
+                float ec[10], es[10], tv[16];
+#pragma unroll
+                for (int j = 0; j < 10; ++j) {
+                    ec[j] = pr[j * EW + q];
+                    es[j] = pr[j * EW + qn];
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) tv[k] = tc[k * P];
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    const int r = (k >> 1) * EW, rn = (k & 1) ? r + EW : r - EW;
-                    const float a = prolong_blend(pr[r + q], pr[rn + q], pr[r + qn], pr[rn + qn]);
+                    const int jc = (k >> 1) + 1, jn = (k & 1) ? jc + 1 : jc - 1;
+                    const float a = prolong_blend(ec[jc], ec[jn], es[jc], es[jn]);
                     const bool kn = (mbk >> k) & 1u;
-                    const float old = tc[k * P];
-                    tc[k * P] = kn ? old : (PRO == 1 ? __fadd_rn(old, a) : a);
+                    tc[k * P] = kn ? tv[k] : (PRO == 1 ? __fadd_rn(tv[k], a) : a);
                     pmax = fmaxf(pmax, kn ? 0.f : fabsf(a));
                 }
             }
