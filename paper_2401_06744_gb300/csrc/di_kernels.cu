@@ -202,7 +202,7 @@ __device__ __forceinline__ void values_down_body(const uint8_t* __restrict__ c, 
         float num = 0.f;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (wt[k] != 0.f) num += wt[k] * bc[idx[k]];
+            if (wt[k] != 0.f) num = __fmaf_rn(wt[k], bc[idx[k]], num);
         bH[ch * nH + P] = num * inv;
     }
 }
@@ -218,32 +218,60 @@ __global__ void k_values_down(const uint8_t* __restrict__ c, const float* __rest
 // naive downsampling, the same weights and sums as values_down_body), and the
 // warp of 32 consecutive X packs the 32 mask bits of its row (known or beyond
 // the image = 1) and counts the unknown ones; the CTAs of the last column
-// write the padding word of their rows.  The neighbouring coarse cells'
-// masks that the modified weights need are formed from the fine mask too, so
-// the level needs no second pass.  values = 0: masks only (a given start).
+// write the padding word of their rows.  Each thread reads its four children's
+// mask bytes once (8-byte aligned pairs where the image allows); the modified
+// weights take the four neighbouring coarse cells' masks from a shared tile
+// of the CTA's cells and their one-cell halo, so the level needs no second
+// pass.  values = 0: masks only (a given start).
 __global__ void __launch_bounds__(256)
 k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int w, int h, int C,
                 uint8_t* __restrict__ cH, float* __restrict__ bH, int wH, int hH, int modified,
                 int values, uint32_t* __restrict__ bits, int wpr,
                 unsigned long long* __restrict__ unknown) {
-    const int X = blockIdx.x * 32 + threadIdx.x;
-    const int Y = blockIdx.y * 8 + threadIdx.y;
-    const int lane = threadIdx.x;
-    // coarse cell (Xc, Yc) known: any of its in-image children known
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int X = blockIdx.x * 32 + tx;
+    const int Y = blockIdx.y * 8 + ty;
+    const int lane = tx;
+    // children bytes of coarse cell (Xc, Yc), 0 where a child is off the image
+    const bool pairs = (w & 1) == 0 && (reinterpret_cast<uintptr_t>(c) & 1) == 0;
+    auto children = [&](int Xc, int Yc, uint32_t& c00, uint32_t& c01, uint32_t& c10,
+                        uint32_t& c11) {
+        const int x = 2 * Xc, y = 2 * Yc;
+        const uint8_t* row = c + (size_t)y * w + x;
+        const bool y1 = y + 1 < h;
+        if (pairs) {
+            const uchar2 r0 = *reinterpret_cast<const uchar2*>(row);
+            const uchar2 r1 = y1 ? *reinterpret_cast<const uchar2*>(row + w) : make_uchar2(0, 0);
+            c00 = r0.x; c01 = r0.y; c10 = r1.x; c11 = r1.y;
+        } else {
+            const bool x1 = x + 1 < w;
+            c00 = row[0];
+            c01 = x1 ? row[1] : 0u;
+            c10 = y1 ? row[w] : 0u;
+            c11 = (x1 && y1) ? row[w + 1] : 0u;
+        }
+    };
     auto known = [&](int Xc, int Yc) -> bool {
         if (Xc < 0 || Xc >= wH || Yc < 0 || Yc >= hH) return false;
-        const int x = 2 * Xc, y = 2 * Yc;
-        const uint8_t* row = c + (size_t)y * w;
-        bool m = row[x] != 0;
-        if (x + 1 < w) m |= row[x + 1] != 0;
-        if (y + 1 < h) {
-            m |= row[x + w] != 0;
-            if (x + 1 < w) m |= row[x + w + 1] != 0;
-        }
-        return m;
+        uint32_t a0, a1, a2, a3;
+        children(Xc, Yc, a0, a1, a2, a3);
+        return (a0 | a1 | a2 | a3) != 0u;
     };
     const bool inside = X < wH && Y < hH;
-    const bool kn = inside && known(X, Y);
+    uint32_t ck[4] = {0u, 0u, 0u, 0u};
+    if (inside) children(X, Y, ck[0], ck[1], ck[2], ck[3]);
+    const bool kn = (ck[0] | ck[1] | ck[2] | ck[3]) != 0u;
+    // masks of the CTA's coarse cells and their direct neighbours
+    __shared__ uint8_t s_kn[10][34];
+    const bool nbrs = values && modified;  // uniform over the grid
+    if (nbrs) {
+        s_kn[ty + 1][tx + 1] = kn ? 1 : 0;
+        if (ty == 0) s_kn[0][tx + 1] = known(X, Y - 1) ? 1 : 0;
+        if (ty == 7) s_kn[9][tx + 1] = known(X, Y + 1) ? 1 : 0;
+        if (tx == 0) s_kn[ty + 1][0] = known(X - 1, Y) ? 1 : 0;
+        if (tx == 31) s_kn[ty + 1][33] = known(X + 1, Y) ? 1 : 0;
+        __syncthreads();
+    }
     if (inside) {
         const size_t nH = (size_t)wH * hH, P = (size_t)Y * wH + X;
         cH[P] = kn ? 1 : 0;
@@ -252,28 +280,21 @@ k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int 
             if (!kn) {
                 for (int ch = 0; ch < C; ++ch) bH[ch * nH + P] = 0.f;
             } else {
-                // masks of the four direct neighbour cells (for the modified weights)
-                const bool kl = known(X - 1, Y), kr = known(X + 1, Y);
-                const bool ku = known(X, Y - 1), kd = known(X, Y + 1);
+                const bool kl = nbrs && s_kn[ty + 1][tx], kr = nbrs && s_kn[ty + 1][tx + 2];
+                const bool ku = nbrs && s_kn[ty][tx + 1], kd = nbrs && s_kn[ty + 2][tx + 1];
                 float wt[4];
-                size_t idx[4];
                 float den = 0.f, cnt = 0.f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int x = 2 * X + (k & 1), y = 2 * Y + (k >> 1);
                     wt[k] = 0.f;
-                    idx[k] = 0;
-                    if (x >= w || y >= h) continue;
-                    const size_t p = (size_t)y * w + x;
-                    idx[k] = p;
-                    if (!c[p]) continue;
+                    if (x >= w || y >= h || !ck[k]) continue;
                     cnt += 1.f;
                     if (!modified) { wt[k] = 1.f; continue; }
-                    int m = 0;
-                    const int xi = x ^ 1, yi = y ^ 1;  // partners inside the cell
-                    if (xi < w) m += c[(size_t)y * w + xi] != 0;
-                    if (yi < h) m += c[(size_t)yi * w + x] != 0;
-                    const int xo = (x & 1) ? x + 1 : x - 1;  // neighbours across the cell
+                    // partners inside the cell (0 off the image), then the
+                    // neighbours across the cell's sides
+                    int m = (ck[k ^ 1] != 0u) + (ck[k ^ 2] != 0u);
+                    const int xo = (x & 1) ? x + 1 : x - 1;
                     const int yo = (y & 1) ? y + 1 : y - 1;
                     if (xo >= 0 && xo < w) m += (x & 1) ? kr : kl;
                     if (yo >= 0 && yo < h) m += (y & 1) ? kd : ku;
@@ -285,17 +306,19 @@ k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int 
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int x = 2 * X + (k & 1), y = 2 * Y + (k >> 1);
-                        wt[k] = (x < w && y < h && c[idx[k]]) ? 1.f : 0.f;
+                        wt[k] = (x < w && y < h && ck[k]) ? 1.f : 0.f;
                     }
                     den = cnt;
                 }
                 const float inv = 1.f / fmaxf(1.f, den);
+                const size_t p0 = (size_t)(2 * Y) * w + 2 * X;
                 for (int ch = 0; ch < C; ++ch) {
-                    const float* bc = b + ch * n;
+                    const float* bc = b + ch * n + p0;
                     float num = 0.f;
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (wt[k] != 0.f) num += wt[k] * bc[idx[k]];
+                        if (wt[k] != 0.f)
+                            num = __fmaf_rn(wt[k], bc[(k >> 1) * (size_t)w + (k & 1)], num);
                     bH[ch * nH + P] = num * inv;
                 }
             }
@@ -313,9 +336,9 @@ k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int 
     if (unknown) {
         __shared__ unsigned s_u[8];
         const unsigned c8 = __reduce_add_sync(0xffffffffu, unk);
-        if (lane == 0) s_u[threadIdx.y] = c8;
+        if (lane == 0) s_u[ty] = c8;
         __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
+        if (tx == 0 && ty == 0) {
             unsigned long long a = 0;
             for (int i = 0; i < 8; ++i) a += s_u[i];
             if (a) atomicAdd(unknown, a);
