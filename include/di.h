@@ -143,6 +143,10 @@ typedef struct {
                          rule) are formed in FP64 from the FP32 iterate and rounded once --
                          the outer refinement for tolerances near FP32's resolution of
                          values up to 255; FP64 is used nowhere else [0] */
+    int local_iters_cascade; /* CG steps of the local solves of the cascade's iteration on the
+                                finest level, the one after the interpolation from the first
+                                coarse level (its start has the decode's largest residual, so
+                                the local stop ends none of them early) [local_iters] */
 } di_config;
 
 /* Statistics of the last di_inpaint call on a context. */

@@ -35,7 +35,8 @@ class di_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("graph", ctypes.c_int),
                 ("start", ctypes.c_int), ("local_iters_coarse", ctypes.c_int),
-                ("local_stop", ctypes.c_float), ("refine_fp64", ctypes.c_int)]
+                ("local_stop", ctypes.c_float), ("refine_fp64", ctypes.c_int),
+                ("local_iters_cascade", ctypes.c_int)]
 
 
 class di_stats(ctypes.Structure):

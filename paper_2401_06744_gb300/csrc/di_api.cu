@@ -169,6 +169,7 @@ bool config_ok(const di_config& c) {
     if (c.local_iters_coarse < 0) return false;
     if (!std::isfinite(c.local_stop)) return false;
     if (c.refine_fp64 != 0 && c.refine_fp64 != 1) return false;
+    if (c.local_iters_cascade < 0) return false;
     // the 16-bit modes store the coarse levels narrow: 32x32 blocks and the
     // block smoother only (the global CG smoother keeps FP32 vectors)
     if (c.precision != DI_PREC_FP32 && (c.block != 32 || c.smoother != DI_SMOOTH_ORAS))
@@ -414,14 +415,17 @@ struct Sched {
     // pro_e, pro_max, pro_mode: a coarser field prolonged into the start
     // (fuse_prolong; mode 1 adds a correction, mode 0 interpolates a solution
     // with in = b).
+    // cascade: the cascade's smoothing step (cfg.local_iters_cascade on level 0).
     di_status smooth(int l, const float* in, int zero_in, float* out, unsigned* maxupd,
                      bool restart = true, const float* pro_e = nullptr,
-                     unsigned* pro_max = nullptr, int pro_mode = 1) {
+                     unsigned* pro_max = nullptr, int pro_mode = 1, bool cascade = false) {
         const di_config& cfg = ctx->cfg;
         if (cfg.smoother == DI_SMOOTH_ORAS)
             return run_oras(l, in, zero_in, out,
-                            l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
-                                                                : cfg.local_iters,
+                            l == 0 && cascade && cfg.local_iters_cascade > 0
+                                ? cfg.local_iters_cascade
+                            : l > 0 && cfg.local_iters_coarse > 0 ? cfg.local_iters_coarse
+                                                                  : cfg.local_iters,
                             maxupd, abs2 > 0.f ? -abs2 : 0.f, pro_e, pro_max, pro_mode);
         const Level& v = ctx->lv[l];
         int rhs_zero;
@@ -671,13 +675,13 @@ bool capture_cascade(di_ctx* ctx, Sched& S, int Leff) {
         Level& cv = lv[l + 1];
         S.root = l;
         if (S.fuse_prolong(l)) {
-            if (S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0)) return false;
+            if (S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0, true)) return false;
             continue;
         }
         if (launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, S.s, S.stor(l + 1),
                            S.stor(l)))
             return false;
-        if (S.smooth(l, v.u[1], 0, v.u[0], nullptr)) return false;
+        if (S.smooth(l, v.u[1], 0, v.u[0], nullptr, true, nullptr, nullptr, 1, true)) return false;
     }
     S.root = 0;
     return true;
@@ -1207,12 +1211,12 @@ di_status inpaint_impl(di_ctx* ctx, const float* f, const uint8_t* c, int width,
             } else if (S.fuse_prolong(l)) {
                 // reduced FMG and multilevel: one smoothing step per level,
                 // from b on the mask and the interpolated coarser solution
-                st = S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0);
+                st = S.smooth(l, v.b, 0, v.u[0], nullptr, true, cv.u[0], nullptr, 0, true);
                 if (st) return st;
             } else {
                 DI_CUDA(ctx, launch_prolong(cv.u[0], v.b, v.c, v.w, v.h, C, v.u[1], 0, nullptr, s,
                                             S.stor(l + 1), S.stor(l)));
-                st = S.smooth(l, v.u[1], 0, v.u[0], nullptr);
+                st = S.smooth(l, v.u[1], 0, v.u[0], nullptr, true, nullptr, nullptr, 1, true);
                 if (st) return st;
             }
         }

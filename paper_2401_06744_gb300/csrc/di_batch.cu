@@ -216,6 +216,11 @@ struct Builder {
         const di_config& c = b->cfg;
         return l > 0 && c.local_iters_coarse > 0 ? c.local_iters_coarse : c.local_iters;
     }
+    // the cascade's smoothing step on level l
+    int Kc(int l) const {
+        const di_config& c = b->cfg;
+        return l == 0 && c.local_iters_cascade > 0 ? c.local_iters_cascade : K(l);
+    }
 
     void build_tables() {
         const di_config& cfg = b->cfg;
@@ -298,7 +303,7 @@ struct Builder {
                     s.C = I.C;
                     s.mode = 0;
                     add_grid(pro, s, kBProlong, v.w, v.h, I.C, &c2);
-                    add_oras(ora, i, l, kWhenBelowTop, v.u[1], 0, v.b, 1, v.u[0], K(l), abs2(i),
+                    add_oras(ora, i, l, kWhenBelowTop, v.u[1], 0, v.b, 1, v.u[0], Kc(l), abs2(i),
                              nullptr, &units);
                 } else {  // the coarsest level: the single-block solve of the start
                     add_oras(ora, i, l, kWhenCoarsestStart, v.u[1], 0, v.b, 1, v.u[0],
