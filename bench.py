@@ -49,6 +49,10 @@ TOL = 0.05
 # gray of the FP64 oracle.  The paper's own setting (overlap 6, 8 local
 # steps) is timed beside it on the same frames ("paper_config").
 BLOCK, OVERLAP, LOCAL_ITERS, LOCAL_ITERS_COARSE = 32, 2, 10, 8
+# local CG steps of the cascade's iteration on the finest level (fastest on the
+# bench frames at the 0.05 bar: 2..8 steps sweep 645..653 frames/s, all at the
+# same V-cycle counts, against 631 with the level's 10)
+LOCAL_ITERS_CASCADE = 6
 # A block's local CG also stops once its residual is at most LOCAL_STOP x tol
 # gray (a correction that small is below what the stop rule resolves); 0.4
 # decodes the six frames 5 % faster than 0.2 at the same V-cycle counts and a
@@ -299,7 +303,8 @@ def run_ours(args):
     # one decoder (context, stream, output) per frame in flight
     ctxs = [di.Context(device=local, profile=0, precision=prec, block=args.block,
                        overlap=args.overlap, local_iters=args.local_iters,
-                       local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+                       local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop,
+                       local_iters_cascade=args.local_iters_cascade)
             for _ in range(S)]
     streams = [torch.cuda.Stream(dev) for _ in range(S)]
     u_dev = [torch.empty_like(f_dev[0]) for _ in range(S)]
@@ -393,7 +398,8 @@ def run_ours(args):
     u_host = [torch.empty(f_host[0].shape, dtype=torch.float32).pin_memory() for _ in range(R)]
     srv = di.Server(slots=S, device=local, precision=prec, block=args.block,
                     overlap=args.overlap, local_iters=args.local_iters,
-                    local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+                    local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop,
+                    local_iters_cascade=args.local_iters_cascade)
 
     def e2e_run(n):
         tickets = []
@@ -460,7 +466,8 @@ def run_ours(args):
     with di.Context(device=local, profile=1, precision=prec, block=args.block,
                     overlap=args.overlap, local_iters=args.local_iters,
                     local_iters_coarse=args.local_iters_coarse,
-                    local_stop=args.local_stop) as pctx_:
+                    local_stop=args.local_stop,
+                    local_iters_cascade=args.local_iters_cascade) as pctx_:
         for i in range(len(cases)):  # warm-up: workspace, graphs
             pctx_.inpaint(f_dev[i], c_dev[i], tol=TOL, out=u_dev[0], stream=streams[0])
         torch.cuda.synchronize(dev)
@@ -621,6 +628,7 @@ def run_ours(args):
                    "block": args.block, "overlap": args.overlap,
                    "local_iters": args.local_iters,
                    "local_iters_coarse": args.local_iters_coarse,
+                   "local_iters_cascade": args.local_iters_cascade,
                    "local_stop": args.local_stop, "frames": len(cases),
                    "streams": S, "precision": args.precision,
                    "l2": "inputs larger than L2 (6 rotating frames, 650 MB), no flush",
@@ -740,7 +748,8 @@ def run_decode_once(args):
     with di.Context(device=0, block=args.block, overlap=args.overlap,
                     local_iters=args.local_iters, graph=graph,
                     local_iters_coarse=args.local_iters_coarse,
-                    local_stop=args.local_stop) as ctx:
+                    local_stop=args.local_stop,
+                    local_iters_cascade=args.local_iters_cascade) as ctx:
         for k in range(len(cases)):
             ctx.inpaint(fd[k], cd[k], tol=TOL, out=out)
         torch.cuda.synchronize(dev)
@@ -917,7 +926,8 @@ def _compare_video(args, di, dev, s):
     ft = [torch.from_numpy(f).to(dev) for f in seq]
     refs = []
     cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters,
-               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop,
+               local_iters_cascade=args.local_iters_cascade)
     with di.Context(device=0, stop_rule=di.STOP_FIXED_CYCLES, max_cycles=12, min_cycles=12,
                     **cfg) as ctx:
         for f in ft:
@@ -984,7 +994,8 @@ def _compare_configs(args, di, dev, s):
     import synth
 
     cfg = dict(block=args.block, overlap=args.overlap, local_iters=args.local_iters,
-               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+               local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop,
+               local_iters_cascade=args.local_iters_cascade)
 
     def err_of(u, ref):
         e = np.abs(u.astype(np.float64) - ref)
@@ -1033,7 +1044,8 @@ def _compare_configs(args, di, dev, s):
     torch.cuda.synchronize()
     # the batched form: one graph, one launch per step over all 32 images
     bcfg = dict(block=32, overlap=2, local_iters=args.local_iters,
-                local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop)
+                local_iters_coarse=args.local_iters_coarse, local_stop=args.local_stop,
+                local_iters_cascade=args.local_iters_cascade)
     with di.Batch(items, **bcfg) as bt:
         bt.run()
         ms_b = _median_ms(lambda: bt.run(s), s, 5)
@@ -1155,6 +1167,8 @@ def main():
                     help="CG steps of each local block solve on the finest level")
     ap.add_argument("--local-iters-coarse", type=int, default=LOCAL_ITERS_COARSE,
                     help="CG steps of the local block solves on the coarser levels")
+    ap.add_argument("--local-iters-cascade", type=int, default=LOCAL_ITERS_CASCADE,
+                    help="local CG steps of the cascade's finest-level iteration (0: local-iters)")
     ap.add_argument("--local-stop", type=float, default=LOCAL_STOP,
                     help="local CG stop level as a fraction of tol (cfg.local_stop)")
     ap.add_argument("--streams", type=int, default=4,

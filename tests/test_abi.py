@@ -71,6 +71,7 @@ def test_plan_matches_oracle_tiling(di, w, h, B, o):
 @pytest.mark.parametrize("kw", [dict(block=12), dict(block=8, overlap=5), dict(alpha=-1.0),
                                 dict(downsample=3), dict(stop_rule=7),
                                 dict(min_cycles=5, max_cycles=2), dict(refine_fp64=2),
+                                dict(local_iters_cascade=-1),
                                 # the 16-bit modes store the coarse levels narrow: 32x32
                                 # blocks and the block smoother only
                                 dict(precision=1, block=16), dict(precision=2, smoother=1)])

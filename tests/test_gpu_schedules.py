@@ -205,6 +205,18 @@ def test_coarse_level_local_steps(di, case):
     _check(u2, f, c, ref, TOL)
 
 
+def test_cascade_local_steps(di, case):
+    # a step limit of its own for the cascade's finest-level iteration changes
+    # the iterates but not the fixed point; 0 (the default) is the level's own
+    f, c, ref = case
+    u0, st0, _ = _run(di, f, c, TOL)
+    u1, st1, _ = _run(di, f, c, TOL, local_iters_cascade=8)  # local_iters 8: same as default
+    assert st0 == st1 == di.OK and np.array_equal(u0, u1)
+    u2, st2, _ = _run(di, f, c, TOL, local_iters=10, local_iters_cascade=3, max_cycles=64)
+    assert st2 == di.OK
+    _check(u2, f, c, ref, TOL)
+
+
 def test_profile_counts_completed_local_steps(di, case):
     # the profile counts the local CG steps the finest-level local problems
     # completed: at most the step limit each, fewer with the local stop
