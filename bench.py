@@ -89,6 +89,7 @@ DRAM_PROFILE = os.path.join(ROOT, "profiles", "dram_4k_rgb_decode.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2401_06744_gb300", "csrc", n)
                   for n in ("di_kernels.cu", "di_internal.h")]
 LATENCY_FRAMES = 240
+E2E_RUNS = 3
 
 
 def _link_gbs(dev) -> dict:
@@ -402,28 +403,42 @@ def run_ours(args):
                     local_iters_cascade=args.local_iters_cascade)
 
     def e2e_run(n):
-        tickets = []
-        for i in range(n):
-            if i >= R:
-                _, info = srv.wait(tickets[i - R])
-                if info["status"] != di.OK:
-                    raise RuntimeError(di.status_string(info["status"]))
-            k = i % len(cases)
-            tickets.append(srv.submit(f_host[k], c_host[k], TOL, out=u_host[i % R]))
-        for t in tickets[max(0, n - R):]:
+        tickets, lat = [], []
+
+        def done(t):
             _, info = srv.wait(t)
             if info["status"] != di.OK:
                 raise RuntimeError(di.status_string(info["status"]))
+            lat.append((info["latency_ms"], info["queue_ms"]))
 
-    e2e_run(6 * S)  # warm-up: every slot's buffer sets and graphs
+        for i in range(n):
+            if i >= R:
+                done(tickets[i - R])
+            k = i % len(cases)
+            tickets.append(srv.submit(f_host[k], c_host[k], TOL, out=u_host[i % R]))
+        for t in tickets[max(0, n - R):]:
+            done(t)
+        return lat
+
     link = _link_gbs(dev)  # the host link's copy rate, which bounds this leg
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps)
-    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_run(6 * S)  # warm-up: every slot's buffer sets and graphs
+    # three timed runs; the line reports their median and each run's rate and
+    # slowest request (submit to result, and of that the wait for a slot)
+    e2e_runs, e2e_ms_runs = [], []
+    for _ in range(E2E_RUNS):
+        barrier()
+        t0 = time.perf_counter()
+        lat = e2e_run(e2e_steps)
+        ms_ = (time.perf_counter() - t0) * 1e3
+        if ws > 1:
+            ms_ = max_over_ranks(ms_, dev)
+        slow = max(lat)
+        e2e_ms_runs.append(ms_)
+        e2e_runs.append({"frames_per_s": round(job_rate(e2e_steps, ws, ms_), 1),
+                         "slowest_request_ms": round(slow[0], 1),
+                         "its_queue_ms": round(slow[1], 1)})
+    e2e_ms = sorted(e2e_ms_runs)[len(e2e_ms_runs) // 2]  # the median run (max over ranks)
     srv.close()
-    if ws > 1:
-        e2e_ms = max_over_ranks(e2e_ms, dev)
     h2d = f_host[0].numel() * 4 + c_host[0].numel()
     d2h = u_host[0].numel() * 4
 
@@ -653,9 +668,10 @@ def run_ours(args):
         "e2e": {"value": round(job_rate(e2e_steps, ws, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "frames": e2e_steps,
+                "runs": e2e_runs,
                 "path": f"C ABI di_server_submit / di_server_wait, {S} slots, page-locked "
                         "host buffers, host wall clock from the first submit to the last "
-                        "result",
+                        f"result; the median of {E2E_RUNS} runs",
                 "link_gbs": link,
                 "link_bound": round(1e9 / (h2d / link["h2d"] + d2h / link["d2h"]), 1),
                 "link_note": "page-locked copies of 256 MB each way measured before the "
