@@ -179,9 +179,12 @@ struct Builder {
         segs.insert(segs.end(), v.begin(), v.end());
     }
     // a block-kernel segment of image i on level l (in -> out)
+    // pro_e, pro_mode, pro_max, pro_check: the start prolonged from level
+    // l + 1 inside the block kernel (BatchSeg)
     void add_oras(std::vector<BatchSeg>& v, int i, int l, int when, const float* in, int zero_in,
                   const float* rhs, int rhs_zero, float* out, int iters, float rtol2,
-                  unsigned* maxupd, int* units) {
+                  unsigned* maxupd, int* units, const float* pro_e = nullptr, int pro_mode = 0,
+                  unsigned* pro_max = nullptr, int pro_check = 0) {
         const BLevel& lv = b->im[i].lv[l];
         BatchSeg s = base(i, l, when);
         s.w = lv.w;
@@ -199,6 +202,10 @@ struct Builder {
         s.wpr = mask_words_per_row(lv.w);
         s.nbx = axis_blocks(lv.w, 32, b->cfg.overlap);
         s.nby = axis_blocks(lv.h, 32, b->cfg.overlap);
+        s.pro_e = pro_e;
+        s.pro_mode = pro_e ? pro_mode : 0;
+        s.pro_max = pro_max;
+        s.pro_check = pro_check;
         s.first = *units;
         *units += s.nbx * s.nby;
         v.push_back(s);
@@ -279,8 +286,8 @@ struct Builder {
     void build_cascade() {
         const int n = b->n;
         for (int l = Lmax - 1; l >= 0; --l) {
-            std::vector<BatchSeg> sel, pro, ora;
-            int c1 = 0, c2 = 0, units = 0;
+            std::vector<BatchSeg> sel, ora;
+            int c1 = 0, units = 0;
             for (int i = 0; i < n; ++i) {
                 const BImage& I = b->im[i];
                 if (l >= I.L) continue;
@@ -294,24 +301,17 @@ struct Builder {
                 s.C = I.C;
                 add_grid(sel, s, kBSelect, v.w, v.h, I.C, &c1);
                 if (l + 1 < I.L) {
+                    // the coarser level's solution interpolated inside the
+                    // smoothing step: b on the mask, P u_{l+1} elsewhere
                     const BLevel& cv = I.lv[l + 1];
-                    s = base(i, l, kWhenBelowTop);
-                    s.in0 = cv.u[0];
-                    s.in1 = v.b;
-                    s.in2 = v.c;
-                    s.out0 = v.u[1];
-                    s.C = I.C;
-                    s.mode = 0;
-                    add_grid(pro, s, kBProlong, v.w, v.h, I.C, &c2);
-                    add_oras(ora, i, l, kWhenBelowTop, v.u[1], 0, v.b, 1, v.u[0], Kc(l), abs2(i),
-                             nullptr, &units);
+                    add_oras(ora, i, l, kWhenBelowTop, v.b, 0, v.b, 1, v.u[0], Kc(l), abs2(i),
+                             nullptr, &units, cv.u[0], 2);
                 } else {  // the coarsest level: the single-block solve of the start
                     add_oras(ora, i, l, kWhenCoarsestStart, v.u[1], 0, v.b, 1, v.u[0],
                              b->cfg.coarse_iters, kCoarseRtol2B, nullptr, &units);
                 }
             }
             push(kBSelect, sel, c1);
-            push(kBProlong, pro, c2);
             push(-1, ora, units);
         }
     }
@@ -357,34 +357,33 @@ struct Builder {
             push(kBRestrict, res, c1);
             push(-1, ora, units);
         }
-        // up: post-smoothing of level l (not the coarsest), then its
-        // correction prolongated into level l - 1
-        for (int l = Lmax - 1; l >= 1; --l) {
-            std::vector<BatchSeg> ora, pro;
-            int units = 0, c1 = 0;
+        // up: the post-smoothing of every level that has a coarser one, with
+        // that level's correction prolonged into its start inside the block
+        // kernel (while the coarser level is in use for the image); level 0
+        // of an image without coarser levels smooths plainly
+        for (int l = Lmax - 2; l >= 0; --l) {
+            std::vector<BatchSeg> ora;
+            int units = 0;
             for (int i = 0; i < n; ++i) {
                 const BImage& I = b->im[i];
-                if (l >= I.L) continue;
-                const BLevel& v = I.lv[l];
-                const BLevel& fl = I.lv[l - 1];
-                const bool coarsest = l == I.L - 1;
-                if (!coarsest)
-                    add_oras(ora, i, l, kWhenCycle, v.u[1], 0, v.r, 0, v.u[0], K(l), abs2(i),
-                             nullptr, &units);
-                BatchSeg s = base(i, l, kWhenCycle);
-                s.in0 = coarsest ? v.u[1] : v.u[0];
-                s.in2 = fl.c;
-                s.out0 = fl.u[1];
-                s.C = I.C;
-                s.mode = 1;
-                s.maxupd = l - 1 == 0 ? upd(i, 1) : nullptr;
-                add_grid(pro, s, kBProlong, fl.w, fl.h, I.C, &c1);
+                const BLevel& v = I.lv[std::min(l, I.L - 1)];
+                if (l + 1 < I.L) {
+                    const BLevel& cv = I.lv[l + 1];
+                    const float* e = l + 1 == I.L - 1 ? cv.u[1] : cv.u[0];
+                    if (l == 0)
+                        add_oras(ora, i, 0, kWhenCycle, v.u[1], 0, v.b, 1, v.u[0], K(0), abs2(i),
+                                 upd(i, 2), &units, e, 1, upd(i, 1), 1);
+                    else
+                        add_oras(ora, i, l, kWhenCycle, v.u[1], 0, v.r, 0, v.u[0], K(l), abs2(i),
+                                 nullptr, &units, e, 1, nullptr, 1);
+                } else if (l == 0) {
+                    add_oras(ora, i, 0, kWhenCycle, v.u[1], 0, v.b, 1, v.u[0], K(0), abs2(i),
+                             upd(i, 2), &units);
+                }
             }
             push(-1, ora, units);
-            push(kBProlong, pro, c1);
         }
-        // level 0 post-smoothing: u[1] -> u[0]
-        {
+        if (Lmax == 1) {  // every image has one level: its post-smoothing alone
             std::vector<BatchSeg> ora;
             int units = 0;
             for (int i = 0; i < n; ++i) {

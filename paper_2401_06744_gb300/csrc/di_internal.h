@@ -231,6 +231,14 @@ struct BatchSeg {
     unsigned long long* counter;  // pack: the image's unknown count of this level
     int zero_in, rhs_zero, iters, nbx, nby, wpr, mode, keep;
     float rtol2;
+    // block kernel: the start prolonged from the next coarser level inside the
+    // kernel (prolong_into_tile) -- pro_mode 0 none, 1 u_in + P pro_e at
+    // unknown pixels (the correction; largest |P pro_e| into *pro_max), 2
+    // u_in at known and P pro_e at unknown pixels (the cascade, u_in = b);
+    // pro_check 1: only while level + 1 is in use for the image
+    const float* pro_e;
+    unsigned* pro_max;
+    int pro_mode, pro_check;
 };
 
 // Per-image decode state of a batch (device arrays of n images).

@@ -1286,6 +1286,97 @@ struct Smem2W {
     }
 };
 
+// The start of an iteration formed by prolongation inside a 32x32 block's
+// tile (Section 4.4's cell-centred weights): the block pixels of this
+// thread's column (x0 and y0 + row0 are even, so row row0 + k has parent
+// patch row 1 + row0 / 2 + k / 2 and takes the coarse row above it for even
+// k, below it for odd k; the column likewise), then the halo pixels the
+// residual reads: warp 0 the row above the block and the column left of it,
+// warp 1 the row below and the column right of it, one pixel of each per
+// lane (block pixels of a neighbouring block, which counts them in the
+// maximum).  pe: the block's coarse patch (cell (r, q) = coarse row
+// y0 / 2 - 1 + r, column x0 / 2 - 1 + q, pitch Smem2W::EPW, clamped to the
+// level); mbk: the known bits of the thread's block pixels, hk: of its two
+// halo pixels (known or off the image).  ADD: u + P e at unknown pixels
+// (a correction), else P e there (an interpolated solution); known pixels
+// keep their tile value.  pmax gains the largest |P e| over the unknown
+// block pixels.  Branch-free (every patch index stays inside the patch); the
+// ten patch rows of both columns and the sixteen tile values are read before
+// anything is stored (the stores could alias them otherwise), so the loads
+// are in flight together.
+template <bool ADD>
+__device__ __forceinline__ void prolong_into_tile(float* tw, const float* pe, int row0, int col,
+                                                  int lane, int wi, int x0, int y0, uint32_t mbk,
+                                                  uint32_t hk, float& pmax) {
+    constexpr int EW = Smem2W::EPW, P = Smem2W::PU, B = 32;
+    {
+        const int q = 1 + (col >> 1), qn = (col & 1) ? q + 1 : q - 1;
+        const float* pr = pe + (row0 >> 1) * EW;  // patch row of coarse row Yb - 1
+        float* tc = tw + (row0 + 1) * P + col + 1;
+        float ec[10], es[10], tv[16];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            ec[j] = pr[j * EW + q];
+            es[j] = pr[j * EW + qn];
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) tv[k] = tc[k * P];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int jc = (k >> 1) + 1, jn = (k & 1) ? jc + 1 : jc - 1;
+            const float a = prolong_blend(ec[jc], ec[jn], es[jc], es[jn]);
+            const bool kn = (mbk >> k) & 1u;
+            tc[k * P] = kn ? tv[k] : (ADD ? __fadd_rn(tv[k], a) : a);
+            pmax = fmaxf(pmax, kn ? 0.f : fabsf(a));
+        }
+    }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int hy = side == 0 ? (wi == 0 ? y0 - 1 : y0 + B) : y0 + lane;
+        const int hx = side == 0 ? x0 + lane : (wi == 0 ? x0 - 1 : x0 + B);
+        const int r = (hy >> 1) - (y0 >> 1) + 1, q = (hx >> 1) - (x0 >> 1) + 1;
+        const int rn = (hy & 1) ? r + 1 : r - 1, qn = (hx & 1) ? q + 1 : q - 1;
+        const float a = prolong_blend(pe[r * EW + q], pe[rn * EW + q], pe[r * EW + qn],
+                                      pe[rn * EW + qn]);
+        float* tp = tw + (hy - y0 + 1) * P + (hx - x0 + 1);
+        const bool kn = (hk >> side) & 1u;  // known or off the image
+        const float old = *tp;
+        *tp = kn ? old : (ADD ? __fadd_rn(old, a) : a);
+    }
+}
+
+// The coarse cells a task's prolongation reads, by 4-byte cp.async (all 64
+// threads): rows (py0 >> 1) - 1 + r and columns (px0 >> 1) - 1 + q, r, q <
+// 18, each clamped to the level as the prolongation clamps its indices,
+// into dst with pitch Smem2W::EPW.  The caller commits the group.
+__device__ __forceinline__ void copy_patch_clamped(float* dst, const float* e, int px0, int py0,
+                                                   int wH, int hH, int t) {
+    const int Ys = (py0 >> 1) - 1, Xs = (px0 >> 1) - 1;
+    for (int i = t; i < Smem2W::ES; i += 64) {
+        const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
+        const int Y = min(max(Ys + r, 0), hH - 1), X = min(max(Xs + q, 0), wH - 1);
+        cp_async4(dst + r * Smem2W::EPW + q, e + (size_t)Y * wH + X, true);
+    }
+}
+
+// Known bits of a thread's two halo pixels for prolong_into_tile (bit set:
+// known or off the image).
+__device__ __forceinline__ uint32_t halo_known_bits(const uint32_t* __restrict__ mbits, int wpr,
+                                                    int w, int h, int px0, int py0, int wi,
+                                                    int lane) {
+    constexpr int B = 32;
+    const int hy0 = wi == 0 ? py0 - 1 : py0 + B, hx0 = px0 + lane;
+    const int hy1 = py0 + lane, hx1 = wi == 0 ? px0 - 1 : px0 + B;
+    uint32_t k = 3u;
+    if (hx0 >= 0 && hx0 < w && hy0 >= 0 && hy0 < h &&
+        !((__ldg(mbits + (size_t)hy0 * wpr + (hx0 >> 5)) >> (hx0 & 31)) & 1u))
+        k &= ~1u;
+    if (hx1 >= 0 && hx1 < w && hy1 >= 0 && hy1 < h &&
+        !((__ldg(mbits + (size_t)hy1 * wpr + (hx1 >> 5)) >> (hx1 & 31)) & 1u))
+        k &= ~2u;
+    return k;
+}
+
 // Bounded wait for phase `parity` of the mbarrier at shared address `bar`;
 // false if it did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit = 1 << 20) {
@@ -1404,28 +1495,12 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
             // (with TMA, the box issued below; here each cell is clamped to
             // the level as the prolongation clamps its indices)
             if (!use_tma_e) {
-                const int Ys = (py0 >> 1) - 1, Xs = (px0 >> 1) - 1;
-                const float* e = eH + (size_t)ch * wH * hH;
-                float* dst = s_e + bs * Smem2W::ESTRIDE;
-                for (int i = t; i < Smem2W::ES; i += 64) {
-                    const int r = i / Smem2W::EW, q = i - r * Smem2W::EW;
-                    const int Y = min(max(Ys + r, 0), hH - 1), X = min(max(Xs + q, 0), wH - 1);
-                    cp_async4(dst + r * Smem2W::EPW + q, e + (size_t)Y * wH + X, true);
-                }
+                copy_patch_clamped(s_e + bs * Smem2W::ESTRIDE, eH + (size_t)ch * wH * hH, px0,
+                                   py0, wH, hH, t);
                 cp_async_commit();
             }
-            if (blk != have_blk) {
-                // this thread's two halo pixels (see the prolongation below)
-                const int hy0 = wi == 0 ? py0 - 1 : py0 + B, hx0 = px0 + lane;
-                const int hy1 = py0 + lane, hx1 = wi == 0 ? px0 - 1 : px0 + B;
-                nhk = 3u;
-                if (hx0 >= 0 && hx0 < w && hy0 >= 0 && hy0 < h &&
-                    !((__ldg(mbits + (size_t)hy0 * wpr + (hx0 >> 5)) >> (hx0 & 31)) & 1u))
-                    nhk &= ~1u;
-                if (hx1 >= 0 && hx1 < w && hy1 >= 0 && hy1 < h &&
-                    !((__ldg(mbits + (size_t)hy1 * wpr + (hx1 >> 5)) >> (hx1 & 31)) & 1u))
-                    nhk &= ~2u;
-            }
+            // this thread's two halo pixels (see the prolongation below)
+            if (blk != have_blk) nhk = halo_known_bits(mbits, wpr, w, h, px0, py0, wi, lane);
         }
         if (use_tma) {
             if (t == 0) {
@@ -1604,14 +1679,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
         const float* tu = s_u + buf * TILE + du;
         const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
         if constexpr (PRO != 0) {
-            // the start of the iteration in the tile: block pixels of this
-            // thread's column (x0 and y0 + row0 are even, so row row0 + k has
-            // parent patch row 1 + row0 / 2 + k / 2 and takes the coarse row
-            // above it for even k, below it for odd k; the column likewise),
-            // then the halo pixels the residual reads: warp 0 the row above
-            // the block and the column left of it, warp 1 the row below and
-            // the column right of it, one pixel of each per lane (block
-            // pixels of a neighbouring block, which counts them in the maximum)
+            // the start of the iteration in the tile (prolong_into_tile)
             constexpr int EW = Smem2W::EPW;  // patch pitch
             float* tw = s_u + buf * TILE + du;
             const int Ys = (y0 >> 1) - 1, Xs = (x0 >> 1) - 1;
@@ -1629,46 +1697,7 @@ k_oras_2w(const float* __restrict__ u_in, int zero_in, const float* __restrict__
                 }
                 __syncthreads();  // block-uniform branch
             }
-            const float* pe = pw;
-            // Branch-free (every patch index below stays inside the patch, and a
-            // pixel that is known or off the image keeps its tile value).  The
-            // ten patch rows of both columns and the sixteen tile values are
-            // read before anything is stored (the stores could alias them
-            // otherwise), so the loads are in flight together.
-            {
-                const int q = 1 + (col >> 1), qn = (col & 1) ? q + 1 : q - 1;
-                const float* pr = pe + (row0 >> 1) * EW;  // patch row of coarse row Yb - 1
-                float* tc = tw + (row0 + 1) * P + col + 1;
-                float ec[10], es[10], tv[16];
-#pragma unroll
-                for (int j = 0; j < 10; ++j) {
-                    ec[j] = pr[j * EW + q];
-                    es[j] = pr[j * EW + qn];
-                }
-#pragma unroll
-                for (int k = 0; k < 16; ++k) tv[k] = tc[k * P];
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const int jc = (k >> 1) + 1, jn = (k & 1) ? jc + 1 : jc - 1;
-                    const float a = prolong_blend(ec[jc], ec[jn], es[jc], es[jn]);
-                    const bool kn = (mbk >> k) & 1u;
-                    tc[k * P] = kn ? tv[k] : (PRO == 1 ? __fadd_rn(tv[k], a) : a);
-                    pmax = fmaxf(pmax, kn ? 0.f : fabsf(a));
-                }
-            }
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const int hy = side == 0 ? (wi == 0 ? y0 - 1 : y0 + B) : y0 + lane;
-                const int hx = side == 0 ? x0 + lane : (wi == 0 ? x0 - 1 : x0 + B);
-                const int r = (hy >> 1) - (y0 >> 1) + 1, q = (hx >> 1) - (x0 >> 1) + 1;
-                const int rn = (hy & 1) ? r + 1 : r - 1, qn = (hx & 1) ? q + 1 : q - 1;
-                const float a = prolong_blend(pe[r * EW + q], pe[rn * EW + q], pe[r * EW + qn],
-                                              pe[rn * EW + qn]);
-                float* tp = tw + (hy - y0 + 1) * P + (hx - x0 + 1);
-                const bool kn = (hk >> side) & 1u;  // known or off the image
-                const float old = *tp;
-                *tp = kn ? old : (PRO == 1 ? __fadd_rn(old, a) : a);
-            }
+            prolong_into_tile<PRO == 1>(tw, pw, row0, col, lane, wi, x0, y0, mbk, hk, pmax);
             __syncthreads();  // the residual reads the other threads' columns
         }
 
@@ -2476,7 +2505,8 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
     float* const s_u = smem;
     float* const s_wy = smem + Smem2W::WY;
-    float* const s_b = smem + Smem2W::RHS;
+    float* const s_e = smem + Smem2W::EP;  // coarse patches of prolonging segments
+    float* const s_b = smem + Smem2W::RHS_PRO;
     __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
 
     const int t = threadIdx.x;
@@ -2485,6 +2515,10 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
     const int row0 = 16 * wi;
     const int s = B - o;
     const float inv_o1 = o > 1 ? 1.f / (float)(o - 1) : 0.f;
+    // whether a segment's tasks form their start by prolongation (uniform per task)
+    auto prolongs = [&](const BatchSeg& sg) {
+        return sg.pro_mode != 0 && (!sg.pro_check || sg.level + 1 < bs.leff[sg.img]);
+    };
 
     // a task: a unit's segment and block, and a channel
     struct Task {
@@ -2505,12 +2539,18 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
         }
         return false;
     };
-    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu;
+    uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu, nhk = 3u;
     auto prefetch = [&](const Task& tk, int bs_, bool new_blk) {
         const BatchSeg& sg = segs[tk.seg];
         const int w = sg.w, h = sg.h, nbx = sg.nbx;
         const size_t n = (size_t)w * h;
         const int px0 = (tk.blk % nbx) * s, py0 = (tk.blk / nbx) * s;
+        if (prolongs(sg)) {
+            const int wH = (w + 1) / 2, hH = (h + 1) / 2;
+            copy_patch_clamped(s_e + bs_ * Smem2W::ESTRIDE, sg.pro_e + (size_t)tk.ch * wH * hH,
+                               px0, py0, wH, hH, t);
+            if (new_blk) nhk = halo_known_bits(sg.mbits, sg.wpr, w, h, px0, py0, wi, lane);
+        }
         if (!sg.zero_in) {
             const float* src = static_cast<const float*>(sg.in0) + tk.ch * n;
             float* dst = s_u + bs_ * TILE;
@@ -2561,14 +2601,15 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
     f2 ml2 = 0ull, mr2 = 0ull;
     float wx = 0.f, dh = 0.f;
     int x0 = 0, y0 = 0, bh = 0, kx = 0, ky = 0;
-    uint32_t rows_w = 0;
-    float vmax = 0.f;
+    uint32_t rows_w = 0, mbk = 0;
+    float vmax = 0.f, pmax = 0.f;
     unsigned* vmax_slot = nullptr;
+    unsigned* pmax_slot = nullptr;
 
     for (;;) {
         cp_async_wait_all();
         __syncthreads();
-        const uint32_t mlo = nlo, mhi = nhi;
+        const uint32_t mlo = nlo, mhi = nhi, hk = nhk;
         Task nxt = cur;
         int g2 = g;
         const bool more = advance(g2, nxt);
@@ -2584,8 +2625,14 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
                 const float m = warp_max(vmax);
                 if (lane == 0 && m > 0.f) atomicMax(vmax_slot, __float_as_uint(m));
             }
+            if (pmax_slot) {
+                const float m = warp_max(pmax);
+                if (lane == 0 && m > 0.f) atomicMax(pmax_slot, __float_as_uint(m));
+            }
             vmax = 0.f;
+            pmax = 0.f;
             vmax_slot = sg.maxupd;
+            pmax_slot = sg.pro_mode == 1 ? sg.pro_max : nullptr;
             cur_seg = cur.seg;
             cur_blk = -1;
         }
@@ -2623,6 +2670,7 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
                 ndg[k] = pk(-(hc + vc[0]), -(hc + vc[1]));
                 keep[k] = pk(((mb >> k) & 1u) ? 0.f : 1.f, ((mb >> (k + 8)) & 1u) ? 0.f : 1.f);
             }
+            mbk = mb;
             wx = ramp_weight(col, kx, nbx, s, o, inv_o1);
             const float wyl = ramp_weight(lane, ky, nby, s, o, inv_o1);
             if (t < B) s_wy[t] = wyl;
@@ -2630,6 +2678,16 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
         }
         const float* tu = s_u + buf * TILE;
         const float* tb = s_b + buf * Smem2W::BSTRIDE;
+        if (prolongs(sg)) {  // uniform per task
+            const float* pe = s_e + buf * Smem2W::ESTRIDE;
+            if (sg.pro_mode == 1)
+                prolong_into_tile<true>(s_u + buf * TILE, pe, row0, col, lane, wi, x0, y0, mbk, hk,
+                                        pmax);
+            else
+                prolong_into_tile<false>(s_u + buf * TILE, pe, row0, col, lane, wi, x0, y0, mbk,
+                                         hk, pmax);
+            __syncthreads();  // the residual reads the other threads' columns
+        }
 
         f2 x[NP], r[NP], p[NP], q[NP];
         f2 acc0 = 0ull, acc1 = 0ull;
@@ -2741,6 +2799,10 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
     if (vmax_slot) {
         vmax = warp_max(vmax);
         if (lane == 0 && vmax > 0.f) atomicMax(vmax_slot, __float_as_uint(vmax));
+    }
+    if (pmax_slot) {
+        pmax = warp_max(pmax);
+        if (lane == 0 && pmax > 0.f) atomicMax(pmax_slot, __float_as_uint(pmax));
     }
 }
 
@@ -3518,7 +3580,7 @@ cudaError_t launch_batch_oras(const BatchSeg* segs, int nseg, int nunits, int o,
     if (nunits < 1 || nseg < 1) return cudaSuccess;
     if (shared_per_seam(o) != 0) return cudaErrorInvalidValue;  // 0/1 weights only
     int nsm = 0;
-    const size_t smem = Smem2W::bytes(true);
+    const size_t smem = Smem2W::bytes(true, true);
     const int oc = cached_occupancy((const void*)k_batch_oras, 64, smem, smem, &nsm);
     int grid = nsm * oc;
     if (grid > nunits) grid = nunits;

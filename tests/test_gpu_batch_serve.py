@@ -213,7 +213,8 @@ def test_autotune_over_local_steps_cycle_type_and_schedule(di):
         _check_oracle(_solo(di, f, c, **cfg), f, c)
 
 
-def test_batched_form_one_graph_matches_solo_and_oracle(di):
+@pytest.mark.parametrize("cascade", [0, 4])
+def test_batched_form_one_graph_matches_solo_and_oracle(di, cascade):
     # the batched form: a batch of uneven sizes and channel counts decoded as
     # one graph with one launch per step over every image; every image equals
     # its single-image decode bit for bit (the same arithmetic in the same
@@ -233,7 +234,9 @@ def test_batched_form_one_graph_matches_solo_and_oracle(di):
     one = np.zeros_like(c2)
     one[60, 100] = 1
     cases.append((f2, one))
-    cfg = dict(block=32, overlap=2, local_iters=10, local_iters_coarse=8, max_cycles=64)
+    # cascade: the cascade's finest-level step limit (0: the level's own)
+    cfg = dict(block=32, overlap=2, local_iters=10, local_iters_coarse=8, max_cycles=64,
+               local_iters_cascade=cascade)
     items = [(torch.from_numpy(f).to(DEV), torch.from_numpy(c).to(DEV), TOL) for f, c in cases]
     with di.Batch(items, **cfg) as bt:
         for rep in range(2):  # the graph replays on the same buffers
