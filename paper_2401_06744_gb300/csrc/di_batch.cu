@@ -249,8 +249,9 @@ struct Builder {
             push(kBPack, v, cta);
         }
         for (int l = 1; l < Lmax; ++l) {
-            std::vector<BatchSeg> md, vd, pm;
-            int c1 = 0, c2 = 0, c3 = 0;
+            // level l in one pass: mask, mask values, packed words, unknown count
+            std::vector<BatchSeg> v;
+            int cta = 0;
             for (int i = 0; i < n; ++i) {
                 const BImage& I = b->im[i];
                 if (l >= I.L) continue;
@@ -258,27 +259,17 @@ struct Builder {
                 const BLevel& cl = I.lv[l];
                 BatchSeg s = base(i, l, kWhenAlways);
                 s.in0 = fl.c;
-                s.out0 = const_cast<uint8_t*>(cl.c);
-                s.C = 1;
-                add_grid(md, s, kBMaskDown, fl.w, fl.h, 1, &c1);
-                s = base(i, l, kWhenAlways);
-                s.in0 = fl.c;
                 s.in1 = fl.b;
-                s.in2 = cl.c;
-                s.out0 = const_cast<float*>(cl.b);
+                s.out0 = const_cast<uint8_t*>(cl.c);
+                s.out1 = const_cast<float*>(cl.b);
                 s.C = I.C;
                 s.mode = cfg.downsample == 0 ? 1 : 0;
-                add_grid(vd, s, kBValuesDown, fl.w, fl.h, 1, &c2);
-                s = base(i, l, kWhenAlways);
-                s.in0 = cl.c;
                 s.mbits = cl.mbits;
                 s.wpr = mask_words_per_row(cl.w);
                 s.counter = b->bs.counts + (size_t)i * (kMaxLevels + 1) + 1 + l;
-                add_grid(pm, s, kBPack, cl.w, cl.h, 1, &c3);
+                add_grid(v, s, kBPyramid, fl.w, fl.h, 1, &cta);
             }
-            push(kBMaskDown, md, c1);
-            push(kBValuesDown, vd, c2);
-            push(kBPack, pm, c3);
+            push(kBPyramid, v, cta);
         }
     }
 
@@ -458,7 +449,6 @@ extern "C" di_status di_batch_create(const di_config* cfg, int device, const di_
         n0s[i] = (unsigned long long)I.w * I.h;
         tols[i] = I.tol;
     }
-    di_status st = DI_OK;
     // per-image state: leff, top, done, L, tol | n0 | StopState | upd | counts
     const size_t ints = (size_t)5 * n * sizeof(int);
     const size_t o_n0 = align_b(ints);

@@ -212,7 +212,8 @@ enum BatchWhen {
 };
 
 enum BatchKind {  // grid kernels of the batched form
-    kBMaskDown = 0, kBValuesDown = 1, kBPack = 2, kBSelect = 3, kBRestrict = 4, kBProlong = 5
+    kBMaskDown = 0, kBValuesDown = 1, kBPack = 2, kBSelect = 3, kBRestrict = 4, kBProlong = 5,
+    kBPyramid = 6  // one pyramid level in one pass (mask, values, packed words, unknown count)
 };
 
 struct BatchSeg {

@@ -219,18 +219,20 @@ __global__ void k_values_down(const uint8_t* __restrict__ c, const float* __rest
 // warp of 32 consecutive X packs the 32 mask bits of its row (known or beyond
 // the image = 1) and counts the unknown ones; the CTAs of the last column
 // write the padding word of their rows.  Each thread reads its four children's
-// mask bytes once (8-byte aligned pairs where the image allows); the modified
+// mask bytes once (as byte pairs where the image allows); the modified
 // weights take the four neighbouring coarse cells' masks from a shared tile
 // of the CTA's cells and their one-cell halo, so the level needs no second
-// pass.  values = 0: masks only (a given start).
-__global__ void __launch_bounds__(256)
-k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int w, int h, int C,
-                uint8_t* __restrict__ cH, float* __restrict__ bH, int wH, int hH, int modified,
-                int values, uint32_t* __restrict__ bits, int wpr,
-                unsigned long long* __restrict__ unknown) {
+// pass.  values = 0: masks only (a given start).  A CTA of 32 x 8 threads;
+// (bx, by) its position, nbx the CTAs along x (one column per packed word of
+// a coarse row but the padding word).
+__device__ __forceinline__ void pyramid_level_body(
+    const uint8_t* __restrict__ c, const float* __restrict__ b, int w, int h, int C,
+    uint8_t* __restrict__ cH, float* __restrict__ bH, int wH, int hH, int modified, int values,
+    uint32_t* __restrict__ bits, int wpr, unsigned long long* __restrict__ unknown, int bx,
+    int by, int nbx) {
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int X = blockIdx.x * 32 + tx;
-    const int Y = blockIdx.y * 8 + ty;
+    const int X = bx * 32 + tx;
+    const int Y = by * 8 + ty;
     const int lane = tx;
     // children bytes of coarse cell (Xc, Yc), 0 where a child is off the image
     const bool pairs = (w & 1) == 0 && (reinterpret_cast<uintptr_t>(c) & 1) == 0;
@@ -328,9 +330,9 @@ k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int 
     const unsigned word = __ballot_sync(0xffffffffu, X >= wH || kn);
     unsigned unk = 0;
     if (Y < hH) {
-        if (lane == 0) bits[(size_t)Y * wpr + blockIdx.x] = word;
+        if (lane == 0) bits[(size_t)Y * wpr + bx] = word;
         unk = X < wH && !kn ? 1u : 0u;
-        if (blockIdx.x == gridDim.x - 1 && lane == 0)
+        if (bx == nbx - 1 && lane == 0)
             bits[(size_t)Y * wpr + wpr - 1] = 0xffffffffu;  // the padding word
     }
     if (unknown) {
@@ -344,6 +346,15 @@ k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int 
             if (a) atomicAdd(unknown, a);
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_pyramid_level(const uint8_t* __restrict__ c, const float* __restrict__ b, int w, int h, int C,
+                uint8_t* __restrict__ cH, float* __restrict__ bH, int wH, int hH, int modified,
+                int values, uint32_t* __restrict__ bits, int wpr,
+                unsigned long long* __restrict__ unknown) {
+    pyramid_level_body(c, b, w, h, C, cH, bH, wH, hH, modified, values, bits, wpr, unknown,
+                       blockIdx.x, blockIdx.y, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -2467,7 +2478,12 @@ k_batch_grid(const BatchSeg* __restrict__ segs, int nseg, BatchState bs) {
     const int plane = sg.gx * sg.gy;
     const int bz = local / plane, rem = local - bz * plane;
     const int by = rem / sg.gx, bx = rem - by * sg.gx;
-    if (KIND == kBMaskDown)
+    if (KIND == kBPyramid)
+        pyramid_level_body(static_cast<const uint8_t*>(sg.in0), static_cast<const float*>(sg.in1),
+                           w, h, sg.C, static_cast<uint8_t*>(sg.out0),
+                           static_cast<float*>(sg.out1), wH, hH, sg.mode, 1,
+                           const_cast<uint32_t*>(sg.mbits), sg.wpr, sg.counter, bx, by, sg.gx);
+    else if (KIND == kBMaskDown)
         mask_down_body(static_cast<const uint8_t*>(sg.in0), w, h, static_cast<uint8_t*>(sg.out0),
                        wH, hH, bx, by);
     else if (KIND == kBValuesDown)
@@ -2616,7 +2632,7 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
         if (more) prefetch(nxt, buf ^ 1, nxt.seg != cur.seg || nxt.blk != cur.blk);
 
         const BatchSeg& sg = segs[cur.seg];
-        const int w = sg.w, h = sg.h, C = sg.C, nbx = sg.nbx, nby = sg.nby;
+        const int w = sg.w, h = sg.h, nbx = sg.nbx, nby = sg.nby;
         const int zero_in = sg.zero_in, rhs_zero = sg.rhs_zero;
         const size_t n = (size_t)w * h;
         if (cur.seg != cur_seg) {
@@ -3549,7 +3565,7 @@ void batch_grid_dims(int kind, int w, int h, int* gx, int* gy) {
         *gx = (int)(b < 1 ? 1 : b);
         *gy = 1;
     } else if (kind == kBRestrict || kind == kBProlong || kind == kBMaskDown ||
-               kind == kBValuesDown) {  // one thread per coarse cell, 32 x 8 per CTA
+               kind == kBValuesDown || kind == kBPyramid) {  // a coarse cell per thread, 32 x 8 per CTA
         const int wH = (w + 1) / 2, hH = (h + 1) / 2;
         *gx = (wH + 31) / 32;
         *gy = (hH + 7) / 8;
@@ -3569,6 +3585,7 @@ cudaError_t launch_batch_grid(int kind, const BatchSeg* segs, int nseg, int ncta
         case kBSelect: k_batch_grid<kBSelect><<<nctas, blk1, 0, s>>>(segs, nseg, bs); break;
         case kBRestrict: k_batch_grid<kBRestrict><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
         case kBProlong: k_batch_grid<kBProlong><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
+        case kBPyramid: k_batch_grid<kBPyramid><<<nctas, blk2, 0, s>>>(segs, nseg, bs); break;
         default: return cudaErrorInvalidValue;
     }
     count();
