@@ -306,7 +306,9 @@ di_status di_batch_create(const di_config *cfg, int device, const di_image *imgs
                           di_batch **out);
 /* One decode of the batch: imgs must be the images it was created for; their
  * status and cycles are filled.  Waits for the work; returns DI_OK or the
- * first non-OK image status. */
+ * first non-OK image status, or DI_ERR_TIMEOUT (every image's status too)
+ * when a bounded device-side wait of the block kernel ran out, in which case
+ * every output of the run is undefined. */
 di_status di_batch_run(di_batch *b, di_image *imgs, int n, void *stream);
 void di_batch_destroy(di_batch *b);
 

@@ -68,6 +68,7 @@ struct di_batch {
     void* pool = nullptr;      // level buffers of every image
     void* state = nullptr;     // per-image device state
     BatchSeg* dsegs = nullptr; // every launch's segments
+    void* dmaps = nullptr;     // tensor maps of the block-kernel segments (kTileMapsBytes each)
     int* dL = nullptr;
     unsigned long long* dn0 = nullptr;
     BatchState bs;
@@ -99,6 +100,7 @@ void free_batch(di_batch* b) {
     if (b->pool) cudaFree(b->pool);
     if (b->state) cudaFree(b->state);
     if (b->dsegs) cudaFree(b->dsegs);
+    if (b->dmaps) cudaFree(b->dmaps);
     if (b->hstate) cudaFreeHost(b->hstate);
     delete b;
 }
@@ -148,10 +150,15 @@ bool alloc_levels(di_batch* b) {
 }
 
 // The segment tables of every launch, in graph order, and the graph.
+struct alignas(64) TileMaps {
+    unsigned char bytes[kTileMapsBytes];
+};
+
 struct Builder {
     di_batch* b;
     std::vector<BatchSeg> segs;
     std::vector<Launch> launches;
+    std::vector<TileMaps> maps;  // a block segment with tma = 1 holds its index in tmaps
     int Lmax = 0;
 
     BatchSeg base(int img, int level, int when) const {
@@ -206,6 +213,12 @@ struct Builder {
         s.pro_mode = pro_e ? pro_mode : 0;
         s.pro_max = pro_max;
         s.pro_check = pro_check;
+        TileMaps tm;
+        if (make_tile_maps(&tm, in, zero_in, rhs, rhs_zero, lv.w, lv.h, s.C)) {
+            s.tma = 1;
+            s.tmaps = reinterpret_cast<const void*>(static_cast<uintptr_t>(maps.size()));
+            maps.push_back(tm);
+        }
         s.first = *units;
         *units += s.nbx * s.nby;
         v.push_back(s);
@@ -449,13 +462,14 @@ extern "C" di_status di_batch_create(const di_config* cfg, int device, const di_
         n0s[i] = (unsigned long long)I.w * I.h;
         tols[i] = I.tol;
     }
-    // per-image state: leff, top, done, L, tol | n0 | StopState | upd | counts
+    // per-image state: leff, top, done, L, tol | n0 | StopState | upd | counts | err
     const size_t ints = (size_t)5 * n * sizeof(int);
     const size_t o_n0 = align_b(ints);
     const size_t o_st = o_n0 + align_b((size_t)n * sizeof(unsigned long long));
     const size_t o_upd = o_st + align_b((size_t)n * sizeof(StopState));
     const size_t o_cnt = o_upd + align_b((size_t)n * (kMaxUpdSlots + 1) * sizeof(unsigned));
-    const size_t state_bytes = o_cnt + (size_t)n * (kMaxLevels + 1) * sizeof(unsigned long long);
+    const size_t o_err = o_cnt + align_b((size_t)n * (kMaxLevels + 1) * sizeof(unsigned long long));
+    const size_t state_bytes = o_err + sizeof(unsigned);
     if (!alloc_levels(b) || cudaMalloc(&b->state, state_bytes) != cudaSuccess ||
         cudaMallocHost(&b->hstate, (size_t)n * sizeof(StopState)) != cudaSuccess) {
         free_batch(b);
@@ -472,6 +486,7 @@ extern "C" di_status di_batch_create(const di_config* cfg, int device, const di_
     b->bs.st = reinterpret_cast<StopState*>(sp + o_st);
     b->bs.upd = reinterpret_cast<unsigned*>(sp + o_upd);
     b->bs.counts = reinterpret_cast<unsigned long long*>(sp + o_cnt);
+    b->bs.err = reinterpret_cast<unsigned*>(sp + o_err);
     if (cudaMemcpy(b->dL, Ls.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(dtol, tols.data(), n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->dn0, n0s.data(), n * sizeof(unsigned long long), cudaMemcpyHostToDevice) !=
@@ -486,6 +501,19 @@ extern "C" di_status di_batch_create(const di_config* cfg, int device, const di_
     B.build_cascade();
     const size_t n_casc = B.launches.size();
     B.build_cycle();
+    // the block segments' tensor maps, then their device addresses in the tables
+    if (!B.maps.empty()) {
+        if (cudaMalloc(&b->dmaps, B.maps.size() * sizeof(TileMaps)) != cudaSuccess ||
+            cudaMemcpy(b->dmaps, B.maps.data(), B.maps.size() * sizeof(TileMaps),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            free_batch(b);
+            return DI_ERR_OOM;
+        }
+        for (auto& sg : B.segs)
+            if (sg.tma)
+                sg.tmaps = static_cast<const TileMaps*>(b->dmaps) +
+                           reinterpret_cast<uintptr_t>(sg.tmaps);
+    }
     if (cudaMalloc(&b->dsegs, B.segs.size() * sizeof(BatchSeg)) != cudaSuccess ||
         cudaMemcpy(b->dsegs, B.segs.data(), B.segs.size() * sizeof(BatchSeg),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -578,11 +606,18 @@ extern "C" di_status di_batch_run(di_batch* b, di_image* imgs, int n, void* stre
     }
     if (cudaSetDevice(b->device) != cudaSuccess) return DI_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaGraphLaunch(b->exec, s) != cudaSuccess ||
+    unsigned err = 0;
+    if (cudaMemsetAsync(b->bs.err, 0, sizeof(unsigned), s) != cudaSuccess ||
+        cudaGraphLaunch(b->exec, s) != cudaSuccess ||
         cudaMemcpyAsync(b->hstate, b->bs.st, (size_t)n * sizeof(StopState),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+        cudaStreamSynchronize(s) != cudaSuccess ||
+        cudaMemcpy(&err, b->bs.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
         return DI_ERR_CUDA;
+    if (err) {  // a bounded wait of the block kernel ran out: nothing of the run is valid
+        for (int i = 0; i < n; ++i) imgs[i].status = DI_ERR_TIMEOUT;
+        return DI_ERR_TIMEOUT;
+    }
     di_status worst = DI_OK;
     int iters = 1;  // the loop body runs at least once
     for (int i = 0; i < n; ++i) {

@@ -240,7 +240,22 @@ struct BatchSeg {
     const float* pro_e;
     unsigned* pro_max;
     int pro_mode, pro_check;
+    // block kernel: tma = 1 when the u_in and rhs tiles come by TMA through
+    // the two tensor maps at tmaps (device memory, kTileMapsBytes, made by
+    // make_tile_maps); 0: 4-byte cp.async
+    const void* tmaps;
+    int tma;
 };
+
+// Bytes of the two tensor maps (u_in tile, right-hand-side tile) of a block-
+// kernel segment.
+constexpr size_t kTileMapsBytes = 256;
+// Writes the tensor maps of the 32x32 block kernel's u_in and rhs tiles over
+// FP32 [C][h][w] images into out (kTileMapsBytes, 64-byte aligned host
+// memory); a null image (zero_in / rhs_zero) gets no map.  False if an image
+// does not meet TMA's rules (w a multiple of 4, 16-byte aligned base).
+bool make_tile_maps(void* out, const float* u_in, int zero_in, const float* rhs, int rhs_zero,
+                    int w, int h, int C);
 
 // Per-image decode state of a batch (device arrays of n images).
 struct BatchState {
@@ -250,6 +265,7 @@ struct BatchState {
     StopState* st;
     unsigned* upd;  // [n][kMaxUpdSlots + 1]
     unsigned long long* counts;  // [n][kMaxLevels + 1]
+    unsigned* err;               // set to 1 when a bounded wait of the block kernel ran out
     const float* tol;  // stop-rule target per image
 };
 

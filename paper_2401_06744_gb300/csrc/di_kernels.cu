@@ -2506,11 +2506,13 @@ k_batch_grid(const BatchSeg* __restrict__ segs, int nseg, BatchState bs) {
 // The block kernel over the block units of a batch: a unit is one 32x32
 // block of one image's level with all its channels back to back; CTAs are
 // persistent and stride over the units of every image in the launch, skipping
-// the units of images that do not take part.  Tiles by 4-byte cp.async
-// (prefetched while the previous task solves); 0/1 partition weights
-// (overlap 2: each pixel is written by the one block whose weight is 1
-// there).  Otherwise the local problem, the CG and the write are those of
-// k_oras_2w.
+// the units of images that do not take part.  Tiles by TMA through each
+// segment's tensor maps, or by 4-byte cp.async where an image does not allow
+// TMA (prefetched while the previous task solves; a TMA wait that runs out
+// sets *bs.err and the CTA leaves); 0/1 partition weights (overlap 2: each
+// pixel is written by the one block whose weight is 1 there); a segment may
+// form its start by prolongation (BatchSeg).  Otherwise the local problem,
+// the CG and the write are those of k_oras_2w.
 __global__ void __launch_bounds__(64, 8)
 k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, float alpha,
              BatchState bs) {
@@ -2524,6 +2526,7 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
     float* const s_e = smem + Smem2W::EP;  // coarse patches of prolonging segments
     float* const s_b = smem + Smem2W::RHS_PRO;
     __shared__ float s_red1[2], s_red2[2], s_seam[2][32];
+    __shared__ __align__(8) unsigned long long s_bar[2];  // TMA tiles of buffer 0, 1
 
     const int t = threadIdx.x;
     const int lane = t & 31, wi = t >> 5;
@@ -2556,6 +2559,8 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
         return false;
     };
     uint32_t nlo = 0xffffffffu, nhi = 0xffffffffu, nhk = 3u;
+    // bit b: buffer b awaits a TMA completion; parity of its next completion
+    unsigned pend_tma = 0, phase = 0;
     auto prefetch = [&](const Task& tk, int bs_, bool new_blk) {
         const BatchSeg& sg = segs[tk.seg];
         const int w = sg.w, h = sg.h, nbx = sg.nbx;
@@ -2567,7 +2572,27 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
                                px0, py0, wH, hH, t);
             if (new_blk) nhk = halo_known_bits(sg.mbits, sg.wpr, w, h, px0, py0, wi, lane);
         }
-        if (!sg.zero_in) {
+        if (sg.tma) {
+            // the tiles by TMA, as in k_oras_2w (x rounded down to a multiple
+            // of 4; the tile is indexed from the remainder)
+            if (t == 0) {
+                const CUtensorMap* maps = static_cast<const CUtensorMap*>(sg.tmaps);
+                const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[bs_]);
+                const unsigned bytes = (sg.zero_in ? 0u : (unsigned)Smem2W::TMA_U_BYTES) +
+                                       (sg.rhs_zero ? 0u : (unsigned)Smem2W::TMA_B_BYTES);
+                // the buffer's previous contents were read before the loop-top barrier
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(bar), "r"(bytes) : "memory");
+                if (!sg.zero_in)
+                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_u + bs_ * TILE), &maps[0],
+                                (px0 - 1) & ~3, py0 - 1, tk.ch, bar);
+                if (!sg.rhs_zero)
+                    tma_load_3d((unsigned)__cvta_generic_to_shared(s_b + bs_ * Smem2W::BSTRIDE),
+                                &maps[1], px0 & ~3, py0, tk.ch, bar);
+            }
+            pend_tma |= 1u << bs_;
+        } else if (!sg.zero_in) {
             const float* src = static_cast<const float*>(sg.in0) + tk.ch * n;
             float* dst = s_u + bs_ * TILE;
             const int gxa = px0 - 1 + lane, gxb = gxa + 32;
@@ -2583,7 +2608,7 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
                     cp_async4(dst + ty * P + lane + 32, (rok && okb) ? row + gxb : src, rok && okb);
             }
         }
-        if (!sg.rhs_zero) {
+        if (!sg.tma && !sg.rhs_zero) {
             const float* src = static_cast<const float*>(sg.in1) + tk.ch * n;
             float* dst = s_b + bs_ * Smem2W::BSTRIDE;
             const int gx = px0 + lane;
@@ -2610,6 +2635,14 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
     int g = -1;
     Task cur{-1, 0, 0};
     if (!advance(g, cur)) return;  // block-uniform
+    if (t == 0) {
+        for (int k = 0; k < 2; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
+                         :: "r"((unsigned)__cvta_generic_to_shared(&s_bar[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // no thread may probe a barrier before it is initialised
+    __syncthreads();
     prefetch(cur, 0, true);
     int buf = 0;
     int cur_seg = -1, cur_blk = -1;
@@ -2624,7 +2657,20 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
 
     for (;;) {
         cp_async_wait_all();
-        __syncthreads();
+        if ((pend_tma >> buf) & 1u) {  // uniform: the task's segment decides
+            const unsigned bar = (unsigned)__cvta_generic_to_shared(&s_bar[buf]);
+            const bool ok = mbar_wait(bar, (phase >> buf) & 1u);
+            phase ^= 1u << buf;
+            pend_tma &= ~(1u << buf);
+            if (__syncthreads_or(!ok)) {
+                // give the copy one more bounded wait before the CTA leaves
+                if (!ok) mbar_wait(bar, ((phase >> buf) & 1u) ^ 1u);
+                if (t == 0 && bs.err) atomicExch(bs.err, 1u);
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
         const uint32_t mlo = nlo, mhi = nhi, hk = nhk;
         Task nxt = cur;
         int g2 = g;
@@ -2692,16 +2738,19 @@ k_batch_oras(const BatchSeg* __restrict__ segs, int nseg, int nunits, int o, flo
             if (t < B) s_wy[t] = wyl;
             rows_w = __ballot_sync(kFull, wyl > 0.f && lane < bh);
         }
-        const float* tu = s_u + buf * TILE;
-        const float* tb = s_b + buf * Smem2W::BSTRIDE;
+        // TMA tiles start at the 4-aligned column below the halo column
+        const int du = sg.tma ? ((x0 - 1) & 3) : 0;
+        const int db = sg.tma ? (x0 & 3) : 0;
+        const float* tu = s_u + buf * TILE + du;
+        const float* tb = s_b + buf * Smem2W::BSTRIDE + db;
         if (prolongs(sg)) {  // uniform per task
             const float* pe = s_e + buf * Smem2W::ESTRIDE;
             if (sg.pro_mode == 1)
-                prolong_into_tile<true>(s_u + buf * TILE, pe, row0, col, lane, wi, x0, y0, mbk, hk,
-                                        pmax);
+                prolong_into_tile<true>(s_u + buf * TILE + du, pe, row0, col, lane, wi, x0, y0,
+                                        mbk, hk, pmax);
             else
-                prolong_into_tile<false>(s_u + buf * TILE, pe, row0, col, lane, wi, x0, y0, mbk,
-                                         hk, pmax);
+                prolong_into_tile<false>(s_u + buf * TILE + du, pe, row0, col, lane, wi, x0, y0,
+                                         mbk, hk, pmax);
             __syncthreads();  // the residual reads the other threads' columns
         }
 
@@ -3192,6 +3241,15 @@ cudaError_t launch_combine(float* planes, int w, int h, int C, int B, int o, int
 }
 
 }  // namespace
+
+bool make_tile_maps(void* out, const float* u_in, int zero_in, const float* rhs, int rhs_zero,
+                    int w, int h, int C) {
+    CUtensorMap* m = static_cast<CUtensorMap*>(out);
+    std::memset(m, 0, 2 * sizeof(CUtensorMap));
+    static_assert(2 * sizeof(CUtensorMap) == kTileMapsBytes, "two tensor maps");
+    return (zero_in || make_map(&m[0], u_in, w, h, C, Smem2W::PU, Smem2W::TH)) &&
+           (rhs_zero || make_map(&m[1], rhs, w, h, C, Smem2W::PB, 32));
+}
 
 // ---------------------------------------------------------------------------
 // Launch wrappers
