@@ -5,22 +5,30 @@
 // every level (coarse right-hand sides carry the (H/h)^2 = 4 factor).
 //
 // Kernels:
-//   k_count_mask     known / unknown pixel counts of the finest mask
-//   k_mask_down      Section 4.3 mask downsampling (2x2 max pooling)
-//   k_values_down    Section 4.3 modified (or naive) mask-value downsampling
+//   k_pyramid_level  Section 4.3: one pyramid level in one pass (2x2 max pooling of
+//                    the mask, modified or naive mask values, packed mask words,
+//                    unknown count); k_mask_down, k_values_down and k_pack_mask
+//                    are the separate steps (single-step entry points, the finest
+//                    level's packing)
 //   k_residual       r = b - A u with per-CTA partial sums of r^2 (Algorithm 2 step 1)
 //   k_reduce         fixed-order sum of the partials (one global scalar product)
 //   k_restrict       Algorithm 3 steps 2-3 fused: residual + 2x2 averaging (x4)
 //   k_prolong        Section 4.4 bilinear prolongation, cascadic or correction mode
+//                    (where the block kernel cannot form its start by prolongation)
 //   k_select         u = c ? b : 0 (or c ? b : u for a given start)
-//   k_pack_mask      bit-packed copy of a level's mask for the block solver
-//   k_oras_warp      Algorithm 2 step 2 and the D_i-weighted part of step 3:
-//                    one warp per (block, channel); the block and a one-pixel
-//                    halo are staged in shared memory and the local Robin
-//                    problem is solved by plain CG held in registers
+//   k_oras_2w        Algorithm 2 steps 1-3 for 32x32 blocks: two warps per (block,
+//                    channel), plain CG in registers as packed FP32 pairs, tiles by
+//                    TMA; optionally the start formed by prolongation inside it
+//   k_oras_2w_h      the same with FP16 / BF16 local iterates
+//   k_oras_warp      8x8 and 16x16 blocks: one warp per (block, channel)
 //   k_combine_rows/cols  Algorithm 2 step 3 for pixels shared by several
 //                    blocks: sum the weighted block contributions in a fixed
 //                    order (shared rows full width, then shared columns)
+//   k_plan, k_stop   the device-driven decode: levels in use and start, and the
+//                    stop test after every V-cycle (conditional graph nodes)
+//   k_batch_*        the batched form: the same steps over the segment tables of
+//                    every image of a batch
+//   k_cg_*           the global CG smoother of the comparison methods (Section 5)
 //
 // Layout: images planar [C][h][w] float32, masks [h][w] uint8.  The ORAS
 // block pass writes pixels that only one block weights (weight 1) straight to
