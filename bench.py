@@ -441,7 +441,7 @@ def run_ours(args):
             _, info = srv.wait(t)
             if info["status"] != di.OK:
                 raise RuntimeError(di.status_string(info["status"]))
-            lat.append((info["latency_ms"], info["queue_ms"]))
+            lat.append((info["latency_ms"], info["queue_ms"], info["stages_ms"]))
 
         for i in range(n):
             if i >= R:
@@ -464,11 +464,12 @@ def run_ours(args):
         ms_ = (time.perf_counter() - t0) * 1e3
         if ws > 1:
             ms_ = max_over_ranks(ms_, dev)
-        slow = max(lat)
+        slow = max(lat, key=lambda x: x[0])
         e2e_ms_runs.append(ms_)
         e2e_runs.append({"frames_per_s": round(job_rate(e2e_steps, ws, ms_), 1),
                          "slowest_request_ms": round(slow[0], 1),
-                         "its_queue_ms": round(slow[1], 1)})
+                         "its_queue_ms": round(slow[1], 1),
+                         "its_stages_ms": {k: round(v, 1) for k, v in slow[2].items()}})
     e2e_ms = sorted(e2e_ms_runs)[len(e2e_ms_runs) // 2]  # the median run (max over ranks)
     srv.close()
     h2d = f_host[0].numel() * 4 + c_host[0].numel()

@@ -367,6 +367,12 @@ typedef struct {
     double latency_ms;        /* submit to completion */
     double queue_ms;          /* submit to start */
     long long footprint_bytes; /* device bytes charged against the budget */
+    /* the slot's stages after the start (their sum with queue_ms is latency_ms): */
+    double copy_in_ms;        /* host-to-device copy of f and c */
+    double wait_decode_ms;    /* until the slot's decoder takes it */
+    double decode_ms;         /* the decode, its status and statistics */
+    double wait_out_ms;       /* until the slot's output stage takes it */
+    double copy_out_ms;       /* device-to-host copy of u */
 } di_request_info;
 
 di_status di_server_create(const di_config *cfg, int device, int slots, long long mem_budget,

@@ -78,7 +78,9 @@ class di_tune_space(ctypes.Structure):
 class di_request_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double),
-                ("footprint_bytes", ctypes.c_longlong)]
+                ("footprint_bytes", ctypes.c_longlong), ("copy_in_ms", ctypes.c_double),
+                ("wait_decode_ms", ctypes.c_double), ("decode_ms", ctypes.c_double),
+                ("wait_out_ms", ctypes.c_double), ("copy_out_ms", ctypes.c_double)]
 
 
 class DiError(RuntimeError):
@@ -621,7 +623,10 @@ class Server:
         st = load().di_server_wait(self._h, int(ticket), ctypes.byref(info))
         f, c, u = self._live.pop(ticket)
         return u, {"status": st, "cycles": info.cycles, "latency_ms": info.latency_ms,
-                   "queue_ms": info.queue_ms, "footprint_bytes": info.footprint_bytes}
+                   "queue_ms": info.queue_ms, "footprint_bytes": info.footprint_bytes,
+                   "stages_ms": {"copy_in": info.copy_in_ms, "wait_decode": info.wait_decode_ms,
+                                 "decode": info.decode_ms, "wait_out": info.wait_out_ms,
+                                 "copy_out": info.copy_out_ms}}
 
     def close(self):
         if self._h:

@@ -292,7 +292,9 @@ struct Request {
     int w, h, ch;
     float tol;
     size_t bytes;  // device footprint while in flight
-    std::chrono::steady_clock::time_point t_submit, t_start, t_done;
+    // submitted, taken by a slot, copied in, taken by the decoder, decoded,
+    // taken by the output stage, done
+    std::chrono::steady_clock::time_point t_submit, t_start, t_in, t_dec0, t_dec1, t_out0, t_done;
     di_status status = DI_OK;
     int cycles = 0;
     int set = -1;  // buffer set of its slot
@@ -449,6 +451,7 @@ void input_stage(di_server* srv, ServerSlot* sl) {
             cudaGetLastError();
             r->status = DI_ERR_CUDA;
         }
+        r->t_in = std::chrono::steady_clock::now();
         sl->to_decode.push(r);
     }
     sl->to_decode.close();
@@ -458,6 +461,7 @@ void decode_stage(di_server* srv, ServerSlot* sl) {
     cudaSetDevice(srv->device);
     Request* r = nullptr;
     while (sl->to_decode.pop(r)) {
+        r->t_dec0 = std::chrono::steady_clock::now();
         if (r->status == DI_OK) {
             BufSet& b = sl->sets[r->set];
             di_status st = di_inpaint(sl->s.ctx, b.f, b.c, r->w, r->h, r->ch, r->tol, b.u,
@@ -470,6 +474,7 @@ void decode_stage(di_server* srv, ServerSlot* sl) {
             r->status = st;
             r->cycles = ss.cycles;
         }
+        r->t_dec1 = std::chrono::steady_clock::now();
         sl->to_output.push(r);
     }
     sl->to_output.close();
@@ -479,6 +484,7 @@ void output_stage(di_server* srv, ServerSlot* sl) {
     cudaSetDevice(srv->device);
     Request* r = nullptr;
     while (sl->to_output.pop(r)) {
+        r->t_out0 = std::chrono::steady_clock::now();
         if (r->status == DI_OK || r->status == DI_ERR_NOT_CONVERGED) {
             BufSet& b = sl->sets[r->set];
             const size_t pxch = (size_t)r->w * r->h * r->ch;
@@ -596,6 +602,11 @@ extern "C" di_status di_server_wait(di_server* srv, long long ticket, di_request
         info->latency_ms = ms(r->t_done - r->t_submit).count();
         info->queue_ms = ms(r->t_start - r->t_submit).count();
         info->footprint_bytes = (long long)r->bytes;
+        info->copy_in_ms = ms(r->t_in - r->t_start).count();
+        info->wait_decode_ms = ms(r->t_dec0 - r->t_in).count();
+        info->decode_ms = ms(r->t_dec1 - r->t_dec0).count();
+        info->wait_out_ms = ms(r->t_out0 - r->t_dec1).count();
+        info->copy_out_ms = ms(r->t_done - r->t_out0).count();
     }
     di_status st = r->status;
     delete r;

@@ -141,6 +141,10 @@ def test_server_poisson_mixed_load(di):
     lat = sorted(r[1]["latency_ms"] for r in results)
     assert all(r[1]["status"] == di.OK for r in results)
     assert lat[-1] > 0
+    for _, info in results:  # the stages after the start add up to the rest of the latency
+        st = info["stages_ms"]
+        assert min(st.values()) >= 0.0 and st["decode"] > 0.0
+        assert abs(info["queue_ms"] + sum(st.values()) - info["latency_ms"]) < 1e-3
     for k, ((f, c), (u, info)) in enumerate(zip(reqs, results)):
         assert np.array_equal(u[:, c == 1], f[:, c == 1])
         if k % 3 == 0:  # same result alone as in the mix
