@@ -623,6 +623,37 @@ __device__ __forceinline__ void restrict_body(const TU* __restrict__ u, const TB
     if (cH[P]) { stf(rH + ch * nH + P, 0.f); return; }
     const TU* uc = u + ch * n;
     const int x0 = 2 * X - 1, y0 = 2 * Y - 1;
+    if (VEC && X >= 1 && Y >= 1 && 2 * X + 2 < w && 2 * Y + 2 < h) {
+        // a cell whose 4x4 patch lies inside the image (all but the border
+        // cells): every child has four neighbours and the count is 4, so the
+        // same sums as below without a bounds test (the same bits)
+        const TU* r0 = uc + (size_t)y0 * w + x0;
+        float t[4][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 mid = *reinterpret_cast<const float2*>(r0 + (size_t)j * w + 1);
+            t[j][1] = mid.x;
+            t[j][2] = mid.y;
+            t[j][0] = (j == 1 || j == 2) ? ldf(r0 + (size_t)j * w) : 0.f;
+            t[j][3] = (j == 1 || j == 2) ? ldf(r0 + (size_t)j * w + 3) : 0.f;
+        }
+        R sum = 0;
+#pragma unroll
+        for (int j = 1; j <= 2; ++j) {
+            float2 rb = make_float2(0.f, 0.f);
+            if (!rhs_zero)
+                rb = *reinterpret_cast<const float2*>(b + ch * n + (size_t)(y0 + j) * w + x0 + 1);
+#pragma unroll
+            for (int i = 1; i <= 2; ++i) {
+                const R lu = (R)4 * (R)t[j][i] -
+                             ((R)t[j][i - 1] + (R)t[j][i + 1] + (R)t[j - 1][i] + (R)t[j + 1][i]);
+                const R rhs = rhs_zero ? (R)0 : (R)(i == 1 ? rb.x : rb.y);
+                sum += rhs - lu;
+            }
+        }
+        stf(rH + ch * nH + P, (float)sum);
+        return;
+    }
     float t[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
