@@ -30,3 +30,19 @@ def test_reference_arm_prints_one_contract_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_kernel_hash_follows_code_not_comments():
+    # the committed DRAM figures are tied to the kernel code by a hash that
+    # leaves comments out: a comment edit keeps them, a code edit voids them
+    sys.path.insert(0, ROOT)
+    import bench
+
+    code = 'int f(int x) {  // twice x\n    /* a "block" comment */\n    return 2 * x;\n}\n'
+    assert bench._code_only(code) == "int f(int x) {\n    return 2 * x;\n}"
+    assert bench._code_only(code.replace("twice", "double")) == bench._code_only(code)
+    assert bench._code_only(code.replace("2 * x", "3 * x")) != bench._code_only(code)
+    # a comment marker inside a string literal is code
+    assert bench._code_only('const char* s = "a // b";') == 'const char* s = "a // b";'
+    prof = bench._dram_profile()
+    assert prof is not None and len(prof["kernel_sha"]) == 16
